@@ -1,0 +1,622 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties the oracle to something other than itself: a value the paper
+prints (tests/golden), a closed form, an invariant, or a special case that
+reduces to a textbook scheme.  A dropped term, a wrong sign or index, or a
+transposed operand anywhere in the oracle fails at least one of them.
+"""
+import copy
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2608_26908_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def _liquid_box(nx, ny, nz=1, bc=(0, 0, 0), n_phases=2, n_solutes=1, **params):
+    """All-liquid scenario on a small box with no buoyancy unless asked."""
+    sc = inputs.scenario("dendrite3d" if nz > 1 else "dendrite2d", nx=nx, ny=ny,
+                         nz=nz if nz > 1 else None)
+    sc["grid"]["bc"] = list(bc)
+    sc["grid"]["wall_rows"] = [0, 0, 0]
+    sc["n_phases"], sc["n_solutes"] = n_phases, n_solutes
+    p = sc["params"]
+    p["gbeta_c"] = [0.0, 0.0]
+    p["gbeta_T"] = 0.0
+    p["undercool"] = 0.0
+    for k, v in params.items():
+        p[k] = v
+    cells = nx * ny * nz
+    phi = np.zeros((n_phases, cells))
+    phi[0] = 1.0
+    mu = np.zeros((n_solutes, cells))
+    return sc, phi.reshape(-1), mu.reshape(-1)
+
+
+def _feq(w, c, rho, u):
+    """Second-order equilibrium used only to build initial populations."""
+    cu = np.einsum("ka,ax->kx", c[:, : u.shape[0]].astype(float), u)
+    uu = (u * u).sum(axis=0)
+    return w[:, None] * rho[None, :] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uu[None, :])
+
+
+# ----------------------------------------------------------------- lattices
+def test_d2q9_weights_and_numbering_match_paper_table():
+    w, c = oracle.lattice(9)
+    for row in _golden("lattice_weights.txt"):
+        if row[0] != "D2Q9":
+            continue
+        c2, count, num, den = int(row[1]), int(row[2]), int(row[3]), int(row[4])
+        sel = [k for k in range(9) if (c[k] ** 2).sum() == c2]
+        assert len(sel) == count
+        for k in sel:
+            assert w[k] == pytest.approx(num / den, abs=0, rel=1e-15)
+    for k, cx, cy in (map(int, r) for r in _golden("d2q9_numbering.txt")):
+        assert (c[k, 0], c[k, 1], c[k, 2]) == (cx, cy, 0)
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_lattice_moments_are_isotropic(q):
+    w, c = oracle.lattice(q)
+    D = 2 if q == 9 else 3
+    wf = [Fraction(x).limit_denominator(1000) for x in w]
+    assert sum(wf) == 1
+    for a in range(D):
+        assert sum(wf[k] * c[k, a] for k in range(q)) == 0
+        for b in range(D):
+            m2 = sum(wf[k] * c[k, a] * c[k, b] for k in range(q))
+            assert m2 == (Fraction(1, 3) if a == b else 0)
+    # fourth moment: (1/9)(d_ab d_cd + d_ac d_bd + d_ad d_bc)
+    d = np.eye(D, dtype=int)
+    for a in range(D):
+        for b in range(D):
+            for e in range(D):
+                for g in range(D):
+                    m4 = sum(wf[k] * c[k, a] * c[k, b] * c[k, e] * c[k, g] for k in range(q))
+                    iso = Fraction(d[a, b] * d[e, g] + d[a, e] * d[b, g] + d[a, g] * d[b, e], 9)
+                    assert m4 == iso
+    # each direction has its opposite
+    for k in range(q):
+        assert any((c[j] == -c[k]).all() for j in range(q))
+
+
+def test_presets_follow_appendix_b():
+    tab = {(r[0], r[1]): float(r[2]) for r in _golden("appendix_b_parameters.txt")}
+    den = inputs.scenario("dendrite2d")["params"]
+    eut = inputs.scenario("eutectic2d")["params"]
+    assert den["eps"] == pytest.approx(tab["binary", "eps"] / tab["binary", "dx"])
+    assert eut["eps"] == pytest.approx(tab["eutectic", "eps"] / tab["eutectic", "dx"])
+    assert den["D_liq"] == pytest.approx(
+        tab["common", "D_liquid"] * tab["binary", "dt"] / tab["binary", "dx"] ** 2)
+    assert eut["D_liq"] == pytest.approx(
+        tab["common", "D_liquid"] * tab["eutectic", "dt"] / tab["eutectic", "dx"] ** 2)
+    assert den["gamma"][0][1] == pytest.approx(tab["common", "gamma"] / tab["binary", "dx"])
+    assert eut["gamma"][1][2] == pytest.approx(tab["common", "gamma"] / tab["eutectic", "dx"])
+    assert den["delta"][0][1] == pytest.approx(tab["binary", "anisotropy_strength"])
+    assert eut["delta"][1][2] == 0.0 and eut["delta"][0][1] == 0.0
+
+
+# ----------------------------------------------------------------- interpolation
+def _h_of(n_phases, phis, which):
+    """h_which(phi) read back through the composition c = sum_a h_a c_a(mu)
+    with mu = 0, c_which^eq = 1 and every other c^eq = 0."""
+    m = phis.shape[1]
+    sc, _, _ = _liquid_box(m, 3, n_phases=n_phases)
+    for a in range(4):
+        sc["params"]["ceq"][a] = [1.0 if a == which else 0.0, 0.0]
+    phi = np.repeat(phis[:, :, None], 3, axis=2).transpose(0, 2, 1).reshape(n_phases, -1)
+    mu = np.zeros(3 * m)
+    f = oracle.rest_populations(sc)
+    c, _, _ = oracle.derived(sc, phi.reshape(-1), mu, f)
+    return c.reshape(3, m)[1]
+
+
+def test_h_two_phase_is_smoothstep():
+    s = np.linspace(0.0, 1.0, 41)
+    hs = _h_of(2, np.stack([1 - s, s]), 1)
+    np.testing.assert_allclose(hs, s * s * (3 - 2 * s), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("n_phases", [3, 4])
+def test_h_sum_rule_vertices_and_edges(n_phases):
+    rng = np.random.default_rng(7)
+    pts = rng.dirichlet(np.ones(n_phases), size=64).T
+    total = sum(_h_of(n_phases, pts, a) for a in range(n_phases))
+    np.testing.assert_allclose(total, 1.0, rtol=0, atol=1e-14)
+    eye = np.eye(n_phases)
+    for a in range(n_phases):
+        np.testing.assert_allclose(_h_of(n_phases, eye, a), eye[a], atol=1e-15)
+    # on the a-b edge the multi-phase h reduces to the two-phase smoothstep
+    s = np.linspace(0, 1, 17)
+    edge = np.zeros((n_phases, 17))
+    edge[0], edge[n_phases - 1] = 1 - s, s
+    np.testing.assert_allclose(_h_of(n_phases, edge, n_phases - 1), s * s * (3 - 2 * s), atol=1e-15)
+
+
+# ----------------------------------------------------------------- anisotropy
+def test_anisotropy_is_one_plus_delta_cos4theta_in_2d():
+    for delta in (0.0, 0.02, 0.05):
+        for th in np.linspace(0, 2 * math.pi, 37):
+            r = 0.37
+            q = [r * math.cos(th), r * math.sin(th)]
+            A, _ = oracle.gradient_energy(q, delta)
+            assert A == pytest.approx((1 + delta * math.cos(4 * th)) ** 2 * r * r, rel=1e-13)
+
+
+def test_cubic_anisotropy_special_directions_in_3d():
+    d = 0.03
+    for q, ac in (([1, 0, 0], 1 + d), ([1, 1, 0], 1 - d), ([1, 1, 1], 1 - 5 * d / 3)):
+        q = np.array(q, float) * 0.5
+        A, _ = oracle.gradient_energy(q, d)
+        assert A == pytest.approx(ac * ac * (q @ q), rel=1e-13)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gradient_energy_derivative_matches_finite_difference(dim):
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        q = rng.normal(size=dim)
+        _, dA = oracle.gradient_energy(q, 0.04)
+        h = 1e-6
+        fd = np.zeros(dim)
+        for j in range(dim):
+            e = np.zeros(dim)
+            e[j] = h
+            fd[j] = (oracle.gradient_energy(q + e, 0.04)[0] - oracle.gradient_energy(q - e, 0.04)[0]) / (2 * h)
+        np.testing.assert_allclose(dA, fd, rtol=1e-7, atol=1e-9)
+    q = rng.normal(size=dim)
+    _, dA = oracle.gradient_energy(q, 0.0)
+    np.testing.assert_array_equal(dA, 2 * q)
+
+
+# ----------------------------------------------------------------- phase field
+def _lap(a, dim):
+    out = -2 * dim * a
+    for ax in range(dim):
+        out = out + np.roll(a, 1, axis=ax) + np.roll(a, -1, axis=ax)
+    return out
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_isotropic_two_phase_step_is_textbook_allen_cahn(dim):
+    """N = 2, no anisotropy, both phases present everywhere: one step of the
+    multi-phase scheme is the scalar obstacle Allen-Cahn update with the
+    standard 5-point (7-point) Laplacian."""
+    n = 12
+    sc, _, _ = _liquid_box(n, n, n if dim == 3 else 1, delta=[[0.0] * 4 for _ in range(4)],
+                           undercool=0.15)
+    p = sc["params"]
+    grids = np.meshgrid(*[np.arange(n)] * dim, indexing="ij")
+    phase = sum(np.sin(2 * math.pi * (k + 1) * g / n + 0.3 * k) for k, g in enumerate(grids))
+    s = 0.5 + 0.25 * phase / dim  # in (0.25, 0.75); memory order (z,) y, x
+    mu = 0.02 * np.cos(2 * math.pi * grids[0] / n)
+    phi = np.stack([1 - s.reshape(-1), s.reshape(-1)])
+    f = oracle.rest_populations(sc)
+    phi1, _, _ = oracle.run(sc, phi.reshape(-1), mu.reshape(-1), f, 1)
+    # closed-form scalar update
+    g, eps, tau = p["gamma"][0][1], p["eps"], p["tau_phi"]
+    A, cl, cs, S = p["A"][1], p["ceq"][0][0], p["ceq"][1][0], p["S"][1]
+    dpsi = -mu * (cl - cs) + S * p["undercool"]  # psi_l - psi_s at T = T_E - u
+    sm = s
+    lap = _lap(sm, dim)
+    expect = sm + (g * eps * lap - 8 * g / (math.pi ** 2 * eps) * (1 - 2 * sm)
+                   + 3 * sm * (1 - sm) * dpsi) / (tau * eps)
+    np.testing.assert_allclose(phi1.reshape(2, -1)[1], expect.reshape(-1), rtol=0, atol=1e-14)
+    assert A == 1.0
+
+
+def _flat_interface(eps, mu_shift=0.0, steps=2000, delta=0.0):
+    n = int(16 * eps)
+    sc, _, _ = _liquid_box(n, 3, bc=(1, 0, 0), eps=eps, W0=eps)
+    p = sc["params"]
+    for a in range(4):
+        for b in range(4):
+            p["delta"][a][b] = delta if (a != b and (a == 0 or b == 0)) else 0.0
+    p["undercool"] = 0.3
+    x = np.arange(n) + 0.5
+    xc = n / 2
+    half = math.pi ** 2 * eps / 8
+    prof = 0.5 * (1 - np.sin(4 * np.clip(x - xc, -half, half) / (math.pi * eps)))  # solid left
+    s = np.tile(prof, 3)
+    phi = np.stack([1 - s, s]).reshape(-1)
+    dc = p["ceq"][0][0] - p["ceq"][1][0]
+    mu_star = 2 * p["A"][0] * dc * p["undercool"]
+    mu = np.full(3 * n, mu_star + mu_shift)
+    f = oracle.rest_populations(sc)
+    phi1, mu1, f1 = oracle.run(sc, phi, mu, f, steps)
+    return sc, x, prof, phi1.reshape(2, 3, n)[1, 1], mu1.reshape(3, n)[1], mu_star, f1
+
+
+def _crossing(x, s):
+    j = np.where((s[:-1] >= 0.5) & (s[1:] < 0.5))[0][0]
+    return x[j] + (s[j] - 0.5) / (s[j] - s[j + 1])
+
+
+def test_flat_interface_keeps_obstacle_profile_and_converges():
+    """At mu = mu* the grand potentials of solid and liquid are equal: the
+    interface stays put (up to the shift from the solute released while the
+    continuous profile relaxes to the discrete one) and keeps the obstacle
+    profile 0.5 (1 - sin(4 x / (pi eps))) up to a second-order error."""
+    errs, shifts = [], []
+    for eps in (4.0, 8.0):
+        sc, x, prof, s, mu, mu_star, f = _flat_interface(eps)
+        shifts.append(abs(_crossing(x, s) - _crossing(x, prof)))
+        errs.append(np.abs(s - prof).max())
+    assert shifts[0] < 0.03 and shifts[1] < 0.01
+    assert errs[0] < 2e-2
+    assert errs[0] / errs[1] > 3.0  # second order in 1/eps
+
+
+def test_flat_interface_equilibrium_compositions():
+    sc, x, prof, s, mu, mu_star, f = _flat_interface(4.0, steps=400)
+    p = sc["params"]
+    c, _, _ = oracle.derived(sc, np.stack([1 - np.tile(s, 3), np.tile(s, 3)]).reshape(-1),
+                             np.tile(mu, 3), f)
+    c = c.reshape(3, -1)[1]
+    u = p["undercool"]
+    dc = p["ceq"][0][0] - p["ceq"][1][0]
+    assert c[-1] == pytest.approx(p["ceq"][0][0] + dc * u, abs=1e-6)  # 0.555
+    assert c[0] == pytest.approx(p["ceq"][1][0] + dc * u, abs=1e-6)   # 0.205
+
+
+def test_interface_moves_with_the_sign_of_the_driving_force():
+    _, x, prof, s_lo, _, _, _ = _flat_interface(4.0, mu_shift=-0.05, steps=200)
+    _, _, _, s_hi, _, _, _ = _flat_interface(4.0, mu_shift=+0.05, steps=200)
+    x0 = _crossing(x, prof)
+    assert _crossing(x, s_lo) > x0 + 0.05  # mu below mu*: the solid grows
+    assert _crossing(x, s_hi) < x0 - 0.05  # mu above mu*: the solid melts
+
+
+def test_no_ghost_phase_three_phase_equals_two_phase():
+    sc2, _, _ = _liquid_box(40, 6, bc=(1, 0, 0), n_phases=2, undercool=0.3)
+    sc3, _, _ = _liquid_box(40, 6, bc=(1, 0, 0), n_phases=3, undercool=0.3)
+    for sc in (sc2, sc3):
+        p = sc["params"]
+        for a in range(3):
+            for b in range(3):
+                p["gamma"][a][b] = 0.2 if a != b else 0.0
+                p["delta"][a][b] = 0.0
+        p["ceq"][2] = [0.8, 0.0]
+        p["S"][2] = 2 * (0.45 - 0.8) ** 2
+        p["tau_phi"] = 4 * 2 * 0.2
+    x = np.arange(40) + 0.5
+    s = np.tile(np.clip(0.5 - (x - 20) / 10, 0, 1), 6)
+    mu = np.full(240, 0.1)
+    phi2 = np.stack([1 - s, s]).reshape(-1)
+    phi3 = np.stack([1 - s, s, np.zeros_like(s)]).reshape(-1)
+    a2, m2, _ = oracle.run(sc2, phi2, mu, oracle.rest_populations(sc2), 50)
+    a3, m3, _ = oracle.run(sc3, phi3, mu, oracle.rest_populations(sc3), 50)
+    a3 = a3.reshape(3, -1)
+    assert (a3[2] == 0.0).all()
+    np.testing.assert_allclose(a3[1], a2.reshape(2, -1)[1], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(m3, m2, rtol=0, atol=1e-14)
+
+
+def test_simplex_invariant_four_phases():
+    sc = inputs.scenario("eutectic3d", nx=16, ny=16, nz=24)
+    sc["init"]["height"] = 10
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    phi1, _, _ = oracle.run(sc, phi, mu, f, 15)
+    phi1 = phi1.reshape(4, -1)
+    assert phi1.min() >= 0.0
+    np.testing.assert_allclose(phi1.sum(axis=0), 1.0, rtol=0, atol=1e-14)
+    assert (phi1 != phi.reshape(4, -1)).any()
+
+
+# ----------------------------------------------------------------- chemical potential
+@pytest.mark.parametrize("dim", [2, 3])
+def test_frozen_liquid_mu_is_ftcs_heat_equation(dim):
+    """phi = liquid everywhere and U = 0: Eq. conc reduces to the explicit
+    heat equation with diffusivity D; on a periodic box its exact solution is
+    the Fourier multiplier (1 - 2 D sum_d (1 - cos k_d))^n."""
+    n = 16
+    steps = 25
+    sc, phi, _ = _liquid_box(n, n, n if dim == 3 else 1)
+    D = sc["params"]["D_liq"]
+    shape = (n,) * dim
+    mu0 = np.zeros(shape)
+    mu0[(n // 2,) * dim] = 1e-3
+    mu0 = mu0 + 1e-4 * np.cos(2 * math.pi * np.arange(n) / n)  # along x
+    f = oracle.rest_populations(sc)
+    _, mu1, f1 = oracle.run(sc, phi, mu0.reshape(-1), f, steps)
+    ks = np.meshgrid(*[2 * math.pi * np.fft.fftfreq(n)] * dim, indexing="ij")
+    mult = 1 - 2 * D * sum(1 - np.cos(k) for k in ks)
+    expect = np.real(np.fft.ifftn(np.fft.fftn(mu0) * mult ** steps))
+    np.testing.assert_allclose(mu1.reshape(shape), expect, rtol=0, atol=1e-17)
+    np.testing.assert_allclose(f1, f, rtol=0, atol=1e-15)
+
+
+# ----------------------------------------------------------------- lattice Boltzmann
+def _taylor_green_rate(L, tau):
+    sc, phi, mu = _liquid_box(L, L, tau_f=tau)
+    w, c = oracle.lattice(9)
+    x, y = np.meshgrid(np.arange(L), np.arange(L), indexing="xy")
+    k = 2 * math.pi / L
+    U0 = 1e-4
+    u = np.stack([U0 * np.cos(k * x) * np.sin(k * y), -U0 * np.sin(k * x) * np.cos(k * y)])
+    f = _feq(w, c, np.ones(L * L), u.reshape(2, -1)).reshape(-1)
+    t0, t1 = 100, 300
+    _, _, f = oracle.run(sc, phi, mu, f, t0)
+    _, _, ua = oracle.derived(sc, phi, mu, f, t0)
+    _, _, f = oracle.run(sc, phi, mu, f, t1 - t0, n0=t0)
+    _, _, ub = oracle.derived(sc, phi, mu, f, t1)
+    ref = u.reshape(-1)
+    amps = [(ua * ref).sum() / (ref * ref).sum(), (ub * ref).sum() / (ref * ref).sum()]
+    rate = -math.log(amps[1] / amps[0]) / (t1 - t0)
+    nu = (tau - 0.5) / 3
+    return rate / (2 * nu * k * k)
+
+
+def test_taylor_green_decays_at_the_bgk_viscosity():
+    r32 = _taylor_green_rate(32, 0.8)
+    r64 = _taylor_green_rate(64, 0.8)
+    assert abs(r32 - 1) < 1e-2
+    assert abs(r64 - 1) < 3e-3
+    assert abs(r32 - 1) / abs(r64 - 1) > 3.0  # second order in k
+
+
+def _poiseuille(tau, H=16, steps=6000):
+    F0 = 1e-6
+    sc, phi, mu = _liquid_box(H, 4, bc=(1, 0, 0), tau_f=tau, gbeta_T=F0, T_ref=0.0, T_E=1.0)
+    f = oracle.rest_populations(sc)
+    _, _, f = oracle.run(sc, phi, mu, f, steps)
+    _, rho, u = oracle.derived(sc, phi, mu, f, steps)
+    uy = u.reshape(2, 4, H)[1, 2]
+    return F0, (tau - 0.5) / 3, uy, rho
+
+
+def test_poiseuille_between_bounce_back_walls():
+    # bulk: discrete second difference is exactly -F/nu at any tau
+    F0, nu, uy, rho = _poiseuille(0.8)
+    d2 = uy[:-2] - 2 * uy[1:-1] + uy[2:]
+    np.testing.assert_allclose(d2, -F0 / nu, rtol=1e-8)
+    np.testing.assert_allclose(rho, 1.0, atol=1e-12)
+    # halfway bounce-back puts the wall exactly half a cell out when
+    # (tau - 1/2)^2 = 3/16, so the profile is the analytic parabola
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    F0, nu, uy, _ = _poiseuille(tau)
+    H = len(uy)
+    xs = np.arange(H) + 0.5
+    exact = F0 / (2 * nu) * xs * (H - xs)
+    np.testing.assert_allclose(uy, exact, rtol=1e-8)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_uniform_body_force_accelerates_exactly(dim):
+    F0 = 1e-5
+    sc, phi, mu = _liquid_box(6, 6, 6 if dim == 3 else 1, gbeta_T=F0, T_ref=0.0, T_E=1.0)
+    f = oracle.rest_populations(sc)
+    steps = 37
+    _, _, f1 = oracle.run(sc, phi, mu, f, steps)
+    _, rho, u = oracle.derived(sc, phi, mu, f1, steps)
+    u = u.reshape(dim, -1)
+    np.testing.assert_allclose(rho, 1.0, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(u[dim - 1], F0 * (steps + 0.5), rtol=1e-12)
+    np.testing.assert_allclose(u[: dim - 1], 0.0, atol=1e-20)
+
+
+def test_drag_stops_flow_in_solid():
+    """Uniform force through a box whose right half is solid: the implicit
+    drag makes the velocity in the solid the terminal value F/kappa-scaled
+    value far below the liquid one."""
+    F0 = 1e-6
+    sc, _, mu = _liquid_box(32, 4, bc=(1, 0, 0), gbeta_T=F0, T_ref=0.0, T_E=1.0)
+    sc["params"]["h_drag"] = 50.0
+    s = np.tile((np.arange(32) >= 16).astype(float), 4)
+    phi = np.stack([1 - s, s]).reshape(-1)
+    mu = np.full(128, 2 * 0.3 * 0.35)  # hold the interface near rest
+    sc["params"]["undercool"] = 0.3
+    f = oracle.rest_populations(sc)
+    _, _, f1 = oracle.run(sc, phi, mu, f, 400)
+    _, _, u = oracle.derived(sc, phi, mu, f1, 400)
+    uy = u.reshape(2, 4, 32)[1, 1]
+    assert uy[:12].max() > 50 * np.abs(uy[22:]).max()
+
+
+def test_quiescent_isothermal_melt_stays_exactly_at_rest():
+    sc, phi, _ = _liquid_box(20, 14, bc=(0, 1, 0), gbeta_c=[1e-3, 0.0], c_ref=[0.45, 0.0],
+                             gbeta_T=1e-3, T_ref=1.0, T_E=1.0)
+    mu = np.full(20 * 14, 2 * 1.0 * (0.45 - 0.45))
+    f = oracle.rest_populations(sc)
+    _, mu1, f1 = oracle.run(sc, phi, mu, f, 50)
+    np.testing.assert_allclose(f1, f, rtol=0, atol=1e-15)
+    _, _, u = oracle.derived(sc, phi, mu1, f1, 50)
+    assert np.abs(u).max() == 0.0
+
+
+# ----------------------------------------------------------------- conservation
+@pytest.mark.parametrize("case", ["dendrite2d", "eutectic2d", "dendrite3d", "eutectic3d"])
+def test_mass_and_solute_are_conserved(case):
+    sizes = {"dendrite2d": dict(nx=40, ny=36), "eutectic2d": dict(nx=48, ny=40),
+             "dendrite3d": dict(nx=14, ny=16, nz=18), "eutectic3d": dict(nx=16, ny=14, nz=20)}
+    sc = inputs.scenario(case, **sizes[case])
+    if case == "eutectic3d":
+        sc["init"]["height"] = 8
+    if case == "eutectic2d":
+        sc["init"]["height"] = 12
+    sc["params"]["gbeta_c"] = [3e-3, 2e-3]  # strong flow
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    m0, s0, _ = oracle.invariants(sc, phi, mu, f)
+    phi1, mu1, f1 = oracle.run(sc, phi, mu, f, 40)
+    m1, s1, _ = oracle.invariants(sc, phi1, mu1, f1)
+    _, _, u = oracle.derived(sc, phi1, mu1, f1, 40)
+    assert np.abs(u).max() > 1e-6  # there is flow
+    assert abs(m1 - m0) / m0 < 1e-12
+    np.testing.assert_allclose(s1, s0, rtol=1e-12)
+
+
+# ----------------------------------------------------------------- derivatives
+def test_dual_number_derivatives_match_central_differences():
+    sc = inputs.scenario("adjoint2d", nx=24, ny=24)
+    sc["init"]["radius"] = 5.0
+    sc["params"]["gbeta_c"] = [2e-3, 0.0]
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    obj = {"w_frac": 1.0, "w_tip": 1.0, "kappa": 2.0, "x0": 12, "y0": 12, "solid": 1}
+    steps = 12
+    rng = np.random.default_rng(5)
+    dmu = rng.normal(size=mu.shape) * 1e-2
+    J0, dJ = oracle.objective(sc, obj, phi, mu, f, steps, dmu0=dmu)
+    h = 1e-6
+    Jp, _ = oracle.objective(sc, obj, phi, mu + h * dmu, f, steps)
+    Jm, _ = oracle.objective(sc, obj, phi, mu - h * dmu, f, steps)
+    assert dJ == pytest.approx((Jp - Jm) / (2 * h), rel=1e-5)
+    base = copy.deepcopy(sc)
+    for j, key in enumerate(["tau_phi", "delta", "gbeta_c"]):
+        dc = np.zeros(3)
+        dc[j] = 1.0
+        _, dJ = oracle.objective(sc, obj, phi, mu, f, steps, dcoef=dc)
+        vals = []
+        for sgn in (+1, -1):
+            s2 = copy.deepcopy(base)
+            pp = s2["params"]
+            if key == "tau_phi":
+                pp["tau_phi"] = 1.0 / (1.0 / pp["tau_phi"] + sgn * h)
+            elif key == "delta":
+                for a in range(4):
+                    for b in range(4):
+                        if pp["delta"][a][b] != 0.0:
+                            pp["delta"][a][b] += sgn * h
+            else:
+                pp["gbeta_c"][0] += sgn * h
+            vals.append(oracle.objective(s2, obj, phi, mu, f, steps)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert dJ == pytest.approx(fd, rel=1e-4, abs=1e-9), key
+
+
+# ----------------------------------------------------------------- extra pins
+@pytest.mark.parametrize("dim", [2, 3])
+def test_uniform_flow_advects_mu_by_central_differences(dim):
+    """All liquid, uniform velocity U (f = f^eq(1, U), no force keeps U
+    uniform): Eq. conc becomes the FTCS advection-diffusion scheme whose
+    exact periodic solution is the multiplier
+    1 - 2 D sum_d (1 - cos k_d) - i sum_d U_d sin k_d per step."""
+    n, steps = 12, 15
+    sc, phi, _ = _liquid_box(n, n, n if dim == 3 else 1)
+    D = sc["params"]["D_liq"]
+    q = 9 if dim == 2 else 19
+    w, c = oracle.lattice(q)
+    U = np.array([0.011, -0.007, 0.005][:dim])
+    cells = n ** dim
+    u = np.repeat(U[:, None], cells, axis=1)
+    f = _feq(w, c, np.ones(cells), u).reshape(-1)
+    _, _, u0 = oracle.derived(sc, phi, np.zeros(cells), f)
+    Uc = u0.reshape(dim, -1)[:, 0]  # velocity on the grid (x, y[, z])
+    rng = np.random.default_rng(11)
+    mu0 = 1e-3 * rng.normal(size=(n,) * dim)
+    _, mu1, _ = oracle.run(sc, phi, mu0.reshape(-1), f, steps)
+    ks = np.meshgrid(*[2 * math.pi * np.fft.fftfreq(n)] * dim, indexing="ij")  # axes (z,) y, x
+    mult = 1 - 2 * D * sum(1 - np.cos(k) for k in ks)
+    for d in range(dim):
+        mult = mult - 1j * Uc[d] * np.sin(ks[dim - 1 - d])
+    expect = np.real(np.fft.ifftn(np.fft.fftn(mu0) * mult ** steps))
+    np.testing.assert_allclose(mu1.reshape((n,) * dim), expect, rtol=0, atol=1e-15)
+
+
+def test_solutal_buoyancy_sign_and_size():
+    """Uniform liquid richer than c_ref: the force g beta (c_l - c_ref) acts
+    upward along the vertical axis and U grows as F (n + 1/2)."""
+    gb, dc = 2e-4, 0.05
+    sc, phi, _ = _liquid_box(5, 6, gbeta_c=[gb, 0.0], c_ref=[0.45, 0.0])
+    mu = np.full(30, 2 * 1.0 * dc)  # c_l = 0.45 + dc
+    f = oracle.rest_populations(sc)
+    steps = 9
+    _, _, f1 = oracle.run(sc, phi, mu, f, steps)
+    _, _, u = oracle.derived(sc, phi, mu, f1, steps)
+    np.testing.assert_allclose(u.reshape(2, -1)[1], gb * dc * (steps + 0.5), rtol=1e-11)
+
+
+def test_implicit_drag_decay_factor():
+    """Uniform mushy cells (phi_l = 1/2 held by mu = mu*) with an initial
+    uniform flow: F = -rho kappa U with the implicit U gives the exact decay
+    factor (1 - kappa/2) / (1 + kappa/2) per step, kappa = 2 nu h (1 -
+    phi_l)^2 / W0^2."""
+    sc, _, _ = _liquid_box(6, 5, undercool=0.3)
+    p = sc["params"]
+    s = np.full(30, 0.5)
+    phi = np.stack([1 - s, s]).reshape(-1)
+    mu = np.full(30, 2 * 1.0 * 0.35 * 0.3)
+    w, c = oracle.lattice(9)
+    f = _feq(w, c, np.ones(30), np.repeat(np.array([[3e-4], [-1e-4]]), 30, axis=1)).reshape(-1)
+    _, _, u0 = oracle.derived(sc, phi, mu, f)
+    steps = 20
+    phi1, _, f1 = oracle.run(sc, phi, mu, f, steps)
+    np.testing.assert_array_equal(phi1, phi)
+    _, _, u1 = oracle.derived(sc, phi, mu, f1, steps)
+    nu = (p["tau_f"] - 0.5) / 3
+    kappa = 2 * nu * p["h_drag"] * 0.25 / p["W0"] ** 2
+    r = (1 - kappa / 2) / (1 + kappa / 2)
+    np.testing.assert_allclose(u1, u0 * r ** steps, rtol=1e-12)
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_streaming_moves_population_k_along_c_k(q):
+    """tau = 1 makes f* = f^eq; a density excess at one cell then arrives
+    one cell along c_k in population k (Eq. LBMEq_1)."""
+    dim = 2 if q == 9 else 3
+    n = 5
+    sc, phi, mu = _liquid_box(n, n, n if dim == 3 else 1, tau_f=1.0)
+    w, c = oracle.lattice(q)
+    cells = n ** dim
+    rho = np.ones(cells)
+    x0 = (2,) * dim
+    idx = np.ravel_multi_index(x0[::-1], (n,) * dim)
+    rho[idx] = 1.3
+    f = (w[:, None] * rho[None, :]).reshape(-1)
+    _, _, f1 = oracle.run(sc, phi, mu, f, 1)
+    f1 = f1.reshape(q, cells)
+    for k in range(q):
+        dest = tuple((np.array(x0) + c[k, :dim]) % n)
+        j = np.ravel_multi_index(dest[::-1], (n,) * dim)
+        expect = np.full(cells, w[k])
+        expect[j] = 1.3 * w[k]
+        np.testing.assert_allclose(f1[k], expect, rtol=1e-15)
+
+
+def _directional(shift, n0=0, V=0.0, steps=300):
+    ny = 48
+    sc, _, _ = _liquid_box(3, ny, bc=(0, 1, 0), G=4e-3, V=V, v0=20.0)
+    p = sc["params"]
+    eps = p["eps"]
+    yc = p["v0"] + V * n0 + shift
+    y = np.arange(ny) + 0.5
+    half = math.pi ** 2 * eps / 8
+    prof = 0.5 * (1 - np.sin(4 * np.clip(y - yc, -half, half) / (math.pi * eps)))
+    s = np.repeat(prof, 3)
+    phi = np.stack([1 - s, s]).reshape(-1)
+    mu = np.zeros(3 * ny)
+    phi1, _, _ = oracle.run(sc, phi, mu, oracle.rest_populations(sc), steps, n0=n0)
+    s1 = phi1.reshape(2, ny, 3)[1, :, 1]
+    return _crossing(y, prof), _crossing(y, s1)
+
+
+def test_frozen_temperature_gradient_sets_the_front():
+    """T = T_E - u + G (v - v0 - V t): with mu = 0 the front is at rest where
+    T = T_E; above it the liquid is stable, so a front placed higher melts
+    back and one placed lower grows, and the rest position moves with V t."""
+    a, b = _directional(+3.0)
+    assert b < a - 0.02
+    a, b = _directional(-3.0)
+    assert b > a + 0.02
+    a, b = _directional(0.0, n0=4000, V=1e-3, steps=100)  # on the moving isotherm
+    assert abs(b - a) < 0.02
+    a, b = _directional(-4.0, n0=4000, V=1e-3, steps=100)  # at v0: 4 cells below it
+    assert b > a + 0.04
