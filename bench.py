@@ -1,0 +1,381 @@
+"""Benchmark of the coupled Grand-Potential phase-field / lattice-Boltzmann
+step on GB300.
+
+A step is one full time step (phase field, chemical potential, lattice
+Boltzmann) over the workload grid: by default the 2D binary eutectic under
+natural convection, 1024 x 512 cells, D2Q9, three phases, one solute, FP32.
+The state (2 x 52 MB) is smaller than L2, so L2 is flushed (256 MB write)
+before every timed step and each step is timed alone with CUDA events.
+
+Prints one JSON line (rank 0):
+  value       coupled-step MLUPS over all ranks (cells x steps / time)
+  e2e         the same through the public API with the state copied from
+              pinned host memory and phi, mu copied back every step
+  roofline    the dominant kernel (chemical potential + lattice Boltzmann)
+              against the measured HBM copy bandwidth
+  cpu_baseline the FP64 CPU oracle timed on the host cores on a sample
+  clocks      nvidia-smi samples taken during the timed region
+
+--impl reference times the FP64 CPU oracle on the same workload instead.
+Under torchrun every rank runs its own replica of the workload (the path has
+no data-path exchange on one GPU per replica; weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2608_26908_gb300 import inputs  # noqa: E402
+
+METRIC = "coupled-step MLUPS & % of HBM roofline; adjoint/forward time ratio"
+L2_FLUSH_BYTES = 256 << 20
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="eutectic2d", choices=list(inputs.WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp32_f16", "fp32_bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    sc = inputs.scenario(args.workload, precision=args.precision)
+    nx, ny, nz = inputs.dims(sc)
+    desc = "%s %s D%dQ%d N=%d K-1=%d %s" % (
+        args.workload, "x".join(str(n) for n in (nx, ny, nz) if n > 1),
+        3 if nz > 1 else 2, 19 if nz > 1 else 9, sc["n_phases"], sc["n_solutes"], sc["precision"])
+    return sc, desc
+
+
+def dtype_name(sc):
+    return {"fp64": "f64", "fp32": "f32", "fp32_f16": "f32 (f16 storage)",
+            "fp32_bf16": "f32 (bf16 storage)"}[sc["precision"]]
+
+
+def kernel_bytes_per_cell(sc):
+    """Algorithmic bytes per cell of each kernel and of the whole step."""
+    NP, NC = sc["n_phases"], sc["n_solutes"]
+    NS = 1 if NP == 2 else NP
+    Q = 19 if sc["grid"].get("nz", 1) > 1 else 9
+    r = 8 if sc["precision"] == "fp64" else 4
+    s = {"fp64": 8, "fp32": 4, "fp32_f16": 2, "fp32_bf16": 2}[sc["precision"]]
+    pf = (NS + NC + NS) * r                            # phi^n, mu^n -> phi^{n+1}
+    tr = (2 * NS + NC + NC) * r + 2 * Q * s            # phi^n, phi^{n+1}, mu^n, f^n -> mu, f
+    step = 2 * ((NS + NC) * r + Q * s)                 # state read once, written once
+    return pf, tr, step
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel, workload_name):
+    """DRAM bytes per launch from the committed ncu summary, if present."""
+    path = os.path.join(PROFILES, "%s_%s.md" % (kernel, workload_name))
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v == "null" else float(v)
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(sc, seconds):
+    """FP64 oracle MLUPS on the host cores on a bounded sample (the
+    workload's grid, as many steps as fit in about `seconds`)."""
+    from oracle import oracle
+
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    cells = inputs.cells(sc)
+    t0 = time.perf_counter()
+    phi, mu, f = oracle.run(sc, phi, mu, f, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(sc, phi, mu, f, steps, n0=1)
+    dt = time.perf_counter() - t0
+    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": "%d steps of the full %s grid (%d cells) after one step" % (
+                steps, sc["name"], cells)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reference_arm(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    from oracle import oracle
+
+    sc, desc = workload(args)
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    cells = inputs.cells(sc)
+    n = 0
+    for _ in range(args.warmup):
+        phi, mu, f = oracle.run(sc, phi, mu, f, 1, n0=n)
+        n += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        phi, mu, f = oracle.run(sc, phi, mu, f, 1, n0=n)
+        n += 1
+    dt = time.perf_counter() - t0
+    value = cells * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": desc, "cells": cells, "steps_per_iteration": 1},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.max_threads(),
+                         "kind": "oracle",
+                         "sample": "%d full-grid steps of %s" % (args.steps, sc["name"])},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def our_arm(args):
+    import numpy as np
+    import torch
+
+    from paper_2608_26908_gb300 import gpflbm
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    sc, desc = workload(args)
+    cells = inputs.cells(sc)
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    warm = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for e in warm:
+        e.record()  # materialise the event objects
+    for row in ev:
+        for e in row:
+            e.record()
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        flush.zero_()
+        sim.step_timed(warm)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            flush.zero_()
+            sim.step_timed(ev[i])
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    pf_ms = [row[0].elapsed_time(row[1]) for row in ev]
+    tr_ms = [row[1].elapsed_time(row[2]) for row in ev]
+    step_ms = [a + b for a, b in zip(pf_ms, tr_ms)]
+    total_s = sum(step_ms) / 1e3
+    if pg:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_s = float(t.item())
+    mass, solute, frac, st = sim.invariants(allow_nonfinite=True)
+    if st != gpflbm.OK:
+        raise RuntimeError("state is not finite after the timed steps")
+    value = world * cells * args.steps / total_s / 1e6
+
+    # end to end through the public API with pinned host buffers
+    NP, NC, Q = sc["n_phases"], sc["n_solutes"], sim.Q
+    tdt = sim.tdtype
+    h_phi = torch.empty(NP * cells, dtype=tdt, pin_memory=True)
+    h_mu = torch.empty(NC * cells, dtype=tdt, pin_memory=True)
+    h_f = torch.empty(Q * cells, dtype=tdt, pin_memory=True)
+    o_phi = torch.empty((NP, cells), dtype=tdt, pin_memory=True)
+    o_mu = torch.empty((NC, cells), dtype=tdt, pin_memory=True)
+    cur = sim.fields(("phi", "mu", "f"))
+    h_phi.numpy()[:] = cur["phi"].reshape(-1)
+    h_mu.numpy()[:] = cur["mu"].reshape(-1)
+    h_f.numpy()[:] = cur["f"].reshape(-1)
+    import ctypes
+    L = gpflbm.lib()
+    outs = (ctypes.c_void_p * 2)(o_phi.data_ptr(), o_mu.data_ptr())
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    t_now = sim.time()
+
+    def e2e_step():
+        st1 = L.gpflbm_set_state(sim.h, ctypes.c_void_p(h_phi.data_ptr()),
+                                 ctypes.c_void_p(h_mu.data_ptr()), ctypes.c_void_p(h_f.data_ptr()),
+                                 0, t_now, stream)
+        st2 = L.gpflbm_step(sim.h, 1, stream)
+        st3 = L.gpflbm_get_fields(sim.h, gpflbm.FIELD["phi"] | gpflbm.FIELD["mu"], outs, 0, stream)
+        if st1 or st2 or st3:
+            raise RuntimeError("e2e step failed: %s" % L.gpflbm_last_error(sim.h))
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if pg:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    esz = 8 if sc["precision"] == "fp64" else 4
+    e2e = {"value": world * cells * args.e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": (NP + NC + Q) * cells * esz,
+           "d2h_bytes_per_step": (NP + NC) * cells * esz,
+           "steps": args.e2e_steps,
+           "path": "gpflbm_set_state(pinned host) + gpflbm_step(1) + gpflbm_get_fields(pinned host)"}
+
+    if rank != 0:
+        pg.destroy_process_group() if pg else None
+        return 0
+    pf_b, tr_b, step_b = kernel_bytes_per_cell(sc)
+    peak, peak_kind = measured_peaks()
+    tr_avg_s = statistics.mean(tr_ms) / 1e3
+    pf_avg_s = statistics.mean(pf_ms) / 1e3
+    achieved = tr_b * cells / tr_avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic("mu_lbm_kernel", args.workload),
+                "kernel": "mu_lbm_kernel", "bytes_per_cell": tr_b,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else "fallback 6.8 TB/s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dtype_name(sc), "data": "synthetic",
+        "config": {"workload": desc, "cells": cells, "steps_per_iteration": 1,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas x%d" % world},
+        "hbm_roofline_frac_step": step_b * cells / (statistics.mean(step_ms) / 1e3) / 1e9 / peak,
+        "step_bytes_per_cell": step_b,
+        "kernels_ms": {"phase_field_kernel": statistics.mean(pf_ms),
+                       "mu_lbm_kernel": statistics.mean(tr_ms)},
+        "phase_field_roofline_frac": pf_b * cells / pf_avg_s / 1e9 / peak,
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks.summary(),
+        "invariants": {"mass": mass, "solute": list(solute), "solid_frac": frac},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * gpflbm.h -- C ABI of the GB300 (sm_103a) library for the coupled
+ * Grand-Potential phase-field / lattice-Boltzmann time step.
+ *
+ * One step advances the state S^n = {f_k (Q planes), phi_a (N planes),
+ * mu_i (K-1 planes)} to S^{n+1} in the order of the paper's Algorithm 1:
+ *   1. phase-field update, Eq. PhfGrand with the obstacle potential of
+ *      Eq. Wpot, a Lagrange multiplier over the locally present phases and
+ *      a Euclidean projection onto the Gibbs simplex (Sec. 2.1);
+ *   2. chemical-potential update, Eq. conc, in flux form: diffusion,
+ *      antitrapping, the c_a dh_a/dt source and advection by the lattice
+ *      Boltzmann velocity of step n (Sec. 2.1, Algorithm 1);
+ *   3. BGK collision with the second-order equilibrium (Eq. f^eq) and the
+ *      discrete force (Eq. discreteForce) made of the drag G_D and the
+ *      buoyancy G_B (Sec. 2.2), then streaming (Eq. LBMEq_1) with halfway
+ *      bounce-back on wall axes; density and momentum from Eq. rhovel with
+ *      the force-corrected velocity U = (m + F_B/2) / (rho (1 + kappa/2)).
+ *
+ * Conventions for every call:
+ *  - Fields are structure-of-arrays planes, x fastest:
+ *    index = x + nx * (y + ny * z); nz == 1 for 2D.  The vertical axis
+ *    (gravity along -v) is y in 2D and z in 3D.
+ *  - Element type of exchanged fields: double for GPFLBM_FP64, float for
+ *    every other precision.  Populations are always exchanged as the full
+ *    f_k (the library stores f_k - w_k internally).
+ *  - D2Q9 numbering is the paper's lattice figure: 0 rest, 1 (+x), 2 (+y),
+ *    3 (-x), 4 (-y), 5 (+x+y), 6 (-x+y), 7 (-x-y), 8 (+x-y).
+ *    D3Q19 numbering: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (+1,+1,0),
+ *    (-1,-1,0), (+1,-1,0), (-1,+1,0), (+1,0,+1), (-1,0,-1), (+1,0,-1),
+ *    (-1,0,+1), (0,+1,+1), (0,-1,-1), (0,+1,-1), (0,-1,+1).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered and asynchronous unless stated otherwise.
+ *  - Every call returns a gpflbm_status; nothing aborts.  After a failure
+ *    gpflbm_last_error(h) describes it.  A handle is not thread-safe.
+ */
+#ifndef GPFLBM_H
+#define GPFLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpflbm_s* gpflbm_t;
+
+typedef enum {
+  GPFLBM_OK = 0,
+  GPFLBM_ERR_ARG = -1,         /* invalid argument (pointer, size, enum, range) */
+  GPFLBM_ERR_OOM = -2,         /* workspace too small or device allocation failed */
+  GPFLBM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  GPFLBM_ERR_NONFINITE = -4,   /* NaN or Inf found in the state by gpflbm_invariants */
+  GPFLBM_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+  GPFLBM_ERR_STATE = -6,       /* call out of order (e.g. step before set_state) */
+  GPFLBM_ERR_UNSUPPORTED = -7  /* valid but not built: phase/solute count, lattice */
+} gpflbm_status;
+
+enum { GPFLBM_PERIODIC = 0, GPFLBM_WALL = 1 };
+enum { GPFLBM_D2Q9 = 9, GPFLBM_D3Q19 = 19 };
+enum {
+  GPFLBM_FP64 = 0,           /* FP64 arithmetic and storage */
+  GPFLBM_FP32 = 1,           /* FP32 arithmetic and storage */
+  GPFLBM_FP32_F16STORE = 2,  /* FP32 arithmetic, f_k - w_k stored as FP16 times 2^10 */
+  GPFLBM_FP32_BF16STORE = 3  /* FP32 arithmetic, f_k - w_k stored as BF16 */
+};
+enum {
+  GPFLBM_FIELD_PHI = 1,  /* N planes, liquid (phase 0) first */
+  GPFLBM_FIELD_MU = 2,   /* K-1 planes */
+  GPFLBM_FIELD_C = 4,    /* K-1 planes: c_i = sum_a h_a(phi) c_a,i(mu) */
+  GPFLBM_FIELD_F = 8,    /* Q planes, full populations f_k */
+  GPFLBM_FIELD_RHO = 16, /* 1 plane: sum_k f_k */
+  GPFLBM_FIELD_U = 32    /* d planes: force-corrected velocity of the current state */
+};
+
+#define GPFLBM_MAX_PHASES 4
+#define GPFLBM_MAX_SOLUTES 2
+
+/* Grid and storage.  bc[a]: GPFLBM_PERIODIC or GPFLBM_WALL per axis
+ * (WALL = zero-flux for phi and mu, halfway bounce-back for f).
+ * wall_rows[a]: static obstacle rows at both ends of axis a: phi and mu are
+ * frozen there, no solute crosses their faces, and the flow sees them as
+ * solid (drag with phi_l = 0, no buoyancy). */
+typedef struct {
+  int nx, ny, nz;    /* cells per axis; nz == 1 selects 2D */
+  int lattice;       /* GPFLBM_D2Q9 (2D) or GPFLBM_D3Q19 (3D) */
+  int bc[3];
+  int wall_rows[3];
+  int precision;     /* GPFLBM_FP64 ... GPFLBM_FP32_BF16STORE */
+} gpflbm_grid;
+
+/* Material and model parameters, lattice units (dx = dt = 1).  Phase 0 is
+ * the liquid.  Entries beyond n_phases / n_components are ignored. */
+typedef struct {
+  double tau_f;                    /* BGK relaxation time, nu = (tau_f - 1/2) / 3 */
+  double tau_phi;                  /* tau of Eq. PhfGrand (interface mobility = 1/tau_phi) */
+  double eps;                      /* interface width parameter epsilon, cells */
+  double gamma[4][4];              /* interface energy per pair (symmetric, zero diagonal) */
+  double delta[4][4];              /* cubic anisotropy strength per pair (0 = isotropic) */
+  double A[4];                     /* parabolic free energy f_a(c) = A_a |c - ceq_a|^2 */
+  double ceq[4][2];                /* equilibrium composition per phase and solute */
+  double S[4];                     /* psi_a gains S_a (T - T_E); S_0 = 0 for the liquid */
+  double D_liq;                    /* liquid diffusivity; mobility M = D_liq phi_l / (2 A_0) */
+  double a_at;                     /* antitrapping coefficient (0 = off) */
+  double h_drag, W0;               /* drag G_D = -rho kappa U, kappa = 2 nu h (1-phi_l)^2 / W0^2 */
+  double gbeta_c[2], c_ref[2];     /* solutal buoyancy g beta_i (c_l,i - c_ref,i), upward */
+  double gbeta_T, T_ref;           /* thermal buoyancy g beta_T (T - T_ref), upward */
+  double T_E, undercool, G, V, v0; /* T(v, t) = T_E - undercool + G (v - v0 - V t) */
+  double q_floor;                  /* |q|^2 at or below which the anisotropy is dropped */
+} gpflbm_params;
+
+/* Device bytes the library needs for a problem (state ping-pong buffers,
+ * reduction partials, step counter), for a caller that provides the memory.
+ * Returns GPFLBM_ERR_ARG / GPFLBM_ERR_UNSUPPORTED for an invalid or unbuilt
+ * configuration.  Does not touch the GPU. */
+gpflbm_status gpflbm_workspace_bytes(const gpflbm_grid* grid, int n_phases, int n_components,
+                                     size_t* bytes);
+
+/* Create a simulation handle.  n_phases = N (2..4, phase 0 liquid),
+ * n_components = K-1 independent solutes (1..2).  `workspace` is device
+ * memory of at least gpflbm_workspace_bytes() bytes, 256-byte aligned, owned
+ * by the caller and kept alive (and untouched) until gpflbm_destroy; pass
+ * NULL to let the library allocate (and later free) it with cudaMalloc.
+ * The state is undefined until gpflbm_set_state.  On failure *out is NULL. */
+gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_components,
+                            const gpflbm_params* params, void* workspace, size_t workspace_bytes,
+                            gpflbm_t* out);
+
+/* Replace the model parameters (same grid, phase and solute counts). */
+gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params);
+
+/* Load S^n.  phi: N planes (liquid first); mu: K-1 planes; f: Q planes of
+ * full populations, or NULL for the fluid at rest (f_k = w_k).
+ * src_is_device: 1 if the pointers are device memory, 0 for host memory
+ * (pageable or pinned).  The library copies; the caller keeps ownership.
+ * Sets the step counter to t0.  Host sources are read before return. */
+gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, const void* f,
+                               int src_is_device, long long t0, void* stream);
+
+/* Advance n_steps >= 0 steps on `stream` (asynchronous).  Steps are
+ * replayed from a CUDA graph captured on first use. */
+gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream);
+
+/* One step launched directly (not from a graph) that records three caller
+ * CUDA events (cudaEvent_t) on `stream`: events[0] before the phase-field
+ * kernel, events[1] between it and the chemical-potential + lattice-
+ * Boltzmann kernel, events[2] after it, for per-kernel timing with
+ * cudaEventElapsedTime.  Same result as gpflbm_step(h, 1, stream). */
+gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream);
+
+/* Copy fields of the current state out.  field_mask is an OR of
+ * GPFLBM_FIELD_*; dst holds one pointer per set bit, in increasing bit
+ * order, each large enough for that field's planes.  dst_is_device as in
+ * set_state.  For host destinations the call synchronises `stream`. */
+gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* dst,
+                                int dst_is_device, void* stream);
+
+/* Stored population deviations f_k - w_k of the current state, as Q planes
+ * of the exchange type (float or double), for checks of the storage codec. */
+gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, void* stream);
+
+/* Global totals in FP64, by a fixed-order reduction (identical from run to
+ * run): mass = sum_x sum_k (f_k - w_k) + cells, solute[i] = sum_x c_i,
+ * solid_frac = (1/cells) sum_x sum_{a>0} h_a.  Per cell, values are widened
+ * to FP64 first and combined without fused multiply-add.  Order: 256-thread
+ * blocks, grid G = min(ceil(cells/256), 608); thread t of block b adds the
+ * cells b*256 + t + j*G*256 (j = 0, 1, ...) in turn; a warp combines by
+ * xor-butterfly (offsets 16, 8, 4, 2, 1); lane 0 of warps 0..7 are then
+ * added in order; the G block sums are added in order.  Synchronises
+ * `stream`.  Returns GPFLBM_ERR_NONFINITE (totals still written) if any
+ * cell of the state is NaN or Inf.  Any output pointer may be NULL. */
+gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double* solid_frac,
+                                void* stream);
+
+/* Step counter of the current state (the t of T(v, t)). */
+gpflbm_status gpflbm_time(gpflbm_t h, long long* t);
+
+/* Human-readable description of the last failure on h ("" if none). */
+const char* gpflbm_last_error(gpflbm_t h);
+
+/* Release the handle (and the workspace if the library allocated it). */
+void gpflbm_destroy(gpflbm_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPFLBM_H */

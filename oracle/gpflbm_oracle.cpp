@@ -530,7 +530,9 @@ void phase_field_update(const Grid& g, const Coeffs<R>& k, const State<R>& s, do
 
 // Step 2 of Algorithm 1: chemical-potential update (Eq. conc) in flux form:
 // diffusion M grad mu with M = D_liq phi_l / (2 A_l) at phi^{n+1} [R12],
-// antitrapping [R13], advection of h_l c_l U with U^n [R14], the source
+// antitrapping [R13] -a_at eps sum_{a>0} [phi_l]_f [c_l - c_a]_f [dphi_a]_f
+// n_a.e_d (weighted by the liquid on the face: it corrects solute trapping
+// at solid-liquid interfaces only), advection of h_l c_l U with U^n [R14], the source
 // -sum_a c_a (h_a^{n+1} - h_a^n), all divided by chi(phi^{n+1}).
 template <class R>
 void chemical_potential_update(const Grid& g, const State<R>& s, const std::vector<R>& phi_new,
@@ -582,7 +584,8 @@ void chemical_potential_update(const Grid& g, const State<R>& s, const std::vect
                           (c_phase(p, 0, i, mub) - c_phase(p, a, i, mub)));
             R dphi = 0.5 * ((phi_new[a * cells + x] - s.phi[a * cells + x]) +
                             (phi_new[a * cells + y] - s.phi[a * cells + y]));
-            at += dc * dphi * gr[d] / sqrt(g2);
+            R liq = 0.5 * (s.phi[0 * cells + x] + s.phi[0 * cells + y]);
+            at += liq * dc * dphi * gr[d] / sqrt(g2);
           }
           J -= p->a_at * p->eps * at;
         }

@@ -1,0 +1,569 @@
+// C-ABI of the coupled Grand-Potential phase-field / lattice-Boltzmann step
+// (declared and documented in include/gpflbm.h).  Host logic only: argument
+// checks, workspace layout, parameter preparation, CUDA-graph replay of the
+// step, and dispatch to the kernel table of the problem's configuration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gpflbm.h"
+#include "gpflbm_ops.cuh"
+
+using gpflbm::DevParams;
+using gpflbm::Ops;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kChunk = 16;  // steps per replayed CUDA graph
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  size_t phi[2], mu[2], f[2], stage, clock, partial, red;
+  size_t total;
+};
+
+}  // namespace
+
+struct gpflbm_s {
+  gpflbm_grid grid;
+  gpflbm_params params;
+  int NP, NC, Q, D;
+  long long cells, plane;
+  const Ops* ops;
+  Layout lay;
+  unsigned char* ws;
+  bool owns_ws;
+  int cur;            // buffer holding the current state
+  long long t;        // step counter of the current state
+  bool has_state;
+  cudaStream_t capture;
+  cudaGraphExec_t chunk_graph[2];
+  cudaGraphExec_t pair_graph[2];
+  // device parameters in the arithmetic type (only one is used)
+  DevParams<double> pd;
+  DevParams<float> pf;
+  gpflbm::InvParams inv;
+  std::string err;
+};
+
+namespace {
+
+gpflbm_status fail(gpflbm_t h, gpflbm_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+gpflbm_status cuda_fail(gpflbm_t h, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(h, GPFLBM_ERR_CUDA, m);
+}
+
+const Ops* find_ops(int D, int precision, int NP, int NC) {
+  using namespace gpflbm;
+  if (D == 2) {
+    switch (precision) {
+      case GPFLBM_FP64: return ops_d2_fp64(NP, NC);
+      case GPFLBM_FP32: return ops_d2_fp32(NP, NC);
+      case GPFLBM_FP32_F16STORE: return ops_d2_f16(NP, NC);
+      case GPFLBM_FP32_BF16STORE: return ops_d2_bf16(NP, NC);
+    }
+  } else {
+    switch (precision) {
+      case GPFLBM_FP64: return ops_d3_fp64(NP, NC);
+      case GPFLBM_FP32: return ops_d3_fp32(NP, NC);
+      case GPFLBM_FP32_F16STORE: return ops_d3_f16(NP, NC);
+      case GPFLBM_FP32_BF16STORE: return ops_d3_bf16(NP, NC);
+    }
+  }
+  return nullptr;
+}
+
+// Validates the grid; fills D and the kernel table.
+gpflbm_status check_grid(const gpflbm_grid* g, int NP, int NC, int* D, const Ops** ops,
+                         std::string* why) {
+  if (!g) {
+    *why = "grid is NULL";
+    return GPFLBM_ERR_ARG;
+  }
+  if (g->nx < 3 || g->ny < 3 || g->nz < 1 || (g->nz > 1 && g->nz < 3)) {
+    *why = "grid needs nx, ny >= 3 and nz == 1 or nz >= 3";
+    return GPFLBM_ERR_ARG;
+  }
+  const long long cells = (long long)g->nx * g->ny * g->nz;
+  if (cells > (1LL << 31) - 1024) {
+    *why = "grid has more than 2^31 cells";
+    return GPFLBM_ERR_ARG;
+  }
+  *D = g->nz == 1 ? 2 : 3;
+  if ((*D == 2 && g->lattice != GPFLBM_D2Q9) || (*D == 3 && g->lattice != GPFLBM_D3Q19)) {
+    *why = "lattice must be D2Q9 for nz == 1 and D3Q19 otherwise";
+    return GPFLBM_ERR_UNSUPPORTED;
+  }
+  for (int a = 0; a < 3; ++a) {
+    if (g->bc[a] != GPFLBM_PERIODIC && g->bc[a] != GPFLBM_WALL) {
+      *why = "bc must be GPFLBM_PERIODIC or GPFLBM_WALL";
+      return GPFLBM_ERR_ARG;
+    }
+    const int n = a == 0 ? g->nx : (a == 1 ? g->ny : g->nz);
+    if (g->wall_rows[a] < 0 || (a < *D && 2 * g->wall_rows[a] >= n) || (a >= *D && g->wall_rows[a] != 0)) {
+      *why = "wall_rows out of range";
+      return GPFLBM_ERR_ARG;
+    }
+  }
+  if (g->precision < GPFLBM_FP64 || g->precision > GPFLBM_FP32_BF16STORE) {
+    *why = "unknown precision";
+    return GPFLBM_ERR_ARG;
+  }
+  if (NP < 2 || NP > GPFLBM_MAX_PHASES || NC < 1 || NC > GPFLBM_MAX_SOLUTES) {
+    *why = "n_phases must be 2..4 and n_components 1..2";
+    return GPFLBM_ERR_UNSUPPORTED;
+  }
+  *ops = find_ops(*D, g->precision, NP, NC);
+  if (!*ops) {
+    *why = "configuration not built";
+    return GPFLBM_ERR_UNSUPPORTED;
+  }
+  return GPFLBM_OK;
+}
+
+Layout make_layout(const Ops* ops, long long cells, long long plane) {
+  (void)cells;
+  Layout L;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = round_up(off + bytes, kAlign);
+    return at;
+  };
+  for (int i = 0; i < 2; ++i) L.phi[i] = take(ops->stored_phi_planes * plane * ops->real_size);
+  for (int i = 0; i < 2; ++i) L.mu[i] = take(ops->NC * plane * ops->real_size);
+  for (int i = 0; i < 2; ++i) L.f[i] = take(ops->Q * plane * ops->store_size);
+  L.stage = take(ops->Q * plane * ops->real_size);
+  L.clock = take(2 * sizeof(double));
+  L.partial = take(gpflbm::kRedMaxBlocks * (ops->NC + 3) * sizeof(double));
+  L.red = take((ops->NC + 3) * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+template <class Real>
+void fill_params(gpflbm_t h, DevParams<Real>& P) {
+  const gpflbm_params& p = h->params;
+  std::memset(&P, 0, sizeof(P));
+  P.n[0] = h->grid.nx;
+  P.n[1] = h->grid.ny;
+  P.n[2] = h->D == 3 ? h->grid.nz : 1;
+  for (int a = 0; a < 3; ++a) {
+    P.bc[a] = a < h->D ? h->grid.bc[a] : GPFLBM_PERIODIC;
+    P.wall[a] = a < h->D ? h->grid.wall_rows[a] : 0;
+  }
+  P.plane = h->plane;
+  P.eps = (Real)p.eps;
+  P.mob_eps = (Real)(1.0 / (p.tau_phi * p.eps));
+  P.obst = (Real)(16.0 / (kPi * kPi * p.eps));
+  for (int a = 0; a < 4; ++a) {
+    for (int b = 0; b < 4; ++b) {
+      P.gamma[a][b] = (Real)p.gamma[a][b];
+      P.delta[a][b] = (Real)p.delta[a][b];
+    }
+    P.inv2A[a] = (Real)(1.0 / (2.0 * p.A[a]));
+    P.inv4A[a] = (Real)(1.0 / (4.0 * p.A[a]));
+    for (int i = 0; i < 2; ++i) P.ceq[a][i] = (Real)p.ceq[a][i];
+    P.S[a] = (Real)p.S[a];
+  }
+  for (int i = 0; i < 2; ++i) P.dcl_ref[i] = (Real)(p.ceq[0][i] - p.c_ref[i]);
+  P.M0 = (Real)(p.D_liq / (2.0 * p.A[0]));
+  P.at_eps = (Real)(p.a_at * p.eps);
+  const double nu = (p.tau_f - 0.5) / 3.0;
+  P.kappa0 = (Real)(2.0 * nu * p.h_drag / (p.W0 * p.W0));
+  for (int i = 0; i < 2; ++i) P.gbeta_c[i] = (Real)p.gbeta_c[i];
+  P.gbeta_T = (Real)p.gbeta_T;
+  P.dT_ref = (Real)(p.T_E - p.T_ref);
+  P.G = (Real)p.G;
+  P.inv_tau_f = (Real)(1.0 / p.tau_f);
+  P.force_pre = (Real)(1.0 - 0.5 / p.tau_f);
+  P.q_floor = (Real)p.q_floor;
+  P.theta0 = -p.undercool - p.G * p.v0;
+  P.GV = p.G * p.V;
+}
+
+gpflbm_status check_params(const gpflbm_params* p, int NP, std::string* why) {
+  if (!p) {
+    *why = "params is NULL";
+    return GPFLBM_ERR_ARG;
+  }
+  if (!(p->tau_f > 0.5) || !(p->tau_phi > 0.0) || !(p->eps > 0.0) || !(p->W0 > 0.0)) {
+    *why = "need tau_f > 1/2, tau_phi > 0, eps > 0, W0 > 0";
+    return GPFLBM_ERR_ARG;
+  }
+  for (int a = 0; a < NP; ++a)
+    if (!(p->A[a] > 0.0)) {
+      *why = "need A_a > 0 for every phase";
+      return GPFLBM_ERR_ARG;
+    }
+  if (!(p->D_liq >= 0.0) || !(p->q_floor >= 0.0)) {
+    *why = "need D_liq >= 0 and q_floor >= 0";
+    return GPFLBM_ERR_ARG;
+  }
+  return GPFLBM_OK;
+}
+
+void set_device_params(gpflbm_t h) {
+  fill_params(h, h->pd);
+  fill_params(h, h->pf);
+  h->inv.cells = h->cells;
+  h->inv.plane = h->plane;
+  for (int a = 0; a < 4; ++a) {
+    for (int i = 0; i < 2; ++i) h->inv.ceq[a][i] = h->params.ceq[a][i];
+    h->inv.inv2A[a] = 1.0 / (2.0 * h->params.A[a]);
+  }
+}
+
+const void* dev_params(gpflbm_t h) {
+  return h->grid.precision == GPFLBM_FP64 ? (const void*)&h->pd : (const void*)&h->pf;
+}
+
+void* at(gpflbm_t h, size_t off) { return h->ws + off; }
+
+gpflbm::StepIO step_io(gpflbm_t h, int from) {
+  gpflbm::StepIO io;
+  io.phi_in = at(h, h->lay.phi[from]);
+  io.phi_out = at(h, h->lay.phi[1 - from]);
+  io.mu_in = at(h, h->lay.mu[from]);
+  io.mu_out = at(h, h->lay.mu[1 - from]);
+  io.f_in = at(h, h->lay.f[from]);
+  io.f_out = at(h, h->lay.f[1 - from]);
+  io.clock_in = reinterpret_cast<const double*>(at(h, h->lay.clock)) + from;
+  io.clock_out = reinterpret_cast<double*>(at(h, h->lay.clock)) + 1 - from;
+  return io;
+}
+
+void drop_graphs(gpflbm_t h) {
+  for (int i = 0; i < 2; ++i) {
+    if (h->chunk_graph[i]) cudaGraphExecDestroy(h->chunk_graph[i]);
+    if (h->pair_graph[i]) cudaGraphExecDestroy(h->pair_graph[i]);
+    h->chunk_graph[i] = h->pair_graph[i] = nullptr;
+  }
+}
+
+// Captures `steps` consecutive steps starting from buffer `from`.
+gpflbm_status capture(gpflbm_t h, int from, int steps, cudaGraphExec_t* out) {
+  cudaError_t e = cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+  int b = from;
+  cudaError_t le = cudaSuccess;
+  for (int s = 0; s < steps; ++s) {
+    le = h->ops->step(dev_params(h), step_io(h, b), h->capture);
+    if (le != cudaSuccess) break;
+    b = 1 - b;
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(h->capture, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(h, le, "step launch during capture");
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  return GPFLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpflbm_status gpflbm_workspace_bytes(const gpflbm_grid* grid, int n_phases, int n_components,
+                                     size_t* bytes) {
+  int D;
+  const Ops* ops;
+  std::string why;
+  if (!bytes) return GPFLBM_ERR_ARG;
+  gpflbm_status st = check_grid(grid, n_phases, n_components, &D, &ops, &why);
+  if (st != GPFLBM_OK) return st;
+  const long long cells = (long long)grid->nx * grid->ny * grid->nz;
+  *bytes = make_layout(ops, cells, (long long)round_up(cells, 64)).total;
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_components,
+                            const gpflbm_params* params, void* workspace, size_t workspace_bytes,
+                            gpflbm_t* out) {
+  if (!out) return GPFLBM_ERR_ARG;
+  *out = nullptr;
+  int D;
+  const Ops* ops;
+  std::string why;
+  gpflbm_status st = check_grid(grid, n_phases, n_components, &D, &ops, &why);
+  if (st != GPFLBM_OK) {
+    std::fprintf(stderr, "gpflbm_create: %s\n", why.c_str());
+    return st;
+  }
+  st = check_params(params, n_phases, &why);
+  if (st != GPFLBM_OK) {
+    std::fprintf(stderr, "gpflbm_create: %s\n", why.c_str());
+    return st;
+  }
+  gpflbm_t h = new (std::nothrow) gpflbm_s();
+  if (!h) return GPFLBM_ERR_OOM;
+  h->grid = *grid;
+  h->params = *params;
+  h->NP = n_phases;
+  h->NC = n_components;
+  h->D = D;
+  h->Q = ops->Q;
+  h->ops = ops;
+  h->cells = (long long)grid->nx * grid->ny * grid->nz;
+  h->plane = (long long)round_up(h->cells, 64);
+  h->lay = make_layout(ops, h->cells, h->plane);
+  h->cur = 0;
+  h->t = 0;
+  h->has_state = false;
+  if (workspace) {
+    if (workspace_bytes < h->lay.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) {
+      delete h;
+      std::fprintf(stderr, "gpflbm_create: workspace too small or not 256-byte aligned\n");
+      return workspace_bytes < h->lay.total ? GPFLBM_ERR_OOM : GPFLBM_ERR_ARG;
+    }
+    h->ws = static_cast<unsigned char*>(workspace);
+    h->owns_ws = false;
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, h->lay.total);
+    if (e != cudaSuccess) {
+      delete h;
+      return GPFLBM_ERR_OOM;
+    }
+    h->ws = static_cast<unsigned char*>(p);
+    h->owns_ws = true;
+  }
+  cudaError_t e = h->ops->configure();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "gpflbm_create: %s\n", cudaGetErrorString(e));
+    if (h->owns_ws) cudaFree(h->ws);
+    delete h;
+    return GPFLBM_ERR_CUDA;
+  }
+  set_device_params(h);
+  *out = h;
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params) {
+  if (!h) return GPFLBM_ERR_ARG;
+  std::string why;
+  gpflbm_status st = check_params(params, h->NP, &why);
+  if (st != GPFLBM_OK) return fail(h, st, why);
+  h->params = *params;
+  set_device_params(h);
+  drop_graphs(h);  // parameters are baked into captured launches
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, const void* f,
+                               int src_is_device, long long t0, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  if (!phi || !mu) return fail(h, GPFLBM_ERR_ARG, "set_state: phi and mu are required");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t rs = h->ops->real_size;
+  const size_t n = (size_t)h->cells;
+  const void* sp = phi;
+  const void* sm = mu;
+  const void* sf = f;
+  void* phi_d = at(h, h->lay.phi[h->cur]);
+  void* mu_d = at(h, h->lay.mu[h->cur]);
+  void* f_d = at(h, h->lay.f[h->cur]);
+  cudaError_t e;
+  if (!src_is_device) {
+    // stage through the idle buffers: phi in the stage area, mu in the idle
+    // mu buffer, f in the stage area after phi has been converted
+    unsigned char* stage = static_cast<unsigned char*>(at(h, h->lay.stage));
+    e = cudaMemcpyAsync(stage, phi, h->NP * n * rs, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: copy phi");
+    e = h->ops->load(dev_params(h), stage, nullptr, nullptr, phi_d, mu_d, f_d, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load phi");
+    e = cudaMemcpyAsync(stage, mu, h->NC * n * rs, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: copy mu");
+    e = h->ops->load(dev_params(h), nullptr, stage, nullptr, phi_d, mu_d, f_d, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load mu");
+    sp = sm = nullptr;
+    if (f) {
+      e = cudaMemcpyAsync(stage, f, h->Q * n * rs, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "set_state: copy f");
+      sf = stage;
+    }
+  }
+  // (the load launcher always rewrites f: from sf, or the fluid at rest)
+  e = h->ops->load(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
+  double tt[2] = {(double)t0, (double)t0};
+  e = cudaMemcpyAsync(at(h, h->lay.clock), tt, sizeof(tt), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: clock");
+  e = cudaStreamSynchronize(s);  // host sources (and tt) must outlive the copies
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: synchronize");
+  h->t = t0;
+  h->has_state = true;
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  if (n_steps < 0) return fail(h, GPFLBM_ERR_ARG, "step: n_steps < 0");
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "step: no state loaded");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int left = n_steps;
+  while (left > 0) {
+    cudaError_t e;
+    if (left >= kChunk) {
+      if (!h->chunk_graph[h->cur]) {
+        gpflbm_status st = capture(h, h->cur, kChunk, &h->chunk_graph[h->cur]);
+        if (st != GPFLBM_OK) return st;
+      }
+      e = cudaGraphLaunch(h->chunk_graph[h->cur], s);
+      left -= kChunk;  // even: the state returns to the same buffer
+    } else if (left >= 2) {
+      if (!h->pair_graph[h->cur]) {
+        gpflbm_status st = capture(h, h->cur, 2, &h->pair_graph[h->cur]);
+        if (st != GPFLBM_OK) return st;
+      }
+      e = cudaGraphLaunch(h->pair_graph[h->cur], s);
+      left -= 2;
+    } else {
+      e = h->ops->step(dev_params(h), step_io(h, h->cur), s);
+      h->cur = 1 - h->cur;
+      left -= 1;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+  }
+  h->t += n_steps;
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream) {
+  if (!h || !events || !events[0] || !events[1] || !events[2])
+    return fail(h, GPFLBM_ERR_ARG, "step_timed: three events are required");
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "step_timed: no state loaded");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const gpflbm::StepIO io = step_io(h, h->cur);
+  cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(events[0]), s);
+  if (e == cudaSuccess) e = h->ops->step_pf(dev_params(h), io, s);
+  if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(events[1]), s);
+  if (e == cudaSuccess) e = h->ops->step_transport(dev_params(h), io, s);
+  if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(events[2]), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "step_timed");
+  h->cur = 1 - h->cur;
+  h->t += 1;
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* dst,
+                                int dst_is_device, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "get_fields: no state loaded");
+  if (field_mask & ~63u) return fail(h, GPFLBM_ERR_ARG, "get_fields: unknown field bit");
+  if (field_mask && !dst) return fail(h, GPFLBM_ERR_ARG, "get_fields: dst is NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t rs = h->ops->real_size;
+  const size_t n = (size_t)h->cells;
+  const int planes[6] = {h->NP, h->NC, h->NC, h->Q, 1, h->D};
+  int slot = 0;
+  for (int bit = 0; bit < 6; ++bit) {
+    if (!(field_mask & (1u << bit))) continue;
+    void* d = dst[slot++];
+    if (!d) return fail(h, GPFLBM_ERR_ARG, "get_fields: a destination is NULL");
+    void* target = dst_is_device ? d : at(h, h->lay.stage);
+    gpflbm::FieldsIO io;
+    std::memset(&io, 0, sizeof(io));
+    io.phi = at(h, h->lay.phi[h->cur]);
+    io.mu = at(h, h->lay.mu[h->cur]);
+    io.f = at(h, h->lay.f[h->cur]);
+    io.clock = reinterpret_cast<const double*>(at(h, h->lay.clock)) + h->cur;
+    void** outs[6] = {&io.o_phi, &io.o_mu, &io.o_c, &io.o_f, &io.o_rho, &io.o_u};
+    *outs[bit] = target;
+    cudaError_t e = h->ops->fields(dev_params(h), io, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: kernel");
+    if (!dst_is_device) {
+      e = cudaMemcpyAsync(d, target, planes[bit] * n * rs, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: copy");
+      e = cudaStreamSynchronize(s);  // the stage area is reused by the next field
+      if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: synchronize");
+    }
+  }
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, void* stream) {
+  if (!h || !dst) return GPFLBM_ERR_ARG;
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "get_deviations: no state loaded");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* target = dst_is_device ? dst : at(h, h->lay.stage);
+  gpflbm::FieldsIO io;
+  std::memset(&io, 0, sizeof(io));
+  io.phi = at(h, h->lay.phi[h->cur]);
+  io.mu = at(h, h->lay.mu[h->cur]);
+  io.f = at(h, h->lay.f[h->cur]);
+  io.clock = reinterpret_cast<const double*>(at(h, h->lay.clock)) + h->cur;
+  io.o_dev = target;
+  cudaError_t e = h->ops->fields(dev_params(h), io, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_deviations: kernel");
+  if (!dst_is_device) {
+    e = cudaMemcpyAsync(dst, target, h->Q * (size_t)h->cells * h->ops->real_size,
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_deviations: copy");
+  }
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double* solid_frac,
+                                void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "invariants: no state loaded");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long want = (h->cells + gpflbm::kRedThreads - 1) / gpflbm::kRedThreads;
+  const int blocks = (int)(want < gpflbm::kRedMaxBlocks ? want : gpflbm::kRedMaxBlocks);
+  double* partial = reinterpret_cast<double*>(at(h, h->lay.partial));
+  double* red = reinterpret_cast<double*>(at(h, h->lay.red));
+  cudaError_t e = h->ops->invariants(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
+                                     at(h, h->lay.f[h->cur]), partial, blocks, red, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "invariants: kernel");
+  double out[GPFLBM_MAX_SOLUTES + 3];
+  e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "invariants: copy");
+  if (mass) *mass = out[0] + (double)h->cells;
+  if (solute)
+    for (int i = 0; i < h->NC; ++i) solute[i] = out[1 + i];
+  if (solid_frac) *solid_frac = out[h->NC + 1] / (double)h->cells;
+  if (out[h->NC + 2] != 0.0)
+    return fail(h, GPFLBM_ERR_NONFINITE, "invariants: NaN or Inf in the state");
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_time(gpflbm_t h, long long* t) {
+  if (!h || !t) return GPFLBM_ERR_ARG;
+  *t = h->t;
+  return GPFLBM_OK;
+}
+
+const char* gpflbm_last_error(gpflbm_t h) { return h ? h->err.c_str() : "null handle"; }
+
+void gpflbm_destroy(gpflbm_t h) {
+  if (!h) return;
+  drop_graphs(h);
+  if (h->capture) cudaStreamDestroy(h->capture);
+  if (h->owns_ws) cudaFree(h->ws);
+  delete h;
+}
+
+}  // extern "C"

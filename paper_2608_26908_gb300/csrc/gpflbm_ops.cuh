@@ -1,0 +1,180 @@
+// Launchers of the device kernels for one (dimension, phases, solutes,
+// arithmetic type, storage type) combination, gathered in a table of plain
+// function pointers so that the C-ABI layer dispatches at run time.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "gpflbm_kernels.cuh"
+
+namespace gpflbm {
+
+struct StepIO {
+  const void* phi_in;
+  void* phi_out;
+  const void* mu_in;
+  void* mu_out;
+  const void* f_in;
+  void* f_out;
+  const double* clock_in;
+  double* clock_out;
+};
+
+struct FieldsIO {
+  const void* phi;
+  const void* mu;
+  const void* f;
+  const double* clock;
+  void* o_phi;
+  void* o_mu;
+  void* o_c;
+  void* o_f;
+  void* o_rho;
+  void* o_u;
+  void* o_dev;
+};
+
+struct Ops {
+  int D, NP, NC, Q;
+  size_t real_size, store_size;
+  int stored_phi_planes;
+  // opts the step kernels in to their dynamic shared memory (once per process)
+  cudaError_t (*configure)();
+  // one time step S^n -> S^{n+1}
+  cudaError_t (*step)(const void* params, const StepIO& io, cudaStream_t s);
+  // its two launches separately: phase field, then chemical potential + LBM
+  cudaError_t (*step_pf)(const void* params, const StepIO& io, cudaStream_t s);
+  cudaError_t (*step_transport)(const void* params, const StepIO& io, cudaStream_t s);
+  // exchange planes (Real) -> stored state; src_f may be null (rest)
+  cudaError_t (*load)(const void* params, const void* src_phi, const void* src_mu,
+                      const void* src_f, void* phi, void* mu, void* f, cudaStream_t s);
+  cudaError_t (*fields)(const void* params, const FieldsIO& io, cudaStream_t s);
+  cudaError_t (*invariants)(const InvParams& p, const void* phi, const void* mu, const void* f,
+                            double* partial, int blocks, double* out, cudaStream_t s);
+};
+
+template <class K>
+inline cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int D, int NP, int NC, class Real, class Store>
+struct Impl {
+  using G = Geo<D, Real>;
+  static constexpr int Q = D == 2 ? 9 : 19;
+
+  static dim3 tiles(const DevParams<Real>& P) {
+    return dim3((P.n[0] + G::TX - 1) / G::TX, (P.n[1] + G::TY - 1) / G::TY,
+                (P.n[2] + G::TZ - 1) / G::TZ);
+  }
+
+  static cudaError_t configure() {
+    cudaError_t e = allow_smem(phase_field_kernel<D, NP, NC, Real>, PfSmem<D, NP, Real>::bytes);
+    if (e == cudaSuccess)
+      e = allow_smem(mu_lbm_kernel<D, NP, NC, Real, Store>, MlSmem<D, NP, NC, Real>::bytes);
+    return e;
+  }
+
+  static cudaError_t step_pf(const void* params, const StepIO& io, cudaStream_t s) {
+    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+    phase_field_kernel<D, NP, NC, Real><<<tiles(P), G::NT, PfSmem<D, NP, Real>::bytes, s>>>(
+        P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.mu_in),
+        static_cast<Real*>(io.phi_out), io.clock_in);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t step_transport(const void* params, const StepIO& io, cudaStream_t s) {
+    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+    mu_lbm_kernel<D, NP, NC, Real, Store><<<tiles(P), G::NT, MlSmem<D, NP, NC, Real>::bytes, s>>>(
+        P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.phi_out),
+        static_cast<const Real*>(io.mu_in), static_cast<const Store*>(io.f_in),
+        static_cast<Real*>(io.mu_out), static_cast<Store*>(io.f_out), io.clock_in, io.clock_out);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t step(const void* params, const StepIO& io, cudaStream_t s) {
+    cudaError_t e = step_pf(params, io, s);
+    return e == cudaSuccess ? step_transport(params, io, s) : e;
+  }
+
+  static cudaError_t load(const void* params, const void* src_phi, const void* src_mu,
+                          const void* src_f, void* phi, void* mu, void* f, cudaStream_t s) {
+    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+    const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((cells + threads - 1) / threads);
+    if (src_phi)
+      load_phi_kernel<NP, Real, Real><<<blocks, threads, 0, s>>>(
+          cells, P.plane, static_cast<const Real*>(src_phi), static_cast<Real*>(phi));
+    if (src_mu)
+      load_mu_kernel<NC, Real, Real><<<blocks, threads, 0, s>>>(
+          cells, P.plane, static_cast<const Real*>(src_mu), static_cast<Real*>(mu));
+    load_f_kernel<Q, Store, Real><<<blocks, threads, 0, s>>>(
+        cells, P.plane, static_cast<const Real*>(src_f), static_cast<Store*>(f));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t fields(const void* params, const FieldsIO& io, cudaStream_t s) {
+    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+    const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
+    const int threads = 256;
+    const unsigned blocks = (unsigned)((cells + threads - 1) / threads);
+    fields_kernel<D, NP, NC, Real, Store, Real><<<blocks, threads, 0, s>>>(
+        P, static_cast<const Real*>(io.phi), static_cast<const Real*>(io.mu),
+        static_cast<const Store*>(io.f), io.clock, static_cast<Real*>(io.o_phi),
+        static_cast<Real*>(io.o_mu), static_cast<Real*>(io.o_c), static_cast<Real*>(io.o_f),
+        static_cast<Real*>(io.o_rho), static_cast<Real*>(io.o_u), static_cast<Real*>(io.o_dev));
+    return cudaGetLastError();
+  }
+
+  static cudaError_t invariants(const InvParams& p, const void* phi, const void* mu, const void* f,
+                                double* partial, int blocks, double* out, cudaStream_t s) {
+    invariants_kernel<Q, NP, NC, Real, Store><<<blocks, kRedThreads, 0, s>>>(
+        p, static_cast<const Real*>(phi), static_cast<const Real*>(mu),
+        static_cast<const Store*>(f), partial);
+    invariants_finish_kernel<NC + 3><<<1, 32, 0, s>>>(partial, blocks, out);
+    return cudaGetLastError();
+  }
+
+  static const Ops* table() {
+    static const Ops ops = {D,
+                            NP,
+                            NC,
+                            Q,
+                            sizeof(Real),
+                            sizeof(Store),
+                            PhiStore<NP>::NS,
+                            &Impl::configure,
+                            &Impl::step,
+                            &Impl::step_pf,
+                            &Impl::step_transport,
+                            &Impl::load,
+                            &Impl::fields,
+                            &Impl::invariants};
+    return &ops;
+  }
+};
+
+// One function per (dimension, precision) translation unit.
+const Ops* ops_d2_fp64(int NP, int NC);
+const Ops* ops_d2_fp32(int NP, int NC);
+const Ops* ops_d2_f16(int NP, int NC);
+const Ops* ops_d2_bf16(int NP, int NC);
+const Ops* ops_d3_fp64(int NP, int NC);
+const Ops* ops_d3_fp32(int NP, int NC);
+const Ops* ops_d3_f16(int NP, int NC);
+const Ops* ops_d3_bf16(int NP, int NC);
+
+#define GPFLBM_DEFINE_OPS(NAME, DIM, REAL, STORE)                            \
+  const Ops* NAME(int NP, int NC) {                                          \
+    if (NP == 2 && NC == 1) return Impl<DIM, 2, 1, REAL, STORE>::table();    \
+    if (NP == 2 && NC == 2) return Impl<DIM, 2, 2, REAL, STORE>::table();    \
+    if (NP == 3 && NC == 1) return Impl<DIM, 3, 1, REAL, STORE>::table();    \
+    if (NP == 3 && NC == 2) return Impl<DIM, 3, 2, REAL, STORE>::table();    \
+    if (NP == 4 && NC == 1) return Impl<DIM, 4, 1, REAL, STORE>::table();    \
+    if (NP == 4 && NC == 2) return Impl<DIM, 4, 2, REAL, STORE>::table();    \
+    return nullptr;                                                          \
+  }
+
+}  // namespace gpflbm

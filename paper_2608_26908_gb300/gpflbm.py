@@ -1,0 +1,257 @@
+"""Thin ctypes binding of libgpflbm.so (include/gpflbm.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  PyTorch provides the device workspace and the current stream.  If
+the library has not been built, loading it raises -- there is no CPU path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgpflbm.so")
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = (
+    -1, -2, -3, -4, -5, -6, -7)
+PERIODIC, WALL = 0, 1
+D2Q9, D3Q19 = 9, 19
+PRECISION = {"fp64": 0, "fp32": 1, "fp32_f16": 2, "fp32_bf16": 3}
+FIELD = {"phi": 1, "mu": 2, "c": 4, "f": 8, "rho": 16, "u": 32}
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lattice", ctypes.c_int), ("bc", ctypes.c_int * 3),
+                ("wall_rows", ctypes.c_int * 3), ("precision", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("tau_f", ctypes.c_double), ("tau_phi", ctypes.c_double), ("eps", ctypes.c_double),
+        ("gamma", (ctypes.c_double * 4) * 4), ("delta", (ctypes.c_double * 4) * 4),
+        ("A", ctypes.c_double * 4), ("ceq", (ctypes.c_double * 2) * 4), ("S", ctypes.c_double * 4),
+        ("D_liq", ctypes.c_double), ("a_at", ctypes.c_double),
+        ("h_drag", ctypes.c_double), ("W0", ctypes.c_double),
+        ("gbeta_c", ctypes.c_double * 2), ("c_ref", ctypes.c_double * 2),
+        ("gbeta_T", ctypes.c_double), ("T_ref", ctypes.c_double),
+        ("T_E", ctypes.c_double), ("undercool", ctypes.c_double),
+        ("G", ctypes.c_double), ("V", ctypes.c_double), ("v0", ctypes.c_double),
+        ("q_floor", ctypes.c_double),
+    ]
+
+
+class GpflbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("gpflbm status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libgpflbm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libgpflbm.so is not built (%s); run __graft_entry__.build()"
+                               % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, u, ll, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_longlong, ctypes.c_size_t
+        dp = ctypes.POINTER(ctypes.c_double)
+        L.gpflbm_workspace_bytes.argtypes = [ctypes.POINTER(Grid), i, i, ctypes.POINTER(sz)]
+        L.gpflbm_create.argtypes = [ctypes.POINTER(Grid), i, i, ctypes.POINTER(Params), vp, sz,
+                                    ctypes.POINTER(vp)]
+        L.gpflbm_set_params.argtypes = [vp, ctypes.POINTER(Params)]
+        L.gpflbm_set_state.argtypes = [vp, vp, vp, vp, i, ll, vp]
+        L.gpflbm_step.argtypes = [vp, i, vp]
+        L.gpflbm_step_timed.argtypes = [vp, ctypes.POINTER(vp), vp]
+        L.gpflbm_get_fields.argtypes = [vp, u, ctypes.POINTER(vp), i, vp]
+        L.gpflbm_get_deviations.argtypes = [vp, vp, i, vp]
+        L.gpflbm_invariants.argtypes = [vp, dp, dp, dp, vp]
+        L.gpflbm_time.argtypes = [vp, ctypes.POINTER(ll)]
+        L.gpflbm_last_error.argtypes = [vp]
+        L.gpflbm_last_error.restype = ctypes.c_char_p
+        L.gpflbm_destroy.argtypes = [vp]
+        L.gpflbm_destroy.restype = None
+        for name in ("gpflbm_workspace_bytes", "gpflbm_create", "gpflbm_set_params",
+                     "gpflbm_set_state", "gpflbm_step", "gpflbm_step_timed", "gpflbm_get_fields",
+                     "gpflbm_get_deviations", "gpflbm_invariants", "gpflbm_time"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def grid_struct(sc):
+    g = sc["grid"]
+    s = Grid()
+    s.nx, s.ny, s.nz = g["nx"], g["ny"], g.get("nz", 1)
+    s.lattice = D3Q19 if s.nz > 1 else D2Q9
+    for a in range(3):
+        s.bc[a] = g["bc"][a]
+        s.wall_rows[a] = g["wall_rows"][a] if (a < 2 or s.nz > 1) else 0
+    s.precision = PRECISION[sc["precision"]]
+    return s
+
+
+def params_struct(sc):
+    pr = sc["params"]
+    p = Params()
+    for name in ("tau_f", "tau_phi", "eps", "D_liq", "a_at", "h_drag", "W0", "gbeta_T", "T_ref",
+                 "T_E", "undercool", "G", "V", "v0", "q_floor"):
+        setattr(p, name, float(pr[name]))
+    for a in range(4):
+        p.A[a] = pr["A"][a]
+        p.S[a] = pr["S"][a]
+        for b in range(4):
+            p.gamma[a][b] = pr["gamma"][a][b]
+            p.delta[a][b] = pr["delta"][a][b]
+        for i in range(2):
+            p.ceq[a][i] = pr["ceq"][a][i]
+    for i in range(2):
+        p.gbeta_c[i] = pr["gbeta_c"][i]
+        p.c_ref[i] = pr["c_ref"][i]
+    return p
+
+
+def workspace_bytes(sc):
+    n = ctypes.c_size_t()
+    g = grid_struct(sc)
+    st = lib().gpflbm_workspace_bytes(ctypes.byref(g), sc["n_phases"], sc["n_solutes"],
+                                      ctypes.byref(n))
+    if st != OK:
+        raise GpflbmError(st, "workspace_bytes")
+    return n.value
+
+
+def _stream(torch):
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Sim:
+    """One simulation on the current CUDA device; the workspace is a torch
+    tensor, calls run on torch's current stream."""
+
+    def __init__(self, sc):
+        import torch
+        self.torch = torch
+        self.sc = sc
+        self.nx, self.ny, self.nz = sc["grid"]["nx"], sc["grid"]["ny"], sc["grid"].get("nz", 1)
+        self.cells = self.nx * self.ny * self.nz
+        self.dim = 3 if self.nz > 1 else 2
+        self.Q = 19 if self.dim == 3 else 9
+        self.NP, self.NC = sc["n_phases"], sc["n_solutes"]
+        self.dtype = np.float64 if sc["precision"] == "fp64" else np.float32
+        self.tdtype = torch.float64 if sc["precision"] == "fp64" else torch.float32
+        nbytes = workspace_bytes(sc)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self._grid = grid_struct(sc)
+        self._params = params_struct(sc)
+        h = ctypes.c_void_p()
+        st = lib().gpflbm_create(ctypes.byref(self._grid), self.NP, self.NC,
+                                 ctypes.byref(self._params), ctypes.c_void_p(self.workspace.data_ptr()),
+                                 nbytes, ctypes.byref(h))
+        if st != OK:
+            raise GpflbmError(st, "gpflbm_create")
+        self.h = h
+
+    def _check(self, st, what):
+        if st != OK:
+            msg = lib().gpflbm_last_error(self.h).decode()
+            raise GpflbmError(st, "%s: %s" % (what, msg))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gpflbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptr(self, a):
+        """(pointer, is_device, keepalive) of a numpy array or torch tensor."""
+        torch = self.torch
+        if a is None:
+            return None, None, None
+        if isinstance(a, torch.Tensor):
+            a = a.contiguous()
+            if a.dtype != self.tdtype:
+                a = a.to(self.tdtype)
+            return ctypes.c_void_p(a.data_ptr()), a.is_cuda, a
+        a = np.ascontiguousarray(a, dtype=self.dtype)
+        return ctypes.c_void_p(a.ctypes.data), False, a
+
+    def set_params(self, sc):
+        self.sc = sc
+        self._params = params_struct(sc)
+        self._check(lib().gpflbm_set_params(self.h, ctypes.byref(self._params)), "set_params")
+
+    def set_state(self, phi, mu, f=None, t0=0):
+        pp, dphi, k1 = self._ptr(phi)
+        pm, dmu, k2 = self._ptr(mu)
+        pf, df, k3 = self._ptr(f)
+        dev = bool(dphi)
+        if dmu != dev or (f is not None and df != dev):
+            raise ValueError("phi, mu and f must all be host arrays or all device tensors")
+        self._check(lib().gpflbm_set_state(self.h, pp, pm, pf, int(dev), int(t0),
+                                           _stream(self.torch)), "set_state")
+        del k1, k2, k3
+
+    def step(self, n=1):
+        self._check(lib().gpflbm_step(self.h, int(n), _stream(self.torch)), "step")
+
+    def step_timed(self, events):
+        """One step recording three torch.cuda.Event objects (before, between
+        and after the two kernels) on the current stream."""
+        raw = (ctypes.c_void_p * 3)(*[e.cuda_event for e in events])
+        self._check(lib().gpflbm_step_timed(self.h, raw, _stream(self.torch)), "step_timed")
+
+    def time(self):
+        t = ctypes.c_longlong()
+        self._check(lib().gpflbm_time(self.h, ctypes.byref(t)), "time")
+        return t.value
+
+    def _planes(self, name):
+        return {"phi": self.NP, "mu": self.NC, "c": self.NC, "f": self.Q, "rho": 1,
+                "u": self.dim}[name]
+
+    def fields(self, names=("phi", "mu"), device=False):
+        """dict name -> (planes, cells) array (numpy) or tensor (device=True)."""
+        torch = self.torch
+        names = sorted(set(names), key=lambda n: FIELD[n])
+        mask = 0
+        outs = []
+        for n in names:
+            mask |= FIELD[n]
+            shape = (self._planes(n), self.cells)
+            if device:
+                outs.append(torch.empty(shape, dtype=self.tdtype, device="cuda"))
+            else:
+                outs.append(np.empty(shape, dtype=self.dtype))
+        ptrs = (ctypes.c_void_p * len(outs))(
+            *[o.data_ptr() if device else o.ctypes.data for o in outs])
+        self._check(lib().gpflbm_get_fields(self.h, mask, ptrs, int(device), _stream(torch)),
+                    "get_fields")
+        return dict(zip(names, outs))
+
+    def deviations(self):
+        out = np.empty((self.Q, self.cells), dtype=self.dtype)
+        self._check(lib().gpflbm_get_deviations(self.h, ctypes.c_void_p(out.ctypes.data), 0,
+                                                _stream(self.torch)), "get_deviations")
+        return out
+
+    def invariants(self, allow_nonfinite=False):
+        """(mass, solute[K-1], solid_frac) from the fixed-order FP64 reduction."""
+        m = ctypes.c_double()
+        s = (ctypes.c_double * 2)()
+        fr = ctypes.c_double()
+        st = lib().gpflbm_invariants(self.h, ctypes.byref(m), s, ctypes.byref(fr),
+                                     _stream(self.torch))
+        if not (allow_nonfinite and st == ERR_NONFINITE):
+            self._check(st, "invariants")
+        return m.value, np.array(s[: self.NC]), fr.value, st

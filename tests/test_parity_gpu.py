@@ -1,0 +1,166 @@
+"""Parity of the CUDA library with the FP64 oracle, element by element, on
+seeded inputs of every workload (sizes that span several tiles and leave a
+ragged tail), after 100 steps unless stated.
+
+Tolerances (relative L-infinity per field, see parity.rel_err):
+  FP64 arithmetic: 1e-10 for phi, mu, c, rho.  U and the population
+    deviations d_k = f_k - w_k get 1e-8: the oracle carries the full f_k
+    (about 0.1..0.45) in FP64, so each step adds ~1e-16 absolute rounding to
+    every population, ~1e-14 after 100 steps, against deviations and momenta
+    of 1e-6..1e-5 -- up to ~1e-8 relative.
+  FP32 arithmetic: 1e-5 for every field (the stated target).
+  16-bit population storage with FP32 arithmetic: FP16 (x 2^10) 2e-3 for
+    every field but the deviations themselves; BF16 keeps 8 mantissa bits, a
+    relative rounding of 2^-9 = 1.95e-3 on every stored deviation, so U (a sum
+    of them) gets 5e-3 there.
+"""
+import numpy as np
+import pytest
+
+from parity import errors, rel_err, reference, device_run
+from paper_2608_26908_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "fp32_f16": 2e-3, "fp32_bf16": 5e-3}
+FP64_LBM = 1e-8  # U and deviations in FP64, see above
+
+
+def _tol(prec, field):
+    if prec == "fp64" and field in ("u", "dev"):
+        return FP64_LBM
+    return TOL[prec]
+
+CASES = {
+    "dendrite2d": dict(),                                  # 128 x 128, full size
+    "eutectic2d": dict(nx=200, ny=90),                     # crop, ragged tiles
+    "dendrite3d": dict(nx=40, ny=36, nz=33),               # crop, ragged tiles
+    "eutectic3d": dict(nx=36, ny=34, nz=40),               # crop, ragged tiles
+    "adjoint2d": dict(nx=96, ny=80),
+}
+
+
+def _case(name, precision):
+    sc = inputs.scenario(name, precision=precision, **CASES[name])
+    if name == "eutectic3d":
+        sc["init"]["height"] = 12
+    return sc
+
+
+def _report(name, prec, errs):
+    print("%s/%s %s" % (name, prec, " ".join("%s=%.2e" % kv for kv in sorted(errs.items()))))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_parity_100_steps(name, prec):
+    sc = _case(name, prec)
+    errs, sim, got, ref = errors(sc, 100)
+    _report(name, prec, errs)
+    for k, e in errs.items():
+        assert e <= _tol(prec, k), (k, e)
+
+
+@pytest.mark.parametrize("prec", ["fp32_f16", "fp32_bf16"])
+def test_parity_reduced_storage(prec):
+    sc = _case("dendrite3d", prec)
+    errs, sim, got, ref = errors(sc, 100)
+    _report("dendrite3d", prec, errs)
+    for k in ("phi", "mu", "c", "rho", "u"):
+        assert errs[k] <= TOL[prec], (k, errs[k])
+
+
+@pytest.mark.parametrize("np_nc", [(4, 2), (3, 2), (2, 2), (4, 1)])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_parity_other_phase_and_solute_counts(np_nc, dim):
+    NP, NC = np_nc
+    sc = inputs.scenario("eutectic3d" if dim == 3 else "eutectic2d",
+                         nx=37, ny=35 if dim == 2 else 21, nz=19 if dim == 3 else None,
+                         precision="fp64")
+    sc["n_phases"], sc["n_solutes"] = NP, NC
+    p = sc["params"]
+    third = 1.0 / 3.0
+    p["ceq"] = [[third, third], [0.8, 0.1], [0.1, 0.8], [0.1, 0.1]]
+    for a in range(1, 4):
+        p["S"][a] = 2 * sum((p["ceq"][0][i] - p["ceq"][a][i]) ** 2 for i in range(NC))
+        for b in range(4):
+            if a != b:
+                p["gamma"][a][b] = p["gamma"][b][a] = 0.2
+    p["delta"][0][1] = p["delta"][1][0] = 0.03  # one anisotropic pair
+    p["gbeta_c"] = [2e-3, -1e-3]
+    p["c_ref"] = [third, third]
+    nx, ny, nz = inputs.dims(sc)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    x, y, z = x.reshape(-1), y.reshape(-1), z.reshape(-1)
+    vert = z if dim == 3 else y
+    which = 1 + ((x // 6) + (y // 5 if dim == 3 else 0)) % (NP - 1)
+    phi0 = np.zeros((NP, x.size))
+    for a in range(1, NP):
+        phi0[a] = ((vert < 8) & (which == a)).astype(float)
+    phi0[0] = 1.0 - phi0[1:].sum(axis=0)
+    phi0 = phi0.reshape(-1)
+    rng = np.random.default_rng(NP * 10 + NC)
+    mu0 = 2e-3 * rng.uniform(-1, 1, size=NC * x.size)
+    ref = reference(sc, 60, phi0, mu0)
+    sim, got = device_run(sc, 60, phi0, mu0)
+    errs = {k: rel_err(got[k], ref[k]) for k in ("phi", "mu", "c", "rho", "u", "dev")}
+    _report("%dD N=%d K-1=%d" % (dim, NP, NC), "fp64", errs)
+    for k, e in errs.items():
+        assert e <= _tol("fp64", k), (k, e)
+
+
+def test_bench_workload_full_size_fp32():
+    """The benchmark's workload (2D eutectic, 1024 x 512, FP32) at full size,
+    through the same graph-replayed launches bench.py times."""
+    sc = inputs.scenario("eutectic2d")
+    errs, sim, got, ref = errors(sc, 20, chunks=[16, 3, 1])
+    _report("eutectic2d-full", "fp32", errs)
+    for k, e in errs.items():
+        assert e <= TOL["fp32"], (k, e)
+
+
+def test_step_chunking_is_invisible():
+    """1 + 2 + 16 + 1 steps (direct, pair graph, chunk graph) == 20 steps."""
+    sc = _case("dendrite2d", "fp32")
+    _, a = device_run(sc, 20)
+    _, b = device_run(sc, 20, chunks=[1, 2, 16, 1])
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+# Natural size of each field, a floor for the error scale on grids so small
+# that a field stays far below it (a 3 x 3 box keeps mu near its 1e-4 noise
+# while the per-step source terms are ~0.1, and FP32 rounds those).
+FLOOR = {"phi": 1.0, "mu": 0.1, "c": 0.1, "rho": 1.0, "u": 1e-4, "dev": 1e-4}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tiny_and_degenerate_grids(prec):
+    for nx, ny, nz in ((3, 3, 1), (5, 3, 1), (3, 4, 3), (33, 9, 1), (17, 5, 3)):
+        name = "dendrite3d" if nz > 1 else "dendrite2d"
+        sc = inputs.scenario(name, nx=nx, ny=ny, nz=nz if nz > 1 else None, precision=prec)
+        sc["grid"]["wall_rows"] = [0, 0, 0]
+        sc["init"]["radius"] = 1.5
+        sc["params"]["gbeta_c"] = [5e-3, 0.0]
+        ref = reference(sc, 30)
+        _, got = device_run(sc, 30)
+        for k in FLOOR:
+            g = np.asarray(got[k], dtype=np.float64)
+            r = np.asarray(ref[k], dtype=np.float64)
+            e = np.abs(g - r).max() / max(np.abs(r).max(), FLOOR[k])
+            assert e <= _tol(prec, k), (nx, ny, nz, k, e)
+
+
+def test_state_round_trip_is_exact():
+    for prec in ("fp64", "fp32"):
+        sc = _case("eutectic3d", prec)
+        phi0, mu0 = inputs.initial_state(sc)
+        rng = np.random.default_rng(1)
+        q = 19
+        f0 = (1.0 / q + 1e-3 * rng.normal(size=(q, inputs.cells(sc)))).reshape(-1)
+        dt = np.float64 if prec == "fp64" else np.float32
+        sim, got = device_run(sc, 0, phi0, mu0, f0)
+        np.testing.assert_array_equal(got["phi"].reshape(-1), phi0.astype(dt))
+        np.testing.assert_array_equal(got["mu"].reshape(-1), mu0.astype(dt))
+        if prec == "fp64":
+            np.testing.assert_allclose(got["f"].reshape(-1), f0, rtol=0, atol=1e-16)
