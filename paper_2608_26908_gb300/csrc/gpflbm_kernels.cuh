@@ -116,7 +116,7 @@ template <int D, class Real>
 struct Tile;
 template <>
 struct Tile<2, float> {
-  static constexpr int TX = 32, TY = 8, TZ = 1;
+  static constexpr int TX = 64, TY = 8, TZ = 1;
 };
 template <>
 struct Tile<2, double> {
@@ -334,6 +334,35 @@ __device__ __forceinline__ long long cell_index(const DevParams<Real>& P, int x,
   return (long long)x + (long long)P.n[0] * ((long long)y + (long long)P.n[1] * z);
 }
 
+// True when the tile and its one-cell halo lie inside the domain on every
+// axis, so halo cells need no wrapping or mirroring (block-uniform).
+template <int D, class Real>
+__device__ __forceinline__ bool tile_inside(const DevParams<Real>& P, const int* b0) {
+  using G = Geo<D, Real>;
+  const int T[3] = {G::TX, G::TY, G::TZ};
+  bool in = true;
+#pragma unroll
+  for (int a = 0; a < D; ++a) in = in && b0[a] >= 1 && b0[a] + T[a] + 1 <= P.n[a];
+  return in;
+}
+
+// Global coordinates of halo cell h of the tile at b0 (halo offset 1 per axis).
+template <int D, class Real>
+__device__ __forceinline__ void halo_coords(const DevParams<Real>& P, const int* b0, bool inner,
+                                            int h, int* c) {
+  using G = Geo<D, Real>;
+  const int hx = h % G::HX, hy = (h / G::HX) % G::HY, hz = h / (G::HX * G::HY);
+  if (inner) {
+    c[0] = b0[0] + hx - 1;
+    c[1] = b0[1] + hy - 1;
+    c[2] = D == 3 ? b0[2] + hz - 1 : 0;
+  } else {
+    c[0] = fold_axis(P, b0[0] + hx - 1, 0);
+    c[1] = fold_axis(P, b0[1] + hy - 1, 1);
+    c[2] = D == 3 ? fold_axis(P, b0[2] + hz - 1, 2) : 0;
+  }
+}
+
 // Shared-memory layout of the phase-field kernel (bytes).
 template <int D, int NP, class Real>
 struct PfSmem {
@@ -341,7 +370,8 @@ struct PfSmem {
   static constexpr size_t phi = 0;
   static constexpr size_t flux = phi + sizeof(Real) * NP * G::HC;
   static constexpr size_t mask = flux + sizeof(Real) * NP * G::FALL;
-  static constexpr size_t bytes = mask + G::HC + 16;
+  static constexpr size_t multi = mask + G::HC;
+  static constexpr size_t bytes = multi + G::NT + 16;
 };
 
 template <int D, int NP, int NC, class Real>
@@ -351,22 +381,23 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
                        const double* __restrict__ clock) {
   using G = Geo<D, Real>;
   using L = PfSmem<D, NP, Real>;
+  constexpr int NS = PhiStore<NP>::NS;
   extern __shared__ __align__(16) unsigned char smem[];
   Real* s_phi = reinterpret_cast<Real*>(smem + L::phi);
   Real* s_flux = reinterpret_cast<Real*>(smem + L::flux);
   unsigned char* s_mask = smem + L::mask;
+  unsigned char* s_multi = smem + L::multi;
 
   const int tid = threadIdx.x;
   const int b0[3] = {(int)blockIdx.x * G::TX, (int)blockIdx.y * G::TY, (int)blockIdx.z * G::TZ};
+  const bool inner = tile_inside<D>(P, b0);
 
   // 1. phi^n on the tile and its halo, plus the set of phases present
   for (int h = tid; h < G::HC; h += G::NT) {
-    const int hx = h % G::HX, hy = (h / G::HX) % G::HY, hz = h / (G::HX * G::HY);
-    const int gx = fold_axis(P, b0[0] + hx - 1, 0);
-    const int gy = fold_axis(P, b0[1] + hy - 1, 1);
-    const int gz = D == 3 ? fold_axis(P, b0[2] + hz - 1, 2) : 0;
+    int c[3];
+    halo_coords<D>(P, b0, inner, h, c);
     Real v[NP];
-    load_phases<NP>(phi_in, cell_index<D>(P, gx, gy, gz), P.plane, v);
+    load_phases<NP>(phi_in, cell_index<D>(P, c[0], c[1], c[2]), P.plane, v);
     unsigned m = 0;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
@@ -377,34 +408,60 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
   }
   __syncthreads();
 
-  // 2. d-th component of da/d(grad phi_a) on every face of the tile:
+  // 2. cells with more than one phase in their 3^d neighbourhood; elsewhere
+  //    the single present phase keeps phi = 1 (its rate g - Lambda is 0)
+  const int t3[3] = {tid % G::TX, (tid / G::TX) % G::TY, tid / (G::TX * G::TY)};
+  const int gx = b0[0] + t3[0], gy = b0[1] + t3[1], gz = b0[2] + t3[2];
+  const bool inside = gx < P.n[0] && gy < P.n[1] && gz < P.n[2];
+  const int h = (t3[0] + 1) * G::SX + (t3[1] + 1) * G::SY + (t3[2] + G::ZOFF) * G::SZ;
+  unsigned act = 0;
+#pragma unroll
+  for (int dz = -(D == 3 ? 1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) act |= s_mask[h + dx * G::SX + dy * G::SY + dz * G::SZ];
+  const bool multi = inside && __popc(act) >= 2 && !obstacle(P, gx, gy, gz);
+  s_multi[tid] = multi ? 1 : 0;
+  const long long g = inside ? cell_index<D>(P, gx, gy, gz) : 0;
+  if (!__syncthreads_or(multi)) {
+    if (inside)
+#pragma unroll
+      for (int s = 0; s < NS; ++s) phi_out[s * P.plane + g] = s_phi[(NP == 2 ? 1 : s) * G::HC + h];
+    return;
+  }
+
+  // 3. d-th component of da/d(grad phi_a) on the faces of multi-phase cells:
   //    -sum_{b != a} gamma_ab phi_b dA/dq(q_ab), q_ab = phi_a grad phi_b - phi_b grad phi_a
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const int ex = G::fext(d, 0), ey = G::fext(d, 1);
+    const int tstride = d == 0 ? 1 : (d == 1 ? G::TX : G::TX * G::TY);
+    const int Td = d == 0 ? G::TX : (d == 1 ? G::TY : G::TZ);
     for (int i = tid; i < G::fcount(d); i += G::NT) {
       const int f[3] = {i % ex, (i / ex) % ey, i / (ex * ey)};
+      const int tu = f[0] + G::TX * (f[1] + G::TY * f[2]);  // upper tile cell (if f[d] < Td)
+      const bool need = (f[d] < Td && s_multi[tu]) || (f[d] > 0 && s_multi[tu - tstride]);
       const int gd = b0[d] + f[d];  // global index of the upper cell of the face
+      const bool closed = P.bc[d] == kWall && (gd == 0 || gd == P.n[d]);
       Real fl[NP];
 #pragma unroll
       for (int a = 0; a < NP; ++a) fl[a] = Real(0);
-      const bool closed = (P.bc[d] == kWall && (gd == 0 || gd == P.n[d])) || gd > P.n[d];
-      if (!closed) {
-        // halo index of the lower cell a and the upper cell b
+      if (need && !closed) {
         const int hb = (f[0] + 1) * G::SX + (f[1] + 1) * G::SY + (f[2] + G::ZOFF) * G::SZ;
         const int ha = hb - G::hstride(d);
         Real pf[NP], gr[NP][D];
 #pragma unroll
         for (int a = 0; a < NP; ++a) {
-          const Real* s = s_phi + a * G::HC;
-          pf[a] = Real(0.5) * (s[ha] + s[hb]);
+          const Real* sp = s_phi + a * G::HC;
+          pf[a] = Real(0.5) * (sp[ha] + sp[hb]);
 #pragma unroll
           for (int t = 0; t < D; ++t) {
             if (t == d) {
-              gr[a][t] = s[hb] - s[ha];
+              gr[a][t] = sp[hb] - sp[ha];
             } else {
               const int st = G::hstride(t);
-              gr[a][t] = Real(0.25) * (s[ha + st] + s[hb + st] - s[ha - st] - s[hb - st]);
+              gr[a][t] = Real(0.25) * (sp[ha + st] + sp[hb + st] - sp[ha - st] - sp[hb - st]);
             }
           }
         }
@@ -428,22 +485,16 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
   }
   __syncthreads();
 
-  // 3. one cell per thread
-  const int t3[3] = {tid % G::TX, (tid / G::TX) % G::TY, tid / (G::TX * G::TY)};
-  const int gx = b0[0] + t3[0], gy = b0[1] + t3[1], gz = b0[2] + t3[2];
-  if (gx >= P.n[0] || gy >= P.n[1] || gz >= P.n[2]) return;
-  const long long g = cell_index<D>(P, gx, gy, gz);
-  constexpr int NS = PhiStore<NP>::NS;
-  const int h = (t3[0] + 1) * G::SX + (t3[1] + 1) * G::SY + (t3[2] + G::ZOFF) * G::SZ;
+  // 4. one cell per thread
+  if (!inside) return;
   Real ph[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) ph[a] = s_phi[a * G::HC + h];
-  if (obstacle(P, gx, gy, gz)) {
+  if (!multi) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) phi_out[s * P.plane + g] = ph[NP == 2 ? 1 : s];
     return;
   }
-  // divergence of the face fluxes
   Real div[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) div[a] = Real(0);
@@ -487,13 +538,12 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
       dadphi[a] += gab * va;
       dadphi[b] -= gab * vb;
     }
-  // grand potentials psi_b(mu, T)
+  // grand potentials psi_b(mu, T), theta = T - T_E
   Real mu[NC];
 #pragma unroll
   for (int i = 0; i < NC; ++i) mu[i] = mu_in[i * P.plane + g];
-  const double t_now = clock[0];
   const int v_coord = D == 3 ? gz : gy;
-  const Real theta = Real(P.theta0 - P.GV * t_now) + P.G * Real(v_coord);
+  const Real theta = (Real(P.theta0) - Real(P.GV) * Real(clock[0])) + P.G * Real(v_coord);
   Real psi[NP];
 #pragma unroll
   for (int b = 0; b < NP; ++b) {
@@ -514,14 +564,6 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
     }
     rate[a] = P.eps * (div[a] - dadphi[a]) - P.obst * obst - drive;
   }
-  // phases present in the 3^d neighbourhood
-  unsigned act = 0;
-#pragma unroll
-  for (int dz = -(D == 3 ? 1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) act |= s_mask[h + dx * G::SX + dy * G::SY + dz * G::SZ];
   int na = 0;
   Real lam = Real(0);
 #pragma unroll
@@ -538,14 +580,9 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
     if (act & (1u << a)) u[m++] = ph[a] + P.mob_eps * (rate[a] - lam);
   Real out[NP];
   if (NP == 2) {
-    if (m == 2) {
-      // only phi_1 is stored: clamp it to [0, 1] (the two-phase projection)
-      Real s = u[1];
-      s = s < Real(0) ? Real(0) : (s > Real(1) ? Real(1) : s);
-      out[1] = s;
-    } else {
-      out[1] = ph[1];
-    }
+    // only phi_1 is stored: clamp it to [0, 1] (the two-phase projection)
+    Real s = u[1];
+    out[1] = s < Real(0) ? Real(0) : (s > Real(1) ? Real(1) : s);
   } else {
     project_simplex<Real, NP>(u, m);
     m = 0;
@@ -560,15 +597,16 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
 template <int D, int NP, int NC, class Real>
 struct MlSmem {
   using G = Geo<D, Real>;
+  static constexpr int Q = D == 2 ? 9 : 19;
   static constexpr size_t po = 0;                                   // phi^n
   static constexpr size_t pn = po + sizeof(Real) * NP * G::HC;      // phi^{n+1}
   static constexpr size_t mu = pn + sizeof(Real) * NP * G::HC;      // mu^n
-  static constexpr size_t drho = mu + sizeof(Real) * NC * G::HC;    // rho - 1
-  static constexpr size_t u = drho + sizeof(Real) * G::HC;          // U
-  static constexpr size_t F = u + sizeof(Real) * D * G::HC;         // total force
-  static constexpr size_t hl = F + sizeof(Real) * D * G::HC;        // h_liquid(phi^{n+1})
-  static constexpr size_t J = hl + sizeof(Real) * G::HC;            // face fluxes
-  static constexpr size_t bytes = J + sizeof(Real) * NC * G::FALL;
+  static constexpr size_t u = mu + sizeof(Real) * NC * G::HC;       // U^n
+  static constexpr size_t hl = u + sizeof(Real) * D * G::HC;        // h_liquid(phi^{n+1})
+  static constexpr size_t fs = hl + sizeof(Real) * G::HC;           // collided deviations
+  static constexpr size_t J = fs + sizeof(Real) * Q * G::HC;        // face fluxes
+  static constexpr size_t chg = J + sizeof(Real) * NC * G::FALL;    // phi changed
+  static constexpr size_t bytes = chg + G::HC + 16;
 };
 
 template <int D, int NP, int NC, class Real, class Store>
@@ -586,33 +624,37 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
   Real* s_po = reinterpret_cast<Real*>(smem + L::po);
   Real* s_pn = reinterpret_cast<Real*>(smem + L::pn);
   Real* s_mu = reinterpret_cast<Real*>(smem + L::mu);
-  Real* s_drho = reinterpret_cast<Real*>(smem + L::drho);
   Real* s_u = reinterpret_cast<Real*>(smem + L::u);
-  Real* s_F = reinterpret_cast<Real*>(smem + L::F);
   Real* s_hl = reinterpret_cast<Real*>(smem + L::hl);
+  Real* s_fs = reinterpret_cast<Real*>(smem + L::fs);
   Real* s_J = reinterpret_cast<Real*>(smem + L::J);
+  unsigned char* s_chg = smem + L::chg;
 
   const int tid = threadIdx.x;
   const int b0[3] = {(int)blockIdx.x * G::TX, (int)blockIdx.y * G::TY, (int)blockIdx.z * G::TZ};
+  const bool inner = tile_inside<D>(P, b0);
   const double t_now = clock_in[0];
-  const Real theta_base = Real(P.theta0 - P.GV * t_now);
+  const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
+  const Real omega = Real(1) - P.inv_tau_f;
 
-  // 1. stage phi^n, phi^{n+1}, mu^n and the moments of f^n on tile + halo:
-  //    rho, U = (m + F_B/2) / (rho (1 + kappa/2)), F = F_B - rho kappa U
+  // 1. stage phi^n, phi^{n+1}, mu^n on tile + halo; moments of f^n,
+  //    rho, U = (m + F_B/2) / (rho (1 + kappa/2)), F = F_B - rho kappa U,
+  //    and the BGK + Guo collision of every staged cell
   for (int h = tid; h < G::HC; h += G::NT) {
-    const int hx = h % G::HX, hy = (h / G::HX) % G::HY, hz = h / (G::HX * G::HY);
-    const int gx = fold_axis(P, b0[0] + hx - 1, 0);
-    const int gy = fold_axis(P, b0[1] + hy - 1, 1);
-    const int gz = D == 3 ? fold_axis(P, b0[2] + hz - 1, 2) : 0;
-    const long long g = cell_index<D>(P, gx, gy, gz);
+    int c[3];
+    halo_coords<D>(P, b0, inner, h, c);
+    const long long g = cell_index<D>(P, c[0], c[1], c[2]);
     Real po[NP], pn[NP];
     load_phases<NP>(phi_old, g, P.plane, po);
     load_phases<NP>(phi_new, g, P.plane, pn);
+    bool changed = false;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
       s_po[a * G::HC + h] = po[a];
       s_pn[a * G::HC + h] = pn[a];
+      changed = changed || (po[a] != pn[a]);
     }
+    s_chg[h] = changed ? 1 : 0;
     s_hl[h] = interp_h<NP>(pn, 0);
     Real mu[NC];
 #pragma unroll
@@ -620,35 +662,62 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
       mu[i] = mu_in[i * P.plane + g];
       s_mu[i * G::HC + h] = mu[i];
     }
+    Real dk[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(f_in[k * P.plane + g]);
     Real drho = Real(0), m[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) m[a] = Real(0);
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      const Real dk = Codec<Store>::load(f_in[k * P.plane + g]);
-      drho += dk;
+      drho += dk[k];
 #pragma unroll
       for (int a = 0; a < D; ++a)
-        if (Lat::c(k, a) != 0) m[a] += Real(Lat::c(k, a)) * dk;
+        if (Lat::c(k, a) != 0) m[a] += Real(Lat::c(k, a)) * dk[k];
     }
     const Real rho = Real(1) + drho;
-    const Real phil = obstacle(P, gx, gy, gz) ? Real(0) : po[0];
+    const Real phil = obstacle(P, c[0], c[1], c[2]) ? Real(0) : po[0];
     const Real sl = Real(1) - phil;
     const Real kappa = P.kappa0 * sl * sl;
-    const int v_coord = D == 3 ? gz : gy;
-    const Real theta = theta_base + P.G * Real(v_coord);
+    const Real theta = theta_base + P.G * Real(D == 3 ? c[2] : c[1]);
     Real drive = P.gbeta_T * (theta + P.dT_ref);
 #pragma unroll
     for (int i = 0; i < NC; ++i) drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
     const Real FB = rho * phil * drive;
     const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
-    s_drho[h] = drho;
+    Real u[D], F[D];
+    Real uu = Real(0), uF = Real(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const Real fb = a == D - 1 ? FB : Real(0);
-      const Real u = (m[a] + Real(0.5) * fb) * inv;
-      s_u[a * G::HC + h] = u;
-      s_F[a * G::HC + h] = fb - rho * kappa * u;
+      u[a] = (m[a] + Real(0.5) * fb) * inv;
+      F[a] = fb - rho * kappa * u[a];
+      s_u[a * G::HC + h] = u[a];
+      uu += u[a] * u[a];
+      uF += u[a] * F[a];
+    }
+    // f*_k - w_k = (1 - 1/tau) d_k + (feq_k - w_k)/tau + G_k with
+    // feq_k - w_k = w_k [(drho - 1.5 rho U.U) + rho cu (3 + 4.5 cu)],
+    // G_k = w_k [-3 (1 - 1/2tau) U.F + (1 - 1/2tau) cF (3 + 9 cu)]
+    const Real A0 = drho - Real(1.5) * rho * uu;
+    const Real B0 = Real(-3) * P.force_pre * uF;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      Real cu = Real(0), cF = Real(0);
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (Lat::c(k, a) > 0) {
+          cu += u[a];
+          cF += F[a];
+        } else if (Lat::c(k, a) < 0) {
+          cu -= u[a];
+          cF -= F[a];
+        }
+      }
+      const Real wk = Real(Lat::w(k));
+      const Real deq = wk * (A0 + rho * cu * (Real(3) + Real(4.5) * cu));
+      const Real Gk = wk * (B0 + P.force_pre * cF * (Real(3) + Real(9) * cu));
+      s_fs[k * G::HC + h] = omega * dk[k] + P.inv_tau_f * deq + Gk;
     }
   }
   __syncthreads();
@@ -667,7 +736,7 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
 #pragma unroll
       for (int s = 0; s < NC; ++s) J[s] = Real(0);
       bool closed = (P.bc[d] == kWall && (gd == 0 || gd == P.n[d])) || gd > P.n[d];
-      if (!closed) {
+      if (!closed && (P.wall[0] | P.wall[1] | P.wall[2])) {
         int ga[3] = {b0[0] + f[0], b0[1] + f[1], b0[2] + f[2]};
         int gb[3] = {ga[0], ga[1], ga[2]};
         ga[d] -= 1;
@@ -689,7 +758,7 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
           J[s] = -Mf * (mb - ma) +
                  Real(0.5) * (ua * (P.ceq[0][s] + ma * P.inv2A[0]) + ub * (P.ceq[0][s] + mb * P.inv2A[0]));
         }
-        if (P.at_eps != Real(0)) {
+        if (P.at_eps != Real(0) && (s_chg[ha] | s_chg[hb])) {
           Real at[NC];
 #pragma unroll
           for (int s = 0; s < NC; ++s) at[s] = Real(0);
@@ -733,8 +802,8 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
 
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) clock_out[0] = t_now + 1.0;
 
-  // 3. one cell per thread: mu^{n+1}, then f^{n+1} by pulling collided
-  //    populations from the neighbours
+  // 3. one cell per thread: mu^{n+1}, then f^{n+1} pulled from the collided
+  //    populations of the neighbours (halfway bounce-back on walls)
   const int t3[3] = {tid % G::TX, (tid / G::TX) % G::TY, tid / (G::TX * G::TY)};
   const int gc3[3] = {b0[0] + t3[0], b0[1] + t3[1], b0[2] + t3[2]};
   if (gc3[0] >= P.n[0] || gc3[1] >= P.n[1] || gc3[2] >= P.n[2]) return;
@@ -776,45 +845,17 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
     }
   }
 
-  // BGK collision at the source cell x - c_k with the second-order
-  // equilibrium and Guo forcing, then pull; halfway bounce-back on walls.
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    int src[3] = {gc3[0] - Lat::c(k, 0), gc3[1] - Lat::c(k, 1), D == 3 ? gc3[2] - Lat::c(k, 2) : 0};
     bool bounce = false;
 #pragma unroll
-    for (int a = 0; a < D; ++a)
-      if (P.bc[a] == kWall && (src[a] < 0 || src[a] >= P.n[a])) bounce = true;
-    int kk = k, hs = h;
-    long long gs = g;
-    if (bounce) {
-      kk = Lat::opp(k);
-    } else {
-      hs = h - Lat::c(k, 0) * G::SX - Lat::c(k, 1) * G::SY - (D == 3 ? Lat::c(k, 2) * G::SZ : 0);
-#pragma unroll
-      for (int a = 0; a < D; ++a) src[a] = src[a] < 0 ? src[a] + P.n[a] : (src[a] >= P.n[a] ? src[a] - P.n[a] : src[a]);
-      gs = cell_index<D>(P, src[0], src[1], src[2]);
-    }
-    // kk is only known at run time on the bounce path; evaluate the
-    // collision of population kk at the source cell
-    Real cu = Real(0), uu = Real(0), cF = Real(0), uF = Real(0);
-    const Real drho = s_drho[hs];
-    const Real rho = Real(1) + drho;
-#pragma unroll
     for (int a = 0; a < D; ++a) {
-      const Real ua = s_u[a * G::HC + hs], Fa = s_F[a * G::HC + hs];
-      const Real ca = Real(bounce ? Lat::c(Lat::opp(k), a) : Lat::c(k, a));
-      cu += ca * ua;
-      cF += ca * Fa;
-      uu += ua * ua;
-      uF += ua * Fa;
+      const int sa = gc3[a] - Lat::c(k, a);
+      if (P.bc[a] == kWall && (sa < 0 || sa >= P.n[a])) bounce = true;
     }
-    const Real wk = Real(Lat::w(k));  // w of k and of its opposite are equal
-    const Real deq = wk * (drho + rho * (Real(3) * cu + Real(4.5) * cu * cu - Real(1.5) * uu));
-    const Real Gk = P.force_pre * wk * (Real(3) * (cF - uF) + Real(9) * cu * cF);
-    const Real dk = Codec<Store>::load(f_in[kk * P.plane + gs]);
-    const Real dstar = dk - (dk - deq) * P.inv_tau_f + Gk;
-    f_out[k * P.plane + g] = Codec<Store>::put(dstar);
+    const int hs = h - Lat::c(k, 0) * G::SX - Lat::c(k, 1) * G::SY - (D == 3 ? Lat::c(k, 2) * G::SZ : 0);
+    const Real v = bounce ? s_fs[Lat::opp(k) * G::HC + h] : s_fs[k * G::HC + hs];
+    f_out[k * P.plane + g] = Codec<Store>::put(v);
   }
 }
 
