@@ -50,7 +50,7 @@ typedef enum {
   GPFLBM_ERR_OOM = -2,         /* workspace too small or device allocation failed */
   GPFLBM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   GPFLBM_ERR_NONFINITE = -4,   /* NaN or Inf found in the state by gpflbm_invariants */
-  GPFLBM_ERR_TIMEOUT = -5,     /* reserved: a bounded device wait gave up */
+  GPFLBM_ERR_TIMEOUT = -5,     /* a bounded device wait (TMA copy) gave up during a step */
   GPFLBM_ERR_STATE = -6,       /* call out of order (e.g. step before set_state) */
   GPFLBM_ERR_UNSUPPORTED = -7  /* valid but not built: phase/solute count, lattice */
 } gpflbm_status;
@@ -167,7 +167,9 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
  * xor-butterfly (offsets 16, 8, 4, 2, 1); lane 0 of warps 0..7 are then
  * added in order; the G block sums are added in order.  Synchronises
  * `stream`.  Returns GPFLBM_ERR_NONFINITE (totals still written) if any
- * cell of the state is NaN or Inf.  Any output pointer may be NULL. */
+ * cell of the state is NaN or Inf, and GPFLBM_ERR_TIMEOUT if a step since
+ * the last gpflbm_set_state abandoned a bounded wait for its tile copies
+ * (the state is then invalid).  Any output pointer may be NULL. */
 gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double* solid_frac,
                                 void* stream);
 

@@ -26,7 +26,7 @@ constexpr int kChunk = 16;  // steps per replayed CUDA graph
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t phi[2], mu[2], f[2], stage, clock, partial, red;
+  size_t phi[2], mu[2], f[2], stage, clock, err, partial, red;
   size_t total;
 };
 
@@ -37,6 +37,7 @@ struct gpflbm_s {
   gpflbm_params params;
   int NP, NC, Q, D;
   long long cells, plane;
+  int px;  // padded row pitch (elements)
   const Ops* ops;
   Layout lay;
   unsigned char* ws;
@@ -148,6 +149,7 @@ Layout make_layout(const Ops* ops, long long cells, long long plane) {
   for (int i = 0; i < 2; ++i) L.f[i] = take(ops->Q * plane * ops->store_size);
   L.stage = take(ops->Q * plane * ops->real_size);
   L.clock = take(2 * sizeof(double));
+  L.err = take(sizeof(int));
   L.partial = take(gpflbm::kRedMaxBlocks * (ops->NC + 3) * sizeof(double));
   L.red = take((ops->NC + 3) * sizeof(double));
   L.total = off;
@@ -165,6 +167,7 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
     P.bc[a] = a < h->D ? h->grid.bc[a] : GPFLBM_PERIODIC;
     P.wall[a] = a < h->D ? h->grid.wall_rows[a] : 0;
   }
+  P.px = h->px;
   P.plane = h->plane;
   P.eps = (Real)p.eps;
   P.mob_eps = (Real)(1.0 / (p.tau_phi * p.eps));
@@ -221,6 +224,8 @@ void set_device_params(gpflbm_t h) {
   fill_params(h, h->pf);
   h->inv.cells = h->cells;
   h->inv.plane = h->plane;
+  h->inv.nx = h->grid.nx;
+  h->inv.px = h->px;
   for (int a = 0; a < 4; ++a) {
     for (int i = 0; i < 2; ++i) h->inv.ceq[a][i] = h->params.ceq[a][i];
     h->inv.inv2A[a] = 1.0 / (2.0 * h->params.A[a]);
@@ -243,6 +248,7 @@ gpflbm::StepIO step_io(gpflbm_t h, int from) {
   io.f_out = at(h, h->lay.f[1 - from]);
   io.clock_in = reinterpret_cast<const double*>(at(h, h->lay.clock)) + from;
   io.clock_out = reinterpret_cast<double*>(at(h, h->lay.clock)) + 1 - from;
+  io.err = reinterpret_cast<int*>(at(h, h->lay.err));
   return io;
 }
 
@@ -291,7 +297,8 @@ gpflbm_status gpflbm_workspace_bytes(const gpflbm_grid* grid, int n_phases, int 
   gpflbm_status st = check_grid(grid, n_phases, n_components, &D, &ops, &why);
   if (st != GPFLBM_OK) return st;
   const long long cells = (long long)grid->nx * grid->ny * grid->nz;
-  *bytes = make_layout(ops, cells, (long long)round_up(cells, 64)).total;
+  const size_t px = round_up(grid->nx, 8);
+  *bytes = make_layout(ops, cells, (long long)round_up(px * grid->ny * grid->nz, 64)).total;
   return GPFLBM_OK;
 }
 
@@ -323,7 +330,8 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
   h->Q = ops->Q;
   h->ops = ops;
   h->cells = (long long)grid->nx * grid->ny * grid->nz;
-  h->plane = (long long)round_up(h->cells, 64);
+  h->px = (int)round_up(grid->nx, 8);
+  h->plane = (long long)round_up((size_t)h->px * grid->ny * grid->nz, 64);
   h->lay = make_layout(ops, h->cells, h->plane);
   h->cur = 0;
   h->t = 0;
@@ -352,6 +360,12 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
     std::fprintf(stderr, "gpflbm_create: %s\n", cudaGetErrorString(e));
     if (h->owns_ws) cudaFree(h->ws);
     delete h;
+    return GPFLBM_ERR_CUDA;
+  }
+  e = cudaMemset(h->ws, 0, h->lay.total);  // padding cells stay finite
+  if (e != cudaSuccess) {
+    std::fprintf(stderr, "gpflbm_create: %s\n", cudaGetErrorString(e));
+    gpflbm_destroy(h);
     return GPFLBM_ERR_CUDA;
   }
   set_device_params(h);
@@ -409,6 +423,8 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   double tt[2] = {(double)t0, (double)t0};
   e = cudaMemcpyAsync(at(h, h->lay.clock), tt, sizeof(tt), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state: clock");
+  e = cudaMemsetAsync(at(h, h->lay.err), 0, sizeof(int), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: error word");
   e = cudaStreamSynchronize(s);  // host sources (and tt) must outlive the copies
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state: synchronize");
   h->t = t0;
@@ -538,9 +554,14 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
                                      at(h, h->lay.f[h->cur]), partial, blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: kernel");
   double out[GPFLBM_MAX_SOLUTES + 3];
+  int err_word = 0;
   e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&err_word, at(h, h->lay.err), sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: copy");
+  if (err_word != 0)
+    return fail(h, GPFLBM_ERR_TIMEOUT, "a bounded device wait gave up during a step");
   if (mass) *mass = out[0] + (double)h->cells;
   if (solute)
     for (int i = 0; i < h->NC; ++i) solute[i] = out[1 + i];

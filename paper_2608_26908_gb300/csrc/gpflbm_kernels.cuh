@@ -162,6 +162,7 @@ struct DevParams {
   int n[3];            // cells per axis (n[2] = 1 in 2D)
   int bc[3];           // periodic / wall per axis
   int wall[3];         // obstacle rows at both ends of each axis
+  int px;              // row pitch in elements (nx rounded up to 8)
   long long plane;     // elements between consecutive planes of a field
   Real eps;            // epsilon
   Real mob_eps;        // 1 / (tau_phi * eps)
@@ -331,7 +332,7 @@ __device__ __forceinline__ void load_phases(const Real* __restrict__ phi, long l
 
 template <int D, class Real>
 __device__ __forceinline__ long long cell_index(const DevParams<Real>& P, int x, int y, int z) {
-  return (long long)x + (long long)P.n[0] * ((long long)y + (long long)P.n[1] * z);
+  return (long long)x + (long long)P.px * ((long long)y + (long long)P.n[1] * z);
 }
 
 // True when the tile and its one-cell halo lie inside the domain on every
@@ -861,40 +862,48 @@ __global__ void __launch_bounds__(Geo<D, Real>::NT)
 
 // ------------------------------------------------------------------ state I/O
 // phi from N exchange planes (liquid first) to the stored planes.
+// Offset of logical cell x (x fastest, no padding) in the padded layout.
+__device__ __forceinline__ long long padded(long long x, int nx, int px) {
+  return (x % nx) + (long long)px * (x / nx);
+}
+
 template <int NP, class Real, class In>
-__global__ void load_phi_kernel(long long cells, long long plane, const In* __restrict__ src,
-                                Real* __restrict__ dst) {
+__global__ void load_phi_kernel(long long cells, int nx, int px, long long plane,
+                                const In* __restrict__ src, Real* __restrict__ dst) {
   const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (x >= cells) return;
+  const long long o = padded(x, nx, px);
   if (NP == 2) {
-    dst[x] = Real(src[cells + x]);
+    dst[o] = Real(src[cells + x]);
   } else {
 #pragma unroll
-    for (int a = 0; a < NP; ++a) dst[a * plane + x] = Real(src[a * cells + x]);
+    for (int a = 0; a < NP; ++a) dst[a * plane + o] = Real(src[a * cells + x]);
   }
 }
 
 template <int NC, class Real, class In>
-__global__ void load_mu_kernel(long long cells, long long plane, const In* __restrict__ src,
-                               Real* __restrict__ dst) {
+__global__ void load_mu_kernel(long long cells, int nx, int px, long long plane,
+                               const In* __restrict__ src, Real* __restrict__ dst) {
   const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (x >= cells) return;
+  const long long o = padded(x, nx, px);
 #pragma unroll
-  for (int i = 0; i < NC; ++i) dst[i * plane + x] = Real(src[i * cells + x]);
+  for (int i = 0; i < NC; ++i) dst[i * plane + o] = Real(src[i * cells + x]);
 }
 
 // f (full populations, or the fluid at rest when src is null) to deviations.
 template <int Q, class Store, class In>
-__global__ void load_f_kernel(long long cells, long long plane, const In* __restrict__ src,
-                              Store* __restrict__ dst) {
+__global__ void load_f_kernel(long long cells, int nx, int px, long long plane,
+                              const In* __restrict__ src, Store* __restrict__ dst) {
   using Lat = Lattice<Q>;
   const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (x >= cells) return;
+  const long long o = padded(x, nx, px);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
     using R = typename std::conditional<std::is_same<Store, double>::value, double, float>::type;
     const R d = src ? R(src[k * cells + x]) - R(Lat::w(k)) : R(0);
-    dst[k * plane + x] = Codec<Store>::put(d);
+    dst[k * plane + o] = Codec<Store>::put(d);
   }
 }
 
@@ -916,10 +925,11 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
   const int gx = (int)(x % P.n[0]);
   const int gy = (int)((x / P.n[0]) % P.n[1]);
   const int gz = (int)(x / ((long long)P.n[0] * P.n[1]));
+  const long long o = cell_index<D>(P, gx, gy, gz);
   Real p[NP], mu[NC];
-  load_phases<NP>(phi, x, P.plane, p);
+  load_phases<NP>(phi, o, P.plane, p);
 #pragma unroll
-  for (int i = 0; i < NC; ++i) mu[i] = mu_in[i * P.plane + x];
+  for (int i = 0; i < NC; ++i) mu[i] = mu_in[i * P.plane + o];
   if (o_phi)
 #pragma unroll
     for (int a = 0; a < NP; ++a) o_phi[a * cells + x] = Out(p[a]);
@@ -943,7 +953,7 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
   for (int a = 0; a < D; ++a) m[a] = Real(0);
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    const Real dk = Codec<Store>::load(f[k * P.plane + x]);
+    const Real dk = Codec<Store>::load(f[k * P.plane + o]);
     drho += dk;
 #pragma unroll
     for (int a = 0; a < D; ++a)
@@ -974,6 +984,7 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
 // a fixed-order block reduction (see gpflbm_invariants in gpflbm.h).
 struct InvParams {
   long long cells, plane;
+  int nx, px;
   double ceq[4][2];
   double inv2A[4];
 };
@@ -1012,19 +1023,20 @@ __global__ void __launch_bounds__(kRedThreads)
   for (int j = 0; j < NV; ++j) acc[j] = 0.0;
   const long long stride = (long long)gridDim.x * kRedThreads;
   for (long long x = blockIdx.x * (long long)kRedThreads + threadIdx.x; x < P.cells; x += stride) {
+    const long long o = padded(x, P.nx, P.px);
     double p[NP], m[NC];
     if (NP == 2) {
-      p[1] = (double)phi[x];
+      p[1] = (double)phi[o];
       p[0] = __dsub_rn(1.0, p[1]);
     } else {
 #pragma unroll
-      for (int a = 0; a < NP; ++a) p[a] = (double)phi[a * P.plane + x];
+      for (int a = 0; a < NP; ++a) p[a] = (double)phi[a * P.plane + o];
     }
 #pragma unroll
-    for (int i = 0; i < NC; ++i) m[i] = (double)mu[i * P.plane + x];
+    for (int i = 0; i < NC; ++i) m[i] = (double)mu[i * P.plane + o];
     double dm = 0.0;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) dm = __dadd_rn(dm, (double)Codec<Store>::load(f[k * P.plane + x]));
+    for (int k = 0; k < Q; ++k) dm = __dadd_rn(dm, (double)Codec<Store>::load(f[k * P.plane + o]));
     double h[NP];
 #pragma unroll
     for (int a = 0; a < NP; ++a) h[a] = h_exact<NP>(p, a);

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "gpflbm_kernels.cuh"
+#include "step2d.cuh"
 
 namespace gpflbm {
 
@@ -18,6 +19,7 @@ struct StepIO {
   void* f_out;
   const double* clock_in;
   double* clock_out;
+  int* err;  // device error word (bounded waits)
 };
 
 struct FieldsIO {
@@ -38,6 +40,7 @@ struct Ops {
   int D, NP, NC, Q;
   size_t real_size, store_size;
   int stored_phi_planes;
+  int fused;  // 1: one launch per step (2D), 0: phase-field + transport launches (3D)
   // opts the step kernels in to their dynamic shared memory (once per process)
   cudaError_t (*configure)();
   // one time step S^n -> S^{n+1}
@@ -69,14 +72,29 @@ struct Impl {
                 (P.n[2] + G::TZ - 1) / G::TZ);
   }
 
+  using SZ = Step2D<NP, NC, Real, Store>;
+
   static cudaError_t configure() {
+    if (D == 2)
+      return cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
     cudaError_t e = allow_smem(phase_field_kernel<D, NP, NC, Real>, PfSmem<D, NP, Real>::bytes);
     if (e == cudaSuccess)
       e = allow_smem(mu_lbm_kernel<D, NP, NC, Real, Store>, MlSmem<D, NP, NC, Real>::bytes);
     return e;
   }
 
+  static cudaError_t step_fused(const void* params, const StepIO& io, cudaStream_t s) {
+    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+    const dim3 grid((P.n[0] + SZ::OX - 1) / SZ::OX, (P.n[1] + SZ::OY - 1) / SZ::OY);
+    const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
+                          io.f_in,   io.f_out,   io.clock_in, io.clock_out};
+    step2d_kernel<NP, NC, Real, Store><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+    return cudaGetLastError();
+  }
+
   static cudaError_t step_pf(const void* params, const StepIO& io, cudaStream_t s) {
+    if (D == 2) return step_fused(params, io, s);
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     phase_field_kernel<D, NP, NC, Real><<<tiles(P), G::NT, PfSmem<D, NP, Real>::bytes, s>>>(
         P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.mu_in),
@@ -85,6 +103,7 @@ struct Impl {
   }
 
   static cudaError_t step_transport(const void* params, const StepIO& io, cudaStream_t s) {
+    if (D == 2) return cudaSuccess;  // the fused launch did the whole step
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     mu_lbm_kernel<D, NP, NC, Real, Store><<<tiles(P), G::NT, MlSmem<D, NP, NC, Real>::bytes, s>>>(
         P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.phi_out),
@@ -106,12 +125,12 @@ struct Impl {
     const unsigned blocks = (unsigned)((cells + threads - 1) / threads);
     if (src_phi)
       load_phi_kernel<NP, Real, Real><<<blocks, threads, 0, s>>>(
-          cells, P.plane, static_cast<const Real*>(src_phi), static_cast<Real*>(phi));
+          cells, P.n[0], P.px, P.plane, static_cast<const Real*>(src_phi), static_cast<Real*>(phi));
     if (src_mu)
       load_mu_kernel<NC, Real, Real><<<blocks, threads, 0, s>>>(
-          cells, P.plane, static_cast<const Real*>(src_mu), static_cast<Real*>(mu));
+          cells, P.n[0], P.px, P.plane, static_cast<const Real*>(src_mu), static_cast<Real*>(mu));
     load_f_kernel<Q, Store, Real><<<blocks, threads, 0, s>>>(
-        cells, P.plane, static_cast<const Real*>(src_f), static_cast<Store*>(f));
+        cells, P.n[0], P.px, P.plane, static_cast<const Real*>(src_f), static_cast<Store*>(f));
     return cudaGetLastError();
   }
 
@@ -145,6 +164,7 @@ struct Impl {
                             sizeof(Real),
                             sizeof(Store),
                             PhiStore<NP>::NS,
+                            D == 2 ? 1 : 0,
                             &Impl::configure,
                             &Impl::step,
                             &Impl::step_pf,
