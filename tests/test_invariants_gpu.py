@@ -1,0 +1,145 @@
+"""Global conservation reductions on the GPU (FP64, fixed order).
+
+Reading of "bit-for-bit conservation invariants": the FP64 totals come from a
+fixed-order reduction, so they are identical from run to run, and they equal
+bit for bit a re-summation of the downloaded state on the host in the order
+documented for gpflbm_invariants (include/gpflbm.h).  Drift over 100 steps is
+bounded by the arithmetic: 1e-12 relative in FP64, 1e-6 in FP32, 1e-4 with
+16-bit population storage.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2608_26908_gb300 import gpflbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+THREADS, MAX_BLOCKS = 256, 608
+
+
+def _h_exact(p, a):
+    """h_a in FP64 in the kernel's operation order (no fused multiply-add)."""
+    N = len(p)
+    s = np.zeros_like(p[0])
+    for b in range(N):
+        for g in range(b + 1, N):
+            if b != a and g != a:
+                s = s + p[b] * p[g]
+    t1 = (p[a] * p[a]) * (3.0 - 2.0 * p[a])
+    t2 = (2.0 * p[a]) * s
+    return t1 + t2
+
+
+def host_invariants(sim, sc):
+    """Re-sum the downloaded state in the documented order."""
+    NP, NC, cells = sc["n_phases"], sc["n_solutes"], sim.cells
+    fld = sim.fields(("phi", "mu"))
+    dev = sim.deviations().astype(np.float64)
+    phi = fld["phi"].astype(np.float64)
+    if NP == 2:  # only phi_1 is stored; phi_0 = 1 - phi_1 in FP64
+        p = [1.0 - phi[1], phi[1]]
+    else:
+        p = [phi[a] for a in range(NP)]
+    mu = fld["mu"].astype(np.float64)
+    pr = sc["params"]
+    vals = []
+    dm = np.zeros(cells)
+    for k in range(dev.shape[0]):
+        dm = dm + dev[k]
+    vals.append(dm)
+    h = [_h_exact(p, a) for a in range(NP)]
+    for i in range(NC):
+        c = np.zeros(cells)
+        for a in range(NP):
+            c = c + h[a] * (pr["ceq"][a][i] + mu[i] * (1.0 / (2.0 * pr["A"][a])))
+        vals.append(c)
+    sol = np.zeros(cells)
+    for a in range(1, NP):
+        sol = sol + h[a]
+    vals.append(sol)
+    blocks = min((cells + THREADS - 1) // THREADS, MAX_BLOCKS)
+    stride = blocks * THREADS
+    out = []
+    for v in vals:
+        pad = np.zeros(((cells + stride - 1) // stride) * stride)
+        pad[:cells] = v
+        lanes = pad.reshape(-1, stride)           # rows: j = 0, 1, ...
+        acc = np.zeros(stride)
+        for row in lanes:                          # thread-sequential adds
+            acc = acc + row
+        acc = acc.reshape(blocks, THREADS // 32, 32)
+        for off in (16, 8, 4, 2, 1):               # xor butterfly
+            idx = np.arange(32) ^ off
+            acc = acc + acc[:, :, idx]
+        w = acc[:, :, 0]                           # lane 0 of each warp
+        bsum = w[:, 0].copy()
+        for j in range(1, THREADS // 32):
+            bsum = bsum + w[:, j]
+        tot = bsum[0]
+        for b in range(1, blocks):
+            tot = tot + bsum[b]
+        out.append(tot)
+    mass = out[0] + float(cells)
+    return mass, np.array(out[1:1 + NC]), out[1 + NC] / cells
+
+
+CASES = [("dendrite2d", dict(), "fp64"), ("eutectic2d", dict(nx=200, ny=90), "fp32"),
+         ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp32"),
+         ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp32_f16"),
+         ("eutectic3d", dict(nx=36, ny=34, nz=40), "fp32")]
+
+
+@pytest.mark.parametrize("name,size,prec", CASES)
+def test_invariants_match_host_resummation_bit_for_bit(name, size, prec):
+    sc = inputs.scenario(name, precision=prec, **size)
+    if name == "eutectic3d":
+        sc["init"]["height"] = 12
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0)
+    sim.step(37)
+    m1, s1, fr1, st = sim.invariants()
+    m2, s2, fr2, _ = sim.invariants()
+    assert (m1, tuple(s1), fr1) == (m2, tuple(s2), fr2)  # identical run to run
+    hm, hs, hf = host_invariants(sim, sc)
+    assert m1 == hm
+    assert tuple(s1) == tuple(hs)
+    assert fr1 == hf
+
+
+@pytest.mark.parametrize("name,size,prec", CASES)
+def test_conservation_drift_over_100_steps(name, size, prec):
+    sc = inputs.scenario(name, precision=prec, **size)
+    if name == "eutectic3d":
+        sc["init"]["height"] = 12
+    sc["params"]["gbeta_c"] = [2e-3, 1e-3]  # stronger flow than the default
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0)
+    m0, s0, _, _ = sim.invariants()
+    sim.step(100)
+    m1, s1, _, _ = sim.invariants()
+    bound = {"fp64": 1e-12, "fp32": 1e-6, "fp32_f16": 1e-4, "fp32_bf16": 1e-4}[prec]
+    assert abs(m1 - m0) / m0 <= bound
+    np.testing.assert_allclose(s1, s0, rtol=bound)
+    # and they agree with the oracle's totals after the same 100 steps
+    f0 = oracle.rest_populations(sc)
+    phi, mu, f = oracle.run(sc, phi0, mu0, f0, 100)
+    om, os_, of = oracle.invariants(sc, phi, mu, f)
+    assert abs(m1 - om) / om <= bound
+    np.testing.assert_allclose(s1, os_, rtol=max(bound, 1e-6))
+
+
+def test_nonfinite_state_is_reported():
+    sc = inputs.scenario("eutectic2d", nx=64, ny=40)
+    phi0, mu0 = inputs.initial_state(sc)
+    mu0 = mu0.copy()
+    mu0[123] = np.nan
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0)
+    _, _, _, st = sim.invariants(allow_nonfinite=True)
+    assert st == gpflbm.ERR_NONFINITE
+    sim.set_state(*inputs.initial_state(sc))
+    _, _, _, st = sim.invariants()
+    assert st == gpflbm.OK
