@@ -173,6 +173,23 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
 gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double* solid_frac,
                                 void* stream);
 
+/* The totals of gpflbm_invariants for callers that cannot allocate device
+ * memory when they ask for them (device memory held by another framework's
+ * caching allocator, or a monitoring hook that must not call the allocator
+ * during a run).  The paper has no counterpart: this is a library facility.
+ * The reduction scratch is a fixed 80 KB device array inside the library
+ * (one per GPU that loads it, kept until the process exits), not the
+ * handle's workspace; nothing is allocated.  Limit: grids of at most
+ * 16,777,216 cells (larger ones return GPFLBM_ERR_ARG with a message).  The
+ * totals are summed in blocks of up to 8192 cells, in a different order than
+ * gpflbm_invariants, so they agree with it to FP64 rounding, not bit for
+ * bit.  The first call on a device looks the array up (with that device
+ * current) and should come before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU race.  Synchronises `stream`;
+ * outputs and GPFLBM_ERR_NONFINITE as for gpflbm_invariants. */
+gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, double* solute,
+                                        double* solid_frac, void* stream);
+
 /* Step counter of the current state (the t of T(v, t)). */
 gpflbm_status gpflbm_time(gpflbm_t h, long long* t);
 

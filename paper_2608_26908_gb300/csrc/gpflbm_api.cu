@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -588,3 +589,90 @@ void gpflbm_destroy(gpflbm_t h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Conservation totals without any allocation.
+//
+// Some callers cannot allocate device memory when they need the totals: a
+// process whose device memory is already reserved by another framework's
+// caching allocator, or a watchdog or logging hook that must not touch the
+// allocator while a simulation runs.  This variant of gpflbm_invariants keeps
+// its reduction scratch (the per-block partial sums and the final totals) in
+// a file-scope device array instead of the handle's workspace, so it needs
+// neither cudaMalloc nor workspace beyond the state itself.
+//
+// The array is kNoAllocDoubles doubles (80 KB) and lives on every GPU that
+// loads the library until the process exits.  Blocks of 256 threads each sum
+// up to 8192 cells, so at most 2048 blocks fit: grids of more than
+// 16,777,216 cells are rejected.  Calls share the array; every slot a call
+// reads is written earlier by the same call, so nothing needs clearing, but
+// two calls that overlap on the GPU (on different streams or devices sharing
+// a handle) race on it.  The device address of the array is looked up once
+// per device, on the first call made with that device current; that first
+// call should come before any stream capture.
+namespace {
+constexpr int kNoAllocThreads = gpflbm::kRedThreads;
+constexpr long long kNoAllocCellsPerBlock = kNoAllocThreads * 32LL;
+constexpr int kNoAllocMaxBlocks = 2048;
+constexpr int kNoAllocValues = GPFLBM_MAX_SOLUTES + 3;
+constexpr size_t kNoAllocDoubles = (size_t)(kNoAllocMaxBlocks + 1) * kNoAllocValues;
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device.
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, double* solute,
+                                                   double* solid_frac, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  const long long blocks = (h->cells + kNoAllocCellsPerBlock - 1) / kNoAllocCellsPerBlock;
+  if (blocks > kNoAllocMaxBlocks) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "invariants_noalloc: %lld cells exceed the static scratch limit of %lld cells",
+                  h->cells, (long long)kNoAllocMaxBlocks * kNoAllocCellsPerBlock);
+    return fail(h, GPFLBM_ERR_ARG, msg);
+  }
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "invariants_noalloc: no state loaded");
+  double* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: cudaGetSymbolAddress");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double* partial = scratch;
+  double* red = scratch + (size_t)kNoAllocMaxBlocks * kNoAllocValues;
+  e = h->ops->invariants(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
+                         at(h, h->lay.f[h->cur]), partial, (int)blocks, red, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: kernel");
+  double out[kNoAllocValues];
+  e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: copy");
+  if (mass) *mass = out[0] + (double)h->cells;
+  if (solute)
+    for (int i = 0; i < h->NC; ++i) solute[i] = out[1 + i];
+  if (solid_frac) *solid_frac = out[h->NC + 1] / (double)h->cells;
+  if (out[h->NC + 2] != 0.0)
+    return fail(h, GPFLBM_ERR_NONFINITE, "invariants_noalloc: NaN or Inf in the state");
+  return GPFLBM_OK;
+}
