@@ -7,6 +7,7 @@
 
 #include "gpflbm_kernels.cuh"
 #include "step2d.cuh"
+#include "step3d.cuh"
 
 namespace gpflbm {
 
@@ -73,28 +74,35 @@ struct Impl {
   }
 
   using SZ = Step2D<NP, NC, Real, Store>;
+  using S3 = Step3D<NP, NC, Real, Store>;
 
   static cudaError_t configure() {
     if (D == 2)
       return cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
-    cudaError_t e = allow_smem(phase_field_kernel<D, NP, NC, Real>, PfSmem<D, NP, Real>::bytes);
-    if (e == cudaSuccess)
-      e = allow_smem(mu_lbm_kernel<D, NP, NC, Real, Store>, MlSmem<D, NP, NC, Real>::bytes);
-    return e;
+    return cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
   }
 
   static cudaError_t step_fused(const void* params, const StepIO& io, cudaStream_t s) {
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
-    const dim3 grid((P.n[0] + SZ::OX - 1) / SZ::OX, (P.n[1] + SZ::OY - 1) / SZ::OY);
-    const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
-                          io.f_in,   io.f_out,   io.clock_in, io.clock_out};
-    step2d_kernel<NP, NC, Real, Store><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+    if (D == 2) {
+      const dim3 grid((P.n[0] + SZ::OX - 1) / SZ::OX, (P.n[1] + SZ::OY - 1) / SZ::OY);
+      const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
+                            io.f_in,   io.f_out,   io.clock_in, io.clock_out};
+      step2d_kernel<NP, NC, Real, Store><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+    } else {
+      const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
+                      (P.n[2] + S3::ZS - 1) / S3::ZS);
+      const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
+                            io.f_in,   io.f_out,   io.clock_in, io.clock_out};
+      step3d_kernel<NP, NC, Real, Store><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+    }
     return cudaGetLastError();
   }
 
   static cudaError_t step_pf(const void* params, const StepIO& io, cudaStream_t s) {
-    if (D == 2) return step_fused(params, io, s);
+    if (D == 2 || D == 3) return step_fused(params, io, s);
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     phase_field_kernel<D, NP, NC, Real><<<tiles(P), G::NT, PfSmem<D, NP, Real>::bytes, s>>>(
         P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.mu_in),
@@ -103,7 +111,7 @@ struct Impl {
   }
 
   static cudaError_t step_transport(const void* params, const StepIO& io, cudaStream_t s) {
-    if (D == 2) return cudaSuccess;  // the fused launch did the whole step
+    if (D == 2 || D == 3) return cudaSuccess;  // the fused launch did the whole step
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     mu_lbm_kernel<D, NP, NC, Real, Store><<<tiles(P), G::NT, MlSmem<D, NP, NC, Real>::bytes, s>>>(
         P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.phi_out),
@@ -164,7 +172,7 @@ struct Impl {
                             sizeof(Real),
                             sizeof(Store),
                             PhiStore<NP>::NS,
-                            D == 2 ? 1 : 0,
+                            1,
                             &Impl::configure,
                             &Impl::step,
                             &Impl::step_pf,

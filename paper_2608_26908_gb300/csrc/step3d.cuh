@@ -1,0 +1,594 @@
+// Fused 3D step kernel for sm_103a: one launch advances the grid by one time
+// step (Algorithm 1: phase field, chemical potential, lattice Boltzmann).
+//
+// A CTA owns an xy tile and a z segment of ZS planes.  It runs one thread per
+// cell of the tile's one-cell xy halo region ("R1", BX x BY columns) and
+// marches up the segment plane by plane, keeping the planes each stage
+// still needs in shared-memory rings.  At lead plane L it
+//   A. reads phi^n of plane L (its column and, for the first threads, the
+//      ring of columns around R1) and records which phases are present;
+//   B. reads mu^n and f^n of plane C = L-1, forms rho, the implicit-drag
+//      velocity U and the forces, and, for the tile's inner columns of the
+//      owned planes, collides the populations (BGK + Guo) and pushes them to
+//      x + c_k of f^{n+1} in global memory (halfway bounce-back at walls);
+//   C. updates the phase field of plane C where phases mix (face fluxes,
+//      Lambda over the present phases, Gibbs-simplex projection);
+//   D. forms the solute fluxes of plane M = L-2 (in-plane faces and the face
+//      to plane M+1; the face to M-1 comes from the previous plane) and
+//      writes mu^{n+1}, phi^{n+1} of plane M.
+// Pushing instead of pulling means each cell is collided once, by the CTA
+// that owns it, and no collided populations are staged.
+#pragma once
+
+#include "gpflbm_kernels.cuh"
+
+namespace gpflbm {
+
+template <class Real>
+struct Block3D;
+template <>
+struct Block3D<float> {
+  static constexpr int BX = 32, BY = 16, ZS = 16;
+};
+template <>
+struct Block3D<double> {
+  static constexpr int BX = 32, BY = 8, ZS = 16;
+};
+
+template <int NP, int NC, class Real, class Store>
+struct Step3D {
+  static constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZS;
+  static constexpr int NT = BX * BY, Q = 19;
+  static constexpr int NS = PhiStore<NP>::NS;
+  static constexpr int OX = BX - 2, OY = BY - 2;
+  static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;
+  static constexpr int RING = C2 - NT;
+  static constexpr int PFX = (BX + 1) * BY, PFY = BX * (BY + 1);  // in-plane phase-field faces
+  static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
+  static constexpr size_t phi = 0;                                  // 4 planes x NS x C2
+  static constexpr size_t mask = al(phi + sizeof(Real) * 4 * NS * C2);  // 3 planes x C2
+  static constexpr size_t pn = al(mask + 3 * C2);                   // 3 planes x NP x NT
+  static constexpr size_t u = al(pn + sizeof(Real) * 3 * NP * NT);   // 2 planes x 3 x NT
+  static constexpr size_t mu = al(u + sizeof(Real) * 2 * 3 * NT);    // 2 planes x NC x NT
+  static constexpr size_t hl = al(mu + sizeof(Real) * 2 * NC * NT);  // 2 planes x NT
+  static constexpr size_t chg = al(hl + sizeof(Real) * 2 * NT);      // 2 planes x NT bytes
+  static constexpr size_t flux = al(chg + 2 * NT);                   // PF or solute in-plane faces
+  static constexpr size_t flux_n =
+      NP * (PFX + PFY) > 2 * NC * NT ? NP * (PFX + PFY) : 2 * NC * NT;
+  static constexpr size_t bytes = al(flux + sizeof(Real) * flux_n);
+};
+
+struct Step3DIO {
+  const void* phi_in;
+  void* phi_out;
+  const void* mu_in;
+  void* mu_out;
+  const void* f_in;
+  void* f_out;
+  const double* clock_in;
+  double* clock_out;
+};
+
+template <int NP, int NC, class Real, class Store>
+__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
+    step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
+  using S = Step3D<NP, NC, Real, Store>;
+  using Lat = Lattice<19>;
+  constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = 19;
+  constexpr int W2 = S::W2, H2 = S::H2, C2 = S::C2, NS = S::NS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Real* s_phi = reinterpret_cast<Real*>(smem + S::phi);
+  unsigned char* s_mask = smem + S::mask;
+  Real* s_pn = reinterpret_cast<Real*>(smem + S::pn);
+  Real* s_u = reinterpret_cast<Real*>(smem + S::u);
+  Real* s_mu = reinterpret_cast<Real*>(smem + S::mu);
+  Real* s_hl = reinterpret_cast<Real*>(smem + S::hl);
+  unsigned char* s_chg = smem + S::chg;
+  Real* s_flux = reinterpret_cast<Real*>(smem + S::flux);
+
+  const Real* __restrict__ phi_in = static_cast<const Real*>(io.phi_in);
+  const Real* __restrict__ mu_in = static_cast<const Real*>(io.mu_in);
+  const Store* __restrict__ f_in = static_cast<const Store*>(io.f_in);
+  Real* __restrict__ phi_out = static_cast<Real*>(io.phi_out);
+  Real* __restrict__ mu_out = static_cast<Real*>(io.mu_out);
+  Store* __restrict__ f_out = static_cast<Store*>(io.f_out);
+
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = tid / BX;
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2], px = P.px;
+  const long long zst = (long long)px * ny;  // plane stride
+  const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY, z0 = blockIdx.z * ZS;
+  const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
+  const bool inner_xy = x0 >= 2 && x0 - 2 + W2 <= nx && y0 >= 2 && y0 - 2 + H2 <= ny;
+  const int fx = inner_xy ? gx : fold_axis(P, gx, 0);
+  const int fy = inner_xy ? gy : fold_axis(P, gy, 1);
+  const long long gxy = (long long)fy * px + fx;
+  const int r2 = (ty + 1) * W2 + tx + 1;
+  // inner columns of the tile write the tile's cells
+  const bool owner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && gx < nx && gy < ny;
+  const double t_now = io.clock_in[0];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
+  const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
+  const Real omega = Real(1) - P.inv_tau_f;
+
+  int rx = 0, ry = 0;  // ring column held by threads tid < RING
+  long long gring = 0;
+  if (tid < S::RING) {
+    if (tid < W2) {
+      rx = tid;
+      ry = 0;
+    } else if (tid < 2 * W2) {
+      rx = tid - W2;
+      ry = H2 - 1;
+    } else if (tid < 2 * W2 + H2 - 2) {
+      rx = 0;
+      ry = tid - 2 * W2 + 1;
+    } else {
+      rx = W2 - 1;
+      ry = tid - 2 * W2 - (H2 - 2) + 1;
+    }
+    const int qx = inner_xy ? x0 - 2 + rx : fold_axis(P, x0 - 2 + rx, 0);
+    const int qy = inner_xy ? y0 - 2 + ry : fold_axis(P, y0 - 2 + ry, 1);
+    gring = (long long)qy * px + qx;
+  }
+  const int rr2 = ry * W2 + rx;
+
+  auto slot4 = [](int p) { return p & 3; };
+  auto slot3 = [](int p) { return (p + 3) % 3; };
+  auto slot2 = [](int p) { return p & 1; };
+  // phase a of plane p (ring of four) at R1-plus-ring index i
+  auto PH = [&](int p, int a, int i) -> Real {
+    const Real* b = s_phi + slot4(p) * NS * C2;
+    if (NP == 2) return a == 0 ? Real(1) - b[i] : b[i];
+    return b[a * C2 + i];
+  };
+  auto MK = [&](int p, int i) -> unsigned { return s_mask[slot3(p) * C2 + i]; };
+
+  // phase-field z-face fluxes of this column: (C-1, C) carried, (C, C+1) new
+  Real pfz_lo[NP], pfz_hi[NP];
+  // solute z-face fluxes of this column: (M-1, M) carried, (M, M+1) new
+  Real mz_lo[NC], mz_hi[NC];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) pfz_lo[a] = pfz_hi[a] = Real(0);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i] = Real(0);
+
+  // face flux of the phase field between cells A and B (R1-plus-ring indices
+  // in planes pa, pb); normal axis d; t1, t2 the transverse steps (in-plane
+  // index offsets or plane offsets); returns the d-th component of
+  // -sum_{b != a} gamma_ab phi_b dA/dq(q_ab) for every phase
+  auto pf_flux = [&](int pa, int ia, int pb, int ib, int d, bool closed, Real* fl) {
+#pragma unroll
+    for (int a = 0; a < NP; ++a) fl[a] = Real(0);
+    // the cells the stencil reads
+    unsigned grp;
+    Real pf[NP], g3[NP][3];
+    if (d == 2) {
+      grp = MK(pa, ia) | MK(pb, ib) | MK(pa, ia + 1) | MK(pb, ib + 1) | MK(pa, ia - 1) |
+            MK(pb, ib - 1) | MK(pa, ia + W2) | MK(pb, ib + W2) | MK(pa, ia - W2) | MK(pb, ib - W2);
+    } else {
+      const int st = d == 0 ? W2 : 1;
+      grp = MK(pa, ia) | MK(pb, ib) | MK(pa, ia + st) | MK(pb, ib + st) | MK(pa, ia - st) |
+            MK(pb, ib - st) | MK(pa - 1, ia) | MK(pb - 1, ib) | MK(pa + 1, ia) | MK(pb + 1, ib);
+    }
+    if (__popc(grp) < 2 || closed) return;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const Real va = PH(pa, a, ia), vb = PH(pb, a, ib);
+      pf[a] = Real(0.5) * (va + vb);
+      if (d == 2) {
+        g3[a][2] = vb - va;
+        g3[a][0] = Real(0.25) * (PH(pa, a, ia + 1) + PH(pb, a, ib + 1) - PH(pa, a, ia - 1) - PH(pb, a, ib - 1));
+        g3[a][1] = Real(0.25) * (PH(pa, a, ia + W2) + PH(pb, a, ib + W2) - PH(pa, a, ia - W2) - PH(pb, a, ib - W2));
+      } else {
+        const int st = d == 0 ? W2 : 1;  // the other in-plane axis
+        g3[a][d] = vb - va;
+        g3[a][1 - d] = Real(0.25) * (PH(pa, a, ia + st) + PH(pb, a, ib + st) - PH(pa, a, ia - st) - PH(pb, a, ib - st));
+        g3[a][2] = Real(0.25) * (PH(pa + 1, a, ia) + PH(pb + 1, a, ib) - PH(pa - 1, a, ia) - PH(pb - 1, a, ib));
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NP; ++a)
+#pragma unroll
+      for (int b = a + 1; b < NP; ++b) {
+        const Real gab = P.gamma[a][b];
+        if (gab == Real(0)) continue;
+        Real q[3];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) q[t] = pf[a] * g3[b][t] - pf[b] * g3[a][t];
+        const Real v = dAdq<3>(q, P.delta[a][b], P.q_floor, d);
+        fl[a] -= gab * pf[b] * v;
+        fl[b] += gab * pf[a] * v;
+      }
+  };
+
+  const int L0 = z0 - 2, L1 = z0 + ZS + 1;
+  for (int L = L0; L <= L1; ++L) {
+    const int C = L - 1, M = L - 2;
+    // A. phi^n of plane L
+    {
+      const long long zo = (long long)fold_axis(P, L, 2) * zst;
+      Real* b = s_phi + slot4(L) * NS * C2;
+      unsigned m = 0;
+      Real v[NP];
+      load_phases<NP>(phi_in, zo + gxy, P.plane, v);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        if (NP != 2 || a == 1) b[(NP == 2 ? 0 : a) * C2 + r2] = v[a];
+        if (v[a] > Real(0)) m |= 1u << a;
+      }
+      s_mask[slot3(L) * C2 + r2] = (unsigned char)m;
+      if (tid < S::RING) {
+        load_phases<NP>(phi_in, zo + gring, P.plane, v);
+        m = 0;
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          if (NP != 2 || a == 1) b[(NP == 2 ? 0 : a) * C2 + rr2] = v[a];
+          if (v[a] > Real(0)) m |= 1u << a;
+        }
+        s_mask[slot3(L) * C2 + rr2] = (unsigned char)m;
+      }
+    }
+    // B. moments, U and (owned planes, inner columns) collision + push, plane C
+    const bool doC = C >= z0 - 1 && C <= z0 + ZS;
+    if (doC) {
+      const int fzc = fold_axis(P, C, 2);
+      const long long g = (long long)fzc * zst + gxy;
+      const bool obs = obstacle(P, fx, fy, fzc);
+      Real mu[NC];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        mu[i] = mu_in[i * P.plane + g];
+        s_mu[(slot2(C) * NC + i) * NT + tid] = mu[i];
+      }
+      Real dk[Q];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(f_in[k * P.plane + g]);
+      Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        drho += dk[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (Lat::c(k, a) != 0) m3[a] += Real(Lat::c(k, a)) * dk[k];
+      }
+      const Real rho = Real(1) + drho;
+      // phi_l^n of this cell (plane C was read as plane L one step earlier)
+      const Real phl = obs ? Real(0) : PH(C, 0, r2);
+      const Real sl = Real(1) - phl;
+      const Real kappa = P.kappa0 * sl * sl;
+      Real drive = P.gbeta_T * (theta_base + P.G * Real(fzc) + P.dT_ref);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
+      const Real FB = rho * phl * drive;
+      const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
+      Real u[3], F[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const Real fb = a == 2 ? FB : Real(0);
+        u[a] = (m3[a] + Real(0.5) * fb) * inv;
+        F[a] = fb - rho * kappa * u[a];
+        s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
+      }
+      if (owner && C >= z0 && C < z0 + ZS && C < nz) {
+        const Real A0 = drho - Real(1.5) * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const Real B0 = Real(-3) * P.force_pre * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]);
+        const bool inner_z = C >= 1 && C + 1 < nz;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          const int cx = Lat::c(k, 0), cy = Lat::c(k, 1), cz = Lat::c(k, 2);
+          const Real cu = Real(cx) * u[0] + Real(cy) * u[1] + Real(cz) * u[2];
+          const Real cF = Real(cx) * F[0] + Real(cy) * F[1] + Real(cz) * F[2];
+          const Real wk = Real(Lat::w(k));
+          const Real deq = wk * (A0 + rho * cu * (Real(3) + Real(4.5) * cu));
+          const Real Gk = wk * (B0 + P.force_pre * cF * (Real(3) + Real(9) * cu));
+          const Store v = Codec<Store>::put(omega * dk[k] + P.inv_tau_f * deq + Gk);
+          // push to x + c_k; across a wall the population returns reversed
+          int tx_ = gx + cx, ty_ = gy + cy, tz_ = C + cz, kk = k;
+          long long dst;
+          if (inner_xy && inner_z) {
+            dst = (long long)tz_ * zst + (long long)ty_ * px + tx_;
+          } else {
+            const bool bx = P.bc[0] == kWall && (tx_ < 0 || tx_ >= nx);
+            const bool by = P.bc[1] == kWall && (ty_ < 0 || ty_ >= ny);
+            const bool bz = P.bc[2] == kWall && (tz_ < 0 || tz_ >= nz);
+            if (bx || by || bz) {
+              kk = Lat::opp(k);
+              tx_ = gx;
+              ty_ = gy;
+              tz_ = C;
+            } else {
+              tx_ = tx_ < 0 ? tx_ + nx : (tx_ >= nx ? tx_ - nx : tx_);
+              ty_ = ty_ < 0 ? ty_ + ny : (ty_ >= ny ? ty_ - ny : ty_);
+              tz_ = tz_ < 0 ? tz_ + nz : (tz_ >= nz ? tz_ - nz : tz_);
+            }
+            dst = (long long)tz_ * zst + (long long)ty_ * px + tx_;
+          }
+          f_out[kk * P.plane + dst] = v;
+        }
+      }
+    }
+    __syncthreads();
+
+    // C. phase field of plane C where phases mix
+    const bool pfC = C >= z0 - 1 && C <= z0 + ZS;
+    Real out[NP];
+    bool mixed = false, multi = false;
+    unsigned act = 0;
+    if (pfC) {
+      const int fzc = fold_axis(P, C, 2);
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx) act |= MK(C + dz, r2 + dy * W2 + dx);
+      mixed = __popc(act) >= 2;
+      multi = mixed && !obstacle(P, fx, fy, fzc);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) out[a] = PH(C, a, r2);
+    }
+    // A face flux reads cells inside the 3x3x3 neighbourhood of its cell in
+    // plane C, so with no mixed neighbourhood in the plane every face of the
+    // plane (and the z-face above it) is exactly zero.
+    if (!__syncthreads_or(pfC && mixed)) {
+#pragma unroll
+      for (int a = 0; a < NP; ++a) pfz_hi[a] = Real(0);
+    } else {
+      if (pfC) {
+        // in-plane faces of plane C into shared memory
+        Real fl[NP];
+        const bool cx_hi = P.bc[0] == kWall && (gx + 1 == 0 || gx + 1 == nx);
+        pf_flux(C, r2, C, r2 + 1, 0, cx_hi, fl);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + ty * (BX + 1) + tx + 1] = fl[a];
+        if (tx == 0) {
+          const bool cx_lo = P.bc[0] == kWall && (gx == 0 || gx == nx);
+          pf_flux(C, r2 - 1, C, r2, 0, cx_lo, fl);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + ty * (BX + 1)] = fl[a];
+        }
+        const bool cy_hi = P.bc[1] == kWall && (gy + 1 == 0 || gy + 1 == ny);
+        pf_flux(C, r2, C, r2 + W2, 1, cy_hi, fl);
+#pragma unroll
+        for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + S::PFX + (ty + 1) * BX + tx] = fl[a];
+        if (ty == 0) {
+          const bool cy_lo = P.bc[1] == kWall && (gy == 0 || gy == ny);
+          pf_flux(C, r2 - W2, C, r2, 1, cy_lo, fl);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + S::PFX + tx] = fl[a];
+        }
+        // z-faces of this column: (C, C+1), and (C-1, C) on the first plane
+        const bool cz_hi = P.bc[2] == kWall && (C + 1 == 0 || C + 1 == nz);
+        pf_flux(C, r2, C + 1, r2, 2, cz_hi, pfz_hi);
+        if (C == z0 - 1) {
+          const bool cz_lo = P.bc[2] == kWall && (C == 0 || C == nz);
+          pf_flux(C - 1, r2, C, r2, 2, cz_lo, pfz_lo);
+        }
+      }
+      __syncthreads();
+      if (pfC && multi) {
+        Real div[NP], gc[NP][3];
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          const Real* fa = s_flux + a * (S::PFX + S::PFY);
+          div[a] = (fa[ty * (BX + 1) + tx + 1] - fa[ty * (BX + 1) + tx]) +
+                   (fa[S::PFX + (ty + 1) * BX + tx] - fa[S::PFX + ty * BX + tx]) + (pfz_hi[a] - pfz_lo[a]);
+          gc[a][0] = Real(0.5) * (PH(C, a, r2 + 1) - PH(C, a, r2 - 1));
+          gc[a][1] = Real(0.5) * (PH(C, a, r2 + W2) - PH(C, a, r2 - W2));
+          gc[a][2] = Real(0.5) * (PH(C + 1, a, r2) - PH(C - 1, a, r2));
+        }
+        Real ph[NP];
+#pragma unroll
+        for (int a = 0; a < NP; ++a) ph[a] = out[a];
+        Real dadphi[NP];
+#pragma unroll
+        for (int a = 0; a < NP; ++a) dadphi[a] = Real(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a)
+#pragma unroll
+          for (int b = a + 1; b < NP; ++b) {
+            const Real gab = P.gamma[a][b];
+            if (gab == Real(0)) continue;
+            Real q[3], v[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) q[t] = ph[a] * gc[b][t] - ph[b] * gc[a][t];
+            dAdq_vec<3>(q, P.delta[a][b], P.q_floor, v);
+            dadphi[a] += gab * (v[0] * gc[b][0] + v[1] * gc[b][1] + v[2] * gc[b][2]);
+            dadphi[b] -= gab * (v[0] * gc[a][0] + v[1] * gc[a][1] + v[2] * gc[a][2]);
+          }
+        const Real theta = theta_base + P.G * Real(fold_axis(P, C, 2));
+        Real mu[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) mu[i] = s_mu[(slot2(C) * NC + i) * NT + tid];
+        Real psi[NP];
+#pragma unroll
+        for (int b = 0; b < NP; ++b) {
+          Real sv = P.S[b] * theta;
+#pragma unroll
+          for (int i = 0; i < NC; ++i) sv -= mu[i] * mu[i] * P.inv4A[b] + mu[i] * P.ceq[b][i];
+          psi[b] = sv;
+        }
+        Real rate[NP];
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          Real obst = Real(0), drv = Real(0);
+#pragma unroll
+          for (int b = 0; b < NP; ++b) {
+            if (b != a) obst += P.gamma[a][b] * ph[b];
+            drv += psi[b] * interp_dh<NP>(ph, b, a);
+          }
+          rate[a] = P.eps * (div[a] - dadphi[a]) - P.obst * obst - drv;
+        }
+        int na = 0;
+        Real lam = Real(0);
+#pragma unroll
+        for (int a = 0; a < NP; ++a)
+          if (act & (1u << a)) {
+            lam += rate[a];
+            ++na;
+          }
+        lam = lam / Real(na);
+        Real uv[NP];
+        int m = 0;
+#pragma unroll
+        for (int a = 0; a < NP; ++a)
+          if (act & (1u << a)) uv[m++] = ph[a] + P.mob_eps * (rate[a] - lam);
+        if (NP == 2) {
+          Real sv = uv[1];
+          sv = sv < Real(0) ? Real(0) : (sv > Real(1) ? Real(1) : sv);
+          out[1] = sv;
+          out[0] = Real(1) - sv;
+        } else {
+          project_simplex<Real, NP>(uv, m);
+          m = 0;
+#pragma unroll
+          for (int a = 0; a < NP; ++a) out[a] = (act & (1u << a)) ? uv[m++] : Real(0);
+        }
+      }
+    }
+    if (pfC) {
+      bool changed = false;
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        s_pn[(slot3(C) * NP + a) * NT + tid] = out[a];
+        changed = changed || out[a] != PH(C, a, r2);
+      }
+      s_chg[slot2(C) * NT + tid] = changed ? 1 : 0;
+      s_hl[slot2(C) * NT + tid] = interp_h<NP>(out, 0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) pfz_lo[a] = pfz_hi[a];
+    }
+    __syncthreads();
+
+    // D. solute fluxes of plane M and the update of the owned planes
+    const bool doM = M >= z0 - 1 && M <= z0 + ZS - 1;
+    const bool outM = doM && M >= z0 && M < nz;
+    if (doM) {
+      const int fzm = fold_axis(P, M, 2);
+      const bool walls = (P.wall[0] | P.wall[1] | P.wall[2]) != 0;
+      // flux between this cell (plane M) and neighbour nb: d normal axis
+      auto mu_face = [&](int d, int pB, int nbT, int nbR, int gbd, bool obsB, Real* J) {
+        bool closed = (P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d];
+        if (!closed && walls) closed = obstacle(P, fx, fy, fzm) || obsB;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) J[i] = Real(0);
+        if (closed) return;
+        const int pA = M, A = tid, rA = r2;
+        const Real* pnA = s_pn + slot3(pA) * NP * NT;
+        const Real* pnB = s_pn + slot3(pB) * NP * NT;
+        const Real Mf = Real(0.5) * P.M0 * (pnA[A] + pnB[nbT]);  // plane 0 = liquid
+        const Real ua = s_u[(slot2(pA) * 3 + d) * NT + A] * s_hl[slot2(pA) * NT + A];
+        const Real ub = s_u[(slot2(pB) * 3 + d) * NT + nbT] * s_hl[slot2(pB) * NT + nbT];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          const Real ma = s_mu[(slot2(pA) * NC + i) * NT + A], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
+          J[i] = -Mf * (mb - ma) +
+                 Real(0.5) * (ua * (P.ceq[0][i] + ma * P.inv2A[0]) + ub * (P.ceq[0][i] + mb * P.inv2A[0]));
+        }
+        if (P.at_eps != Real(0) && (s_chg[slot2(pA) * NT + A] | s_chg[slot2(pB) * NT + nbT])) {
+          const Real liq = Real(0.5) * (PH(pA, 0, rA) + PH(pB, 0, nbR));
+          Real at[NC];
+#pragma unroll
+          for (int i = 0; i < NC; ++i) at[i] = Real(0);
+#pragma unroll
+          for (int a = 1; a < NP; ++a) {
+            const Real va = PH(pA, a, rA), vb = PH(pB, a, nbR);
+            const Real gn = vb - va;
+            Real t1, t2;
+            if (d == 2) {
+              t1 = Real(0.25) * (PH(pA, a, rA + 1) + PH(pB, a, nbR + 1) - PH(pA, a, rA - 1) - PH(pB, a, nbR - 1));
+              t2 = Real(0.25) * (PH(pA, a, rA + W2) + PH(pB, a, nbR + W2) - PH(pA, a, rA - W2) - PH(pB, a, nbR - W2));
+            } else {
+              const int st = d == 0 ? W2 : 1;
+              t1 = Real(0.25) * (PH(pA, a, rA + st) + PH(pB, a, nbR + st) - PH(pA, a, rA - st) - PH(pB, a, nbR - st));
+              t2 = Real(0.25) * (PH(pA + 1, a, rA) + PH(pB + 1, a, nbR) - PH(pA - 1, a, rA) - PH(pB - 1, a, nbR));
+            }
+            const Real g2 = gn * gn + t1 * t1 + t2 * t2;
+            if (g2 <= Real(1e-12)) continue;
+            const Real nd = liq * gn / sqrt(g2);
+            const Real dphi = Real(0.5) * ((pnA[a * NT + A] - va) + (pnB[a * NT + nbT] - vb));
+            const Real dinv = P.inv2A[0] - P.inv2A[a];
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+              const Real dc = (P.ceq[0][i] - P.ceq[a][i]) +
+                              Real(0.5) * (s_mu[(slot2(pA) * NC + i) * NT + A] + s_mu[(slot2(pB) * NC + i) * NT + nbT]) * dinv;
+              at[i] += dc * dphi * nd;
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < NC; ++i) J[i] -= P.at_eps * at[i];
+        }
+      };
+      // z-face (M, M+1) of this column, for the carry
+      {
+        const int fzb = fold_axis(P, M + 1, 2);
+        mu_face(2, M + 1, tid, r2, M + 1, walls && obstacle(P, fx, fy, fzb), mz_hi);
+      }
+      if (M == z0 - 1) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
+      } else {
+        // in-plane faces of plane M
+        Real J[NC];
+        if (tx < BX - 1) {
+          const bool ob = walls && obstacle(P, fold_axis(P, gx + 1, 0), fy, fzm);
+          mu_face(0, M, tid + 1, r2 + 1, gx + 1, ob, J);
+#pragma unroll
+          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 0) * NT + tid] = J[i];
+        }
+        if (ty < BY - 1) {
+          const bool ob = walls && obstacle(P, fx, fold_axis(P, gy + 1, 1), fzm);
+          mu_face(1, M, tid + BX, r2 + W2, gy + 1, ob, J);
+#pragma unroll
+          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 1) * NT + tid] = J[i];
+        }
+      }
+    }
+    __syncthreads();
+    if (outM && M >= z0 && owner) {
+      const int fzm = M;  // owned planes lie inside the grid
+      const long long g = (long long)fzm * zst + gxy;
+      Real po[NP], pn[NP];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        po[a] = PH(M, a, r2);
+        pn[a] = s_pn[(slot3(M) * NP + a) * NT + tid];
+      }
+#pragma unroll
+      for (int sidx = 0; sidx < NS; ++sidx) phi_out[sidx * P.plane + g] = pn[NP == 2 ? 1 : sidx];
+      if (obstacle(P, fx, fy, fzm)) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = s_mu[(slot2(M) * NC + i) * NT + tid];
+      } else {
+        Real chi = Real(0), hn[NP], ho[NP];
+        const bool changed = s_chg[slot2(M) * NT + tid] != 0;
+#pragma unroll
+        for (int a = 0; a < NP; ++a) {
+          hn[a] = interp_h<NP>(pn, a);
+          ho[a] = changed ? interp_h<NP>(po, a) : hn[a];
+          chi += hn[a] * P.inv2A[a];
+        }
+        const Real ichi = Real(1) / chi;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          const Real* Jx = s_flux + (i * 2 + 0) * NT;
+          const Real* Jy = s_flux + (i * 2 + 1) * NT;
+          const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
+          const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
+          Real src = Real(0);
+#pragma unroll
+          for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu * P.inv2A[a]) * (hn[a] - ho[a]);
+          mu_out[i * P.plane + g] = mu + (-div - src) * ichi;
+        }
+      }
+    }
+    if (doM && M >= z0) {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace gpflbm
