@@ -1,18 +1,12 @@
-// Device code of the coupled Grand-Potential phase-field / lattice-Boltzmann
-// step for sm_103a.  Two kernels per time step, in the order of Algorithm 1:
-//
-//   phase_field_kernel  : phi^n, mu^n            -> phi^{n+1}       (Eq. PhfGrand)
-//   mu_lbm_kernel       : phi^n, phi^{n+1}, mu^n, f^n -> mu^{n+1}, f^{n+1}
-//                         (Eq. conc in flux form; Eq. LBMEq_1 with Eq. f^eq,
-//                          Eq. discreteForce, drag G_D, buoyancy G_B, Eq. rhovel)
-//
-// Both kernels stage their inputs for a tile plus a one-cell halo in shared
-// memory, evaluate every face flux of the tile once (a face is shared by two
-// cells), and write one cell per thread.  Populations are kept as the
-// deviation d_k = f_k - w_k so that FP32 keeps the small momentum
-// m = sum_k c_k d_k to full relative precision; with 16-bit storage the
-// deviation is the stored quantity.  No tensor cores: the step is a
-// bandwidth-bound stencil.
+// Device building blocks shared by the step kernels (step2d.cuh,
+// step3d.cuh): lattice tables (D2Q9 in the paper's numbering, D3Q19), the
+// population storage codec, the run-time parameters, the interpolation and
+// gradient-energy functions of the phase field, the Gibbs-simplex
+// projection; and the state I/O and fixed-order invariants kernels.
+// Populations are kept as the deviation d_k = f_k - w_k so that FP32 keeps
+// the small momentum sum_k c_k d_k to full relative precision; with 16-bit
+// storage the deviation is the stored quantity.  No tensor cores: the step
+// is a bandwidth- and issue-bound stencil, not a contraction.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -109,50 +103,6 @@ template <>
 struct Codec<__nv_bfloat16> {
   __device__ static float load(__nv_bfloat16 s) { return __bfloat162float(s); }
   __device__ static __nv_bfloat16 put(float v) { return __float2bfloat16_rn(v); }
-};
-
-// ------------------------------------------------------------------ tiles
-template <int D, class Real>
-struct Tile;
-template <>
-struct Tile<2, float> {
-  static constexpr int TX = 64, TY = 8, TZ = 1;
-};
-template <>
-struct Tile<2, double> {
-  static constexpr int TX = 32, TY = 8, TZ = 1;
-};
-template <>
-struct Tile<3, float> {
-  static constexpr int TX = 32, TY = 4, TZ = 2;
-};
-template <>
-struct Tile<3, double> {
-  static constexpr int TX = 16, TY = 4, TZ = 2;
-};
-
-template <int D, class Real>
-struct Geo {
-  static constexpr int TX = Tile<D, Real>::TX, TY = Tile<D, Real>::TY, TZ = Tile<D, Real>::TZ;
-  static constexpr int NT = TX * TY * TZ;
-  // halo box: one cell on each side (no z halo in 2D)
-  static constexpr int HX = TX + 2, HY = TY + 2, HZ = D == 3 ? TZ + 2 : 1;
-  static constexpr int HC = HX * HY * HZ;
-  static constexpr int SX = 1, SY = HX, SZ = HX * HY;  // halo strides
-  static constexpr int ZOFF = D == 3 ? 1 : 0;          // halo offset along z
-  // faces normal to each axis: the lower face of every tile cell plus the
-  // upper face of the last cell
-  static constexpr int F0 = (TX + 1) * TY * TZ;
-  static constexpr int F1 = TX * (TY + 1) * TZ;
-  static constexpr int F2 = D == 3 ? TX * TY * (TZ + 1) : 0;
-  static constexpr int FALL = F0 + F1 + F2;
-  __host__ __device__ static constexpr int hstride(int a) { return a == 0 ? SX : (a == 1 ? SY : SZ); }
-  __host__ __device__ static constexpr int fcount(int a) { return a == 0 ? F0 : (a == 1 ? F1 : F2); }
-  __host__ __device__ static constexpr int foff(int a) { return a == 0 ? 0 : (a == 1 ? F0 : F0 + F1); }
-  // face grid extent along axis b for faces normal to axis a
-  __host__ __device__ static constexpr int fext(int a, int b) {
-    return (b == 0 ? TX : (b == 1 ? TY : TZ)) + (a == b ? 1 : 0);
-  }
 };
 
 // ------------------------------------------------------------------ parameters
@@ -333,531 +283,6 @@ __device__ __forceinline__ void load_phases(const Real* __restrict__ phi, long l
 template <int D, class Real>
 __device__ __forceinline__ long long cell_index(const DevParams<Real>& P, int x, int y, int z) {
   return (long long)x + (long long)P.px * ((long long)y + (long long)P.n[1] * z);
-}
-
-// True when the tile and its one-cell halo lie inside the domain on every
-// axis, so halo cells need no wrapping or mirroring (block-uniform).
-template <int D, class Real>
-__device__ __forceinline__ bool tile_inside(const DevParams<Real>& P, const int* b0) {
-  using G = Geo<D, Real>;
-  const int T[3] = {G::TX, G::TY, G::TZ};
-  bool in = true;
-#pragma unroll
-  for (int a = 0; a < D; ++a) in = in && b0[a] >= 1 && b0[a] + T[a] + 1 <= P.n[a];
-  return in;
-}
-
-// Global coordinates of halo cell h of the tile at b0 (halo offset 1 per axis).
-template <int D, class Real>
-__device__ __forceinline__ void halo_coords(const DevParams<Real>& P, const int* b0, bool inner,
-                                            int h, int* c) {
-  using G = Geo<D, Real>;
-  const int hx = h % G::HX, hy = (h / G::HX) % G::HY, hz = h / (G::HX * G::HY);
-  if (inner) {
-    c[0] = b0[0] + hx - 1;
-    c[1] = b0[1] + hy - 1;
-    c[2] = D == 3 ? b0[2] + hz - 1 : 0;
-  } else {
-    c[0] = fold_axis(P, b0[0] + hx - 1, 0);
-    c[1] = fold_axis(P, b0[1] + hy - 1, 1);
-    c[2] = D == 3 ? fold_axis(P, b0[2] + hz - 1, 2) : 0;
-  }
-}
-
-// Shared-memory layout of the phase-field kernel (bytes).
-template <int D, int NP, class Real>
-struct PfSmem {
-  using G = Geo<D, Real>;
-  static constexpr size_t phi = 0;
-  static constexpr size_t flux = phi + sizeof(Real) * NP * G::HC;
-  static constexpr size_t mask = flux + sizeof(Real) * NP * G::FALL;
-  static constexpr size_t multi = mask + G::HC;
-  static constexpr size_t bytes = multi + G::NT + 16;
-};
-
-template <int D, int NP, int NC, class Real>
-__global__ void __launch_bounds__(Geo<D, Real>::NT)
-    phase_field_kernel(const DevParams<Real> P, const Real* __restrict__ phi_in,
-                       const Real* __restrict__ mu_in, Real* __restrict__ phi_out,
-                       const double* __restrict__ clock) {
-  using G = Geo<D, Real>;
-  using L = PfSmem<D, NP, Real>;
-  constexpr int NS = PhiStore<NP>::NS;
-  extern __shared__ __align__(16) unsigned char smem[];
-  Real* s_phi = reinterpret_cast<Real*>(smem + L::phi);
-  Real* s_flux = reinterpret_cast<Real*>(smem + L::flux);
-  unsigned char* s_mask = smem + L::mask;
-  unsigned char* s_multi = smem + L::multi;
-
-  const int tid = threadIdx.x;
-  const int b0[3] = {(int)blockIdx.x * G::TX, (int)blockIdx.y * G::TY, (int)blockIdx.z * G::TZ};
-  const bool inner = tile_inside<D>(P, b0);
-
-  // 1. phi^n on the tile and its halo, plus the set of phases present
-  for (int h = tid; h < G::HC; h += G::NT) {
-    int c[3];
-    halo_coords<D>(P, b0, inner, h, c);
-    Real v[NP];
-    load_phases<NP>(phi_in, cell_index<D>(P, c[0], c[1], c[2]), P.plane, v);
-    unsigned m = 0;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      s_phi[a * G::HC + h] = v[a];
-      if (v[a] > Real(0)) m |= 1u << a;
-    }
-    s_mask[h] = (unsigned char)m;
-  }
-  __syncthreads();
-
-  // 2. cells with more than one phase in their 3^d neighbourhood; elsewhere
-  //    the single present phase keeps phi = 1 (its rate g - Lambda is 0)
-  const int t3[3] = {tid % G::TX, (tid / G::TX) % G::TY, tid / (G::TX * G::TY)};
-  const int gx = b0[0] + t3[0], gy = b0[1] + t3[1], gz = b0[2] + t3[2];
-  const bool inside = gx < P.n[0] && gy < P.n[1] && gz < P.n[2];
-  const int h = (t3[0] + 1) * G::SX + (t3[1] + 1) * G::SY + (t3[2] + G::ZOFF) * G::SZ;
-  unsigned act = 0;
-#pragma unroll
-  for (int dz = -(D == 3 ? 1 : 0); dz <= (D == 3 ? 1 : 0); ++dz)
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) act |= s_mask[h + dx * G::SX + dy * G::SY + dz * G::SZ];
-  const bool multi = inside && __popc(act) >= 2 && !obstacle(P, gx, gy, gz);
-  s_multi[tid] = multi ? 1 : 0;
-  const long long g = inside ? cell_index<D>(P, gx, gy, gz) : 0;
-  if (!__syncthreads_or(multi)) {
-    if (inside)
-#pragma unroll
-      for (int s = 0; s < NS; ++s) phi_out[s * P.plane + g] = s_phi[(NP == 2 ? 1 : s) * G::HC + h];
-    return;
-  }
-
-  // 3. d-th component of da/d(grad phi_a) on the faces of multi-phase cells:
-  //    -sum_{b != a} gamma_ab phi_b dA/dq(q_ab), q_ab = phi_a grad phi_b - phi_b grad phi_a
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const int ex = G::fext(d, 0), ey = G::fext(d, 1);
-    const int tstride = d == 0 ? 1 : (d == 1 ? G::TX : G::TX * G::TY);
-    const int Td = d == 0 ? G::TX : (d == 1 ? G::TY : G::TZ);
-    for (int i = tid; i < G::fcount(d); i += G::NT) {
-      const int f[3] = {i % ex, (i / ex) % ey, i / (ex * ey)};
-      const int tu = f[0] + G::TX * (f[1] + G::TY * f[2]);  // upper tile cell (if f[d] < Td)
-      const bool need = (f[d] < Td && s_multi[tu]) || (f[d] > 0 && s_multi[tu - tstride]);
-      const int gd = b0[d] + f[d];  // global index of the upper cell of the face
-      const bool closed = P.bc[d] == kWall && (gd == 0 || gd == P.n[d]);
-      Real fl[NP];
-#pragma unroll
-      for (int a = 0; a < NP; ++a) fl[a] = Real(0);
-      if (need && !closed) {
-        const int hb = (f[0] + 1) * G::SX + (f[1] + 1) * G::SY + (f[2] + G::ZOFF) * G::SZ;
-        const int ha = hb - G::hstride(d);
-        Real pf[NP], gr[NP][D];
-#pragma unroll
-        for (int a = 0; a < NP; ++a) {
-          const Real* sp = s_phi + a * G::HC;
-          pf[a] = Real(0.5) * (sp[ha] + sp[hb]);
-#pragma unroll
-          for (int t = 0; t < D; ++t) {
-            if (t == d) {
-              gr[a][t] = sp[hb] - sp[ha];
-            } else {
-              const int st = G::hstride(t);
-              gr[a][t] = Real(0.25) * (sp[ha + st] + sp[hb + st] - sp[ha - st] - sp[hb - st]);
-            }
-          }
-        }
-#pragma unroll
-        for (int a = 0; a < NP; ++a)
-#pragma unroll
-          for (int b = a + 1; b < NP; ++b) {
-            const Real gab = P.gamma[a][b];
-            if (gab == Real(0)) continue;
-            Real q[D];
-#pragma unroll
-            for (int t = 0; t < D; ++t) q[t] = pf[a] * gr[b][t] - pf[b] * gr[a][t];
-            const Real v = dAdq<D>(q, P.delta[a][b], P.q_floor, d);
-            fl[a] -= gab * pf[b] * v;  // dA/dq(q_ba) = -dA/dq(q_ab)
-            fl[b] += gab * pf[a] * v;
-          }
-      }
-#pragma unroll
-      for (int a = 0; a < NP; ++a) s_flux[a * G::FALL + G::foff(d) + i] = fl[a];
-    }
-  }
-  __syncthreads();
-
-  // 4. one cell per thread
-  if (!inside) return;
-  Real ph[NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) ph[a] = s_phi[a * G::HC + h];
-  if (!multi) {
-#pragma unroll
-    for (int s = 0; s < NS; ++s) phi_out[s * P.plane + g] = ph[NP == 2 ? 1 : s];
-    return;
-  }
-  Real div[NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) div[a] = Real(0);
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const int ex = G::fext(d, 0), ey = G::fext(d, 1);
-    const int lo = t3[0] + ex * (t3[1] + ey * t3[2]);
-    const int up = lo + (d == 0 ? 1 : (d == 1 ? ex : ex * ey));
-#pragma unroll
-    for (int a = 0; a < NP; ++a)
-      div[a] += s_flux[a * G::FALL + G::foff(d) + up] - s_flux[a * G::FALL + G::foff(d) + lo];
-  }
-  // da/dphi_a = sum_{b != a} gamma_ab dA/dq(q_ab) . grad phi_b (central gradients)
-  Real gc[NP][D];
-#pragma unroll
-  for (int a = 0; a < NP; ++a)
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-      const int st = G::hstride(t);
-      gc[a][t] = Real(0.5) * (s_phi[a * G::HC + h + st] - s_phi[a * G::HC + h - st]);
-    }
-  Real dadphi[NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) dadphi[a] = Real(0);
-#pragma unroll
-  for (int a = 0; a < NP; ++a)
-#pragma unroll
-    for (int b = a + 1; b < NP; ++b) {
-      const Real gab = P.gamma[a][b];
-      if (gab == Real(0)) continue;
-      Real q[D], v[D];
-#pragma unroll
-      for (int t = 0; t < D; ++t) q[t] = ph[a] * gc[b][t] - ph[b] * gc[a][t];
-      dAdq_vec<D>(q, P.delta[a][b], P.q_floor, v);
-      Real va = Real(0), vb = Real(0);
-#pragma unroll
-      for (int t = 0; t < D; ++t) {
-        va += v[t] * gc[b][t];
-        vb += v[t] * gc[a][t];
-      }
-      dadphi[a] += gab * va;
-      dadphi[b] -= gab * vb;
-    }
-  // grand potentials psi_b(mu, T), theta = T - T_E
-  Real mu[NC];
-#pragma unroll
-  for (int i = 0; i < NC; ++i) mu[i] = mu_in[i * P.plane + g];
-  const int v_coord = D == 3 ? gz : gy;
-  const Real theta = (Real(P.theta0) - Real(P.GV) * Real(clock[0])) + P.G * Real(v_coord);
-  Real psi[NP];
-#pragma unroll
-  for (int b = 0; b < NP; ++b) {
-    Real s = P.S[b] * theta;
-#pragma unroll
-    for (int i = 0; i < NC; ++i) s -= mu[i] * mu[i] * P.inv4A[b] + mu[i] * P.ceq[b][i];
-    psi[b] = s;
-  }
-  // unconstrained rates g_a
-  Real rate[NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) {
-    Real obst = Real(0), drive = Real(0);
-#pragma unroll
-    for (int b = 0; b < NP; ++b) {
-      if (b != a) obst += P.gamma[a][b] * ph[b];
-      drive += psi[b] * interp_dh<NP>(ph, b, a);
-    }
-    rate[a] = P.eps * (div[a] - dadphi[a]) - P.obst * obst - drive;
-  }
-  int na = 0;
-  Real lam = Real(0);
-#pragma unroll
-  for (int a = 0; a < NP; ++a)
-    if (act & (1u << a)) {
-      lam += rate[a];
-      ++na;
-    }
-  lam = lam / Real(na);
-  Real u[NP];
-  int m = 0;
-#pragma unroll
-  for (int a = 0; a < NP; ++a)
-    if (act & (1u << a)) u[m++] = ph[a] + P.mob_eps * (rate[a] - lam);
-  Real out[NP];
-  if (NP == 2) {
-    // only phi_1 is stored: clamp it to [0, 1] (the two-phase projection)
-    Real s = u[1];
-    out[1] = s < Real(0) ? Real(0) : (s > Real(1) ? Real(1) : s);
-  } else {
-    project_simplex<Real, NP>(u, m);
-    m = 0;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) out[a] = (act & (1u << a)) ? u[m++] : Real(0);
-  }
-#pragma unroll
-  for (int s = 0; s < NS; ++s) phi_out[s * P.plane + g] = out[NP == 2 ? 1 : s];
-}
-
-// ------------------------------------------------------------------ mu + LBM
-template <int D, int NP, int NC, class Real>
-struct MlSmem {
-  using G = Geo<D, Real>;
-  static constexpr int Q = D == 2 ? 9 : 19;
-  static constexpr size_t po = 0;                                   // phi^n
-  static constexpr size_t pn = po + sizeof(Real) * NP * G::HC;      // phi^{n+1}
-  static constexpr size_t mu = pn + sizeof(Real) * NP * G::HC;      // mu^n
-  static constexpr size_t u = mu + sizeof(Real) * NC * G::HC;       // U^n
-  static constexpr size_t hl = u + sizeof(Real) * D * G::HC;        // h_liquid(phi^{n+1})
-  static constexpr size_t fs = hl + sizeof(Real) * G::HC;           // collided deviations
-  static constexpr size_t J = fs + sizeof(Real) * Q * G::HC;        // face fluxes
-  static constexpr size_t chg = J + sizeof(Real) * NC * G::FALL;    // phi changed
-  static constexpr size_t bytes = chg + G::HC + 16;
-};
-
-template <int D, int NP, int NC, class Real, class Store>
-__global__ void __launch_bounds__(Geo<D, Real>::NT)
-    mu_lbm_kernel(const DevParams<Real> P, const Real* __restrict__ phi_old,
-                  const Real* __restrict__ phi_new, const Real* __restrict__ mu_in,
-                  const Store* __restrict__ f_in, Real* __restrict__ mu_out,
-                  Store* __restrict__ f_out, const double* __restrict__ clock_in,
-                  double* __restrict__ clock_out) {
-  using G = Geo<D, Real>;
-  using L = MlSmem<D, NP, NC, Real>;
-  using Lat = typename LatticeOf<D>::type;
-  constexpr int Q = D == 2 ? 9 : 19;
-  extern __shared__ __align__(16) unsigned char smem[];
-  Real* s_po = reinterpret_cast<Real*>(smem + L::po);
-  Real* s_pn = reinterpret_cast<Real*>(smem + L::pn);
-  Real* s_mu = reinterpret_cast<Real*>(smem + L::mu);
-  Real* s_u = reinterpret_cast<Real*>(smem + L::u);
-  Real* s_hl = reinterpret_cast<Real*>(smem + L::hl);
-  Real* s_fs = reinterpret_cast<Real*>(smem + L::fs);
-  Real* s_J = reinterpret_cast<Real*>(smem + L::J);
-  unsigned char* s_chg = smem + L::chg;
-
-  const int tid = threadIdx.x;
-  const int b0[3] = {(int)blockIdx.x * G::TX, (int)blockIdx.y * G::TY, (int)blockIdx.z * G::TZ};
-  const bool inner = tile_inside<D>(P, b0);
-  const double t_now = clock_in[0];
-  const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
-  const Real omega = Real(1) - P.inv_tau_f;
-
-  // 1. stage phi^n, phi^{n+1}, mu^n on tile + halo; moments of f^n,
-  //    rho, U = (m + F_B/2) / (rho (1 + kappa/2)), F = F_B - rho kappa U,
-  //    and the BGK + Guo collision of every staged cell
-  for (int h = tid; h < G::HC; h += G::NT) {
-    int c[3];
-    halo_coords<D>(P, b0, inner, h, c);
-    const long long g = cell_index<D>(P, c[0], c[1], c[2]);
-    Real po[NP], pn[NP];
-    load_phases<NP>(phi_old, g, P.plane, po);
-    load_phases<NP>(phi_new, g, P.plane, pn);
-    bool changed = false;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      s_po[a * G::HC + h] = po[a];
-      s_pn[a * G::HC + h] = pn[a];
-      changed = changed || (po[a] != pn[a]);
-    }
-    s_chg[h] = changed ? 1 : 0;
-    s_hl[h] = interp_h<NP>(pn, 0);
-    Real mu[NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      mu[i] = mu_in[i * P.plane + g];
-      s_mu[i * G::HC + h] = mu[i];
-    }
-    Real dk[Q];
-#pragma unroll
-    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(f_in[k * P.plane + g]);
-    Real drho = Real(0), m[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) m[a] = Real(0);
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      drho += dk[k];
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-        if (Lat::c(k, a) != 0) m[a] += Real(Lat::c(k, a)) * dk[k];
-    }
-    const Real rho = Real(1) + drho;
-    const Real phil = obstacle(P, c[0], c[1], c[2]) ? Real(0) : po[0];
-    const Real sl = Real(1) - phil;
-    const Real kappa = P.kappa0 * sl * sl;
-    const Real theta = theta_base + P.G * Real(D == 3 ? c[2] : c[1]);
-    Real drive = P.gbeta_T * (theta + P.dT_ref);
-#pragma unroll
-    for (int i = 0; i < NC; ++i) drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
-    const Real FB = rho * phil * drive;
-    const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
-    Real u[D], F[D];
-    Real uu = Real(0), uF = Real(0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const Real fb = a == D - 1 ? FB : Real(0);
-      u[a] = (m[a] + Real(0.5) * fb) * inv;
-      F[a] = fb - rho * kappa * u[a];
-      s_u[a * G::HC + h] = u[a];
-      uu += u[a] * u[a];
-      uF += u[a] * F[a];
-    }
-    // f*_k - w_k = (1 - 1/tau) d_k + (feq_k - w_k)/tau + G_k with
-    // feq_k - w_k = w_k [(drho - 1.5 rho U.U) + rho cu (3 + 4.5 cu)],
-    // G_k = w_k [-3 (1 - 1/2tau) U.F + (1 - 1/2tau) cF (3 + 9 cu)]
-    const Real A0 = drho - Real(1.5) * rho * uu;
-    const Real B0 = Real(-3) * P.force_pre * uF;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      Real cu = Real(0), cF = Real(0);
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        if (Lat::c(k, a) > 0) {
-          cu += u[a];
-          cF += F[a];
-        } else if (Lat::c(k, a) < 0) {
-          cu -= u[a];
-          cF -= F[a];
-        }
-      }
-      const Real wk = Real(Lat::w(k));
-      const Real deq = wk * (A0 + rho * cu * (Real(3) + Real(4.5) * cu));
-      const Real Gk = wk * (B0 + P.force_pre * cF * (Real(3) + Real(9) * cu));
-      s_fs[k * G::HC + h] = omega * dk[k] + P.inv_tau_f * deq + Gk;
-    }
-  }
-  __syncthreads();
-
-  // 2. solute flux through every face of the tile: diffusion
-  //    -M_f (mu_b - mu_a), antitrapping
-  //    -a eps sum_{a>0} [phi_l]_f [c_l - c_a]_f [dphi_a]_f n_a.e_d, advection
-  //    [U_d h_l c_l]_f; zero through walls and obstacle cells
-#pragma unroll
-  for (int d = 0; d < D; ++d) {
-    const int ex = G::fext(d, 0), ey = G::fext(d, 1);
-    for (int i = tid; i < G::fcount(d); i += G::NT) {
-      const int f[3] = {i % ex, (i / ex) % ey, i / (ex * ey)};
-      const int gd = b0[d] + f[d];
-      Real J[NC];
-#pragma unroll
-      for (int s = 0; s < NC; ++s) J[s] = Real(0);
-      bool closed = (P.bc[d] == kWall && (gd == 0 || gd == P.n[d])) || gd > P.n[d];
-      if (!closed && (P.wall[0] | P.wall[1] | P.wall[2])) {
-        int ga[3] = {b0[0] + f[0], b0[1] + f[1], b0[2] + f[2]};
-        int gb[3] = {ga[0], ga[1], ga[2]};
-        ga[d] -= 1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          ga[a] = (a < D) ? fold_axis(P, ga[a], a) : 0;
-          gb[a] = (a < D) ? fold_axis(P, gb[a], a) : 0;
-        }
-        closed = obstacle(P, ga[0], ga[1], ga[2]) || obstacle(P, gb[0], gb[1], gb[2]);
-      }
-      if (!closed) {
-        const int hb = (f[0] + 1) * G::SX + (f[1] + 1) * G::SY + (f[2] + G::ZOFF) * G::SZ;
-        const int ha = hb - G::hstride(d);
-        const Real Mf = Real(0.5) * P.M0 * (s_pn[ha] + s_pn[hb]);  // plane 0 = liquid
-        const Real ua = s_u[d * G::HC + ha] * s_hl[ha], ub = s_u[d * G::HC + hb] * s_hl[hb];
-#pragma unroll
-        for (int s = 0; s < NC; ++s) {
-          const Real ma = s_mu[s * G::HC + ha], mb = s_mu[s * G::HC + hb];
-          J[s] = -Mf * (mb - ma) +
-                 Real(0.5) * (ua * (P.ceq[0][s] + ma * P.inv2A[0]) + ub * (P.ceq[0][s] + mb * P.inv2A[0]));
-        }
-        if (P.at_eps != Real(0) && (s_chg[ha] | s_chg[hb])) {
-          Real at[NC];
-#pragma unroll
-          for (int s = 0; s < NC; ++s) at[s] = Real(0);
-#pragma unroll
-          for (int a = 1; a < NP; ++a) {
-            const Real* sp = s_po + a * G::HC;
-            Real g2 = Real(0), gn = Real(0);
-#pragma unroll
-            for (int t = 0; t < D; ++t) {
-              Real gt;
-              if (t == d) {
-                gt = sp[hb] - sp[ha];
-                gn = gt;
-              } else {
-                const int st = G::hstride(t);
-                gt = Real(0.25) * (sp[ha + st] + sp[hb + st] - sp[ha - st] - sp[hb - st]);
-              }
-              g2 += gt * gt;
-            }
-            if (g2 <= Real(1e-12)) continue;
-            // antitrapping acts where liquid is present: weight by phi_l^n on the face
-            const Real nd = Real(0.5) * (s_po[ha] + s_po[hb]) * gn / sqrt(g2);
-            const Real dphi = Real(0.5) * ((s_pn[a * G::HC + ha] - sp[ha]) + (s_pn[a * G::HC + hb] - sp[hb]));
-            const Real dinv = P.inv2A[0] - P.inv2A[a];
-#pragma unroll
-            for (int s = 0; s < NC; ++s) {
-              const Real dc0 = P.ceq[0][s] - P.ceq[a][s];
-              const Real dc = dc0 + Real(0.5) * (s_mu[s * G::HC + ha] + s_mu[s * G::HC + hb]) * dinv;
-              at[s] += dc * dphi * nd;
-            }
-          }
-#pragma unroll
-          for (int s = 0; s < NC; ++s) J[s] -= P.at_eps * at[s];
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < NC; ++s) s_J[s * G::FALL + G::foff(d) + i] = J[s];
-    }
-  }
-  __syncthreads();
-
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) clock_out[0] = t_now + 1.0;
-
-  // 3. one cell per thread: mu^{n+1}, then f^{n+1} pulled from the collided
-  //    populations of the neighbours (halfway bounce-back on walls)
-  const int t3[3] = {tid % G::TX, (tid / G::TX) % G::TY, tid / (G::TX * G::TY)};
-  const int gc3[3] = {b0[0] + t3[0], b0[1] + t3[1], b0[2] + t3[2]};
-  if (gc3[0] >= P.n[0] || gc3[1] >= P.n[1] || gc3[2] >= P.n[2]) return;
-  const long long g = cell_index<D>(P, gc3[0], gc3[1], gc3[2]);
-  const int h = (t3[0] + 1) * G::SX + (t3[1] + 1) * G::SY + (t3[2] + G::ZOFF) * G::SZ;
-
-  if (obstacle(P, gc3[0], gc3[1], gc3[2])) {
-#pragma unroll
-    for (int s = 0; s < NC; ++s) mu_out[s * P.plane + g] = s_mu[s * G::HC + h];
-  } else {
-    Real po[NP], pn[NP], ho[NP], hn[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      po[a] = s_po[a * G::HC + h];
-      pn[a] = s_pn[a * G::HC + h];
-    }
-    Real chi = Real(0);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      ho[a] = interp_h<NP>(po, a);
-      hn[a] = interp_h<NP>(pn, a);
-      chi += hn[a] * P.inv2A[a];
-    }
-#pragma unroll
-    for (int s = 0; s < NC; ++s) {
-      const Real mu = s_mu[s * G::HC + h];
-      Real div = Real(0);
-#pragma unroll
-      for (int d = 0; d < D; ++d) {
-        const int ex = G::fext(d, 0), ey = G::fext(d, 1);
-        const int lo = t3[0] + ex * (t3[1] + ey * t3[2]);
-        const int up = lo + (d == 0 ? 1 : (d == 1 ? ex : ex * ey));
-        div += s_J[s * G::FALL + G::foff(d) + up] - s_J[s * G::FALL + G::foff(d) + lo];
-      }
-      Real src = Real(0);
-#pragma unroll
-      for (int a = 0; a < NP; ++a) src += (P.ceq[a][s] + mu * P.inv2A[a]) * (hn[a] - ho[a]);
-      mu_out[s * P.plane + g] = mu + (-div - src) / chi;
-    }
-  }
-
-#pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    bool bounce = false;
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const int sa = gc3[a] - Lat::c(k, a);
-      if (P.bc[a] == kWall && (sa < 0 || sa >= P.n[a])) bounce = true;
-    }
-    const int hs = h - Lat::c(k, 0) * G::SX - Lat::c(k, 1) * G::SY - (D == 3 ? Lat::c(k, 2) * G::SZ : 0);
-    const Real v = bounce ? s_fs[Lat::opp(k) * G::HC + h] : s_fs[k * G::HC + hs];
-    f_out[k * P.plane + g] = Codec<Store>::put(v);
-  }
 }
 
 // ------------------------------------------------------------------ state I/O

@@ -57,21 +57,9 @@ struct Ops {
                             double* partial, int blocks, double* out, cudaStream_t s);
 };
 
-template <class K>
-inline cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
 template <int D, int NP, int NC, class Real, class Store>
 struct Impl {
-  using G = Geo<D, Real>;
   static constexpr int Q = D == 2 ? 9 : 19;
-
-  static dim3 tiles(const DevParams<Real>& P) {
-    return dim3((P.n[0] + G::TX - 1) / G::TX, (P.n[1] + G::TY - 1) / G::TY,
-                (P.n[2] + G::TZ - 1) / G::TZ);
-  }
 
   using SZ = Step2D<NP, NC, Real, Store>;
   using S3 = Step3D<NP, NC, Real, Store>;
@@ -101,28 +89,14 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  // the step is one launch; the second half of a timed step is empty
   static cudaError_t step_pf(const void* params, const StepIO& io, cudaStream_t s) {
-    if (D == 2 || D == 3) return step_fused(params, io, s);
-    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
-    phase_field_kernel<D, NP, NC, Real><<<tiles(P), G::NT, PfSmem<D, NP, Real>::bytes, s>>>(
-        P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.mu_in),
-        static_cast<Real*>(io.phi_out), io.clock_in);
-    return cudaGetLastError();
+    return step_fused(params, io, s);
   }
-
-  static cudaError_t step_transport(const void* params, const StepIO& io, cudaStream_t s) {
-    if (D == 2 || D == 3) return cudaSuccess;  // the fused launch did the whole step
-    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
-    mu_lbm_kernel<D, NP, NC, Real, Store><<<tiles(P), G::NT, MlSmem<D, NP, NC, Real>::bytes, s>>>(
-        P, static_cast<const Real*>(io.phi_in), static_cast<const Real*>(io.phi_out),
-        static_cast<const Real*>(io.mu_in), static_cast<const Store*>(io.f_in),
-        static_cast<Real*>(io.mu_out), static_cast<Store*>(io.f_out), io.clock_in, io.clock_out);
-    return cudaGetLastError();
-  }
+  static cudaError_t step_transport(const void*, const StepIO&, cudaStream_t) { return cudaSuccess; }
 
   static cudaError_t step(const void* params, const StepIO& io, cudaStream_t s) {
-    cudaError_t e = step_pf(params, io, s);
-    return e == cudaSuccess ? step_transport(params, io, s) : e;
+    return step_fused(params, io, s);
   }
 
   static cudaError_t load(const void* params, const void* src_phi, const void* src_mu,

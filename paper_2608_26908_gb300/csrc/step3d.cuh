@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
   const Real omega = Real(1) - P.inv_tau_f;
+  const bool has_walls = (P.wall[0] | P.wall[1] | P.wall[2]) != 0;  // obstacle rows
 
   int rx = 0, ry = 0;  // ring column held by threads tid < RING
   long long gring = 0;
@@ -134,7 +135,11 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
   const int rr2 = ry * W2 + rx;
 
   auto slot4 = [](int p) { return p & 3; };
-  auto slot3 = [](int p) { return (p + 3) % 3; };
+  // (p + 3) mod 3; v / 3 = umulhi(v, 0xAAAAAAAB) >> 1 for every 32-bit v
+  auto slot3 = [](int p) {
+    const unsigned v = (unsigned)(p + 3);
+    return (int)(v - 3u * (__umulhi(v, 0xAAAAAAABu) >> 1));
+  };
   auto slot2 = [](int p) { return p & 1; };
   // phase a of plane p (ring of four) at R1-plus-ring index i
   auto PH = [&](int p, int a, int i) -> Real {
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
     if (doC) {
       const int fzc = fold_axis(P, C, 2);
       const long long g = (long long)fzc * zst + gxy;
-      const bool obs = obstacle(P, fx, fy, fzc);
+      const bool obs = has_walls && obstacle(P, fx, fy, fzc);
       Real mu[NC];
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
 #pragma unroll
           for (int dx = -1; dx <= 1; ++dx) act |= MK(C + dz, r2 + dy * W2 + dx);
       mixed = __popc(act) >= 2;
-      multi = mixed && !obstacle(P, fx, fy, fzc);
+      multi = mixed && !(has_walls && obstacle(P, fx, fy, fzc));
 #pragma unroll
       for (int a = 0; a < NP; ++a) out[a] = PH(C, a, r2);
     }
@@ -466,7 +471,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
     const bool outM = doM && M >= z0 && M < nz;
     if (doM) {
       const int fzm = fold_axis(P, M, 2);
-      const bool walls = (P.wall[0] | P.wall[1] | P.wall[2]) != 0;
+      const bool walls = has_walls;
       // flux between this cell (plane M) and neighbour nb: d normal axis
       auto mu_face = [&](int d, int pB, int nbT, int nbR, int gbd, bool obsB, Real* J) {
         bool closed = (P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d];
@@ -557,7 +562,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
       }
 #pragma unroll
       for (int sidx = 0; sidx < NS; ++sidx) phi_out[sidx * P.plane + g] = pn[NP == 2 ? 1 : sidx];
-      if (obstacle(P, fx, fy, fzm)) {
+      if (has_walls && obstacle(P, fx, fy, fzm)) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = s_mu[(slot2(M) * NC + i) * NT + tid];
       } else {
