@@ -141,10 +141,11 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
 gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream);
 
 /* One step launched directly (not from a graph) that records three caller
- * CUDA events (cudaEvent_t) on `stream`: events[0] before the phase-field
- * kernel, events[1] between it and the chemical-potential + lattice-
- * Boltzmann kernel, events[2] after it, for per-kernel timing with
- * cudaEventElapsedTime.  Same result as gpflbm_step(h, 1, stream). */
+ * CUDA events (cudaEvent_t) on `stream`: events[0] before the step kernel
+ * (one fused launch for all three updates), events[1] after it, and
+ * events[2] right after events[1] (the slot of a second launch, which the
+ * fused step does not have), for kernel timing with cudaEventElapsedTime.
+ * Same result as gpflbm_step(h, 1, stream). */
 gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream);
 
 /* Copy fields of the current state out.  field_mask is an OR of
@@ -189,6 +190,50 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
  * outputs and GPFLBM_ERR_NONFINITE as for gpflbm_invariants. */
 gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, double* solute,
                                         double* solid_frac, void* stream);
+
+/* Objective of gpflbm_adjoint, a function of the final state only:
+ *   J = w_frac * (1/cells) sum_x h_1(phi(x))            (solid fraction)
+ *     + w_tip * tip / nx,
+ *   tip = sum_r r p_r,  p = softmax_r(kappa r phi_1(x0 + r, y0)),
+ *   r = 0 .. nx-1-x0: a soft-argmax of the solid front along the +x ray
+ * through (x0, y0).  z0 is ignored in 2D; `solid` must be 1. */
+typedef struct {
+  double w_frac, w_tip, kappa;
+  int x0, y0, z0;
+  int solid;
+} gpflbm_objective;
+
+/* Device bytes gpflbm_adjoint needs for `horizon` steps and checkpoints
+ * every `ckpt_every` steps: ceil(horizon/ckpt_every) checkpoints and
+ * ckpt_every recomputed states (11 planes each), two adjoint states,
+ * 17 scratch planes and 3 FP64 accumulator planes. */
+gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_every, size_t* bytes);
+
+/* Reverse-mode derivative of the discrete map from the current state S^t0
+ * through `horizon` = H steps to J(S^{t0+H}).  The paper defines the step
+ * (the three updates above); the adjoint is the exact transpose of that
+ * discrete step, with the simplex projection differentiated by its active
+ * set: zero through a clamped phase value, the identity where one phase
+ * fills the neighbourhood (the update is then phi^{n+1} = phi^n).
+ * Checkpointing: a forward pass stores S every K = ckpt_every steps; then,
+ * from the last segment back, each segment's states are recomputed from its
+ * checkpoint and K adjoint steps run backwards through them.  Cost: two
+ * forward passes plus H adjoint steps.
+ * Supported: 2D, D2Q9, two phases, one solute, GPFLBM_FP64 or GPFLBM_FP32
+ * (anything else: GPFLBM_ERR_UNSUPPORTED).
+ * Outputs (each may be NULL): *J; dparams[0] = dJ/d(1/tau_phi),
+ * dparams[1] = dJ/d delta_01, dparams[2] = dJ/d gbeta_c[0] (FP64,
+ * accumulated per cell in FP64 and summed in a fixed order); dmu0 =
+ * dJ/dmu(S^t0) as one plane in the exchange layout and type, device or host
+ * memory per dst_is_device.  Per-step contributions are summed with atomics,
+ * so results agree run to run to rounding, not bit for bit.
+ * The handle is left at S^{t0+H}, bit for bit as after gpflbm_step(h, H).
+ * workspace: device memory of gpflbm_adjoint_workspace_bytes() bytes,
+ * 256-byte aligned, or NULL for a cudaMalloc'd block freed before return.
+ * Synchronises `stream`. */
+gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizon, int ckpt_every,
+                             void* workspace, size_t workspace_bytes, double* J, double* dparams,
+                             void* dmu0, int dst_is_device, void* stream);
 
 /* Step counter of the current state (the t of T(v, t)). */
 gpflbm_status gpflbm_time(gpflbm_t h, long long* t);

@@ -217,3 +217,14 @@ def objective(sc, obj, phi, mu, f, n_steps, dmu0=None, dcoef=None, n0=0):
     if rc != 0:
         raise ValueError("oracle_objective rejected the problem")
     return J.value, dJ.value
+
+
+def objective_value(sc, obj, phi):
+    """J of a given state (N phase planes, liquid first), without stepping."""
+    p = problem(sc)
+    o = objective_spec(obj)
+    J = ctypes.c_double()
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    if lib().oracle_objective_value(ctypes.byref(p), ctypes.byref(o), _dp(phi), ctypes.byref(J)) != 0:
+        raise ValueError("oracle_objective_value rejected the problem")
+    return J.value

@@ -11,7 +11,9 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
+#include "adjoint_ops.h"
 #include "gpflbm.h"
 #include "gpflbm_ops.cuh"
 
@@ -676,3 +678,224 @@ extern "C" gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, dou
     return fail(h, GPFLBM_ERR_NONFINITE, "invariants_noalloc: NaN or Inf in the state");
   return GPFLBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Adjoint with checkpointing (2D, two phases, one solute).
+//
+// Workspace: ceil(H/K) checkpoints, K recomputed states of one segment (the
+// segment's first state is its checkpoint), one clock per stored state, two
+// adjoint states (ping-pong), 16 solute-face and 1 phase-field scratch
+// planes, 3 FP64 accumulator planes and the reduction partials.  A stored
+// state is 11 planes: phi_1, mu, f - w (9).
+
+namespace {
+
+struct AdjLayout {
+  size_t state;  // bytes of one stored state
+  int n_ck, K;
+  size_t ckpt, seg, clk, lam[2], mface, lu, gacc, partial, tip, total;
+};
+
+AdjLayout adj_layout(gpflbm_t h, int H, int K) {
+  AdjLayout L;
+  const size_t pl = (size_t)h->plane * h->ops->real_size;
+  L.K = K < H ? K : H;
+  L.n_ck = (H + L.K - 1) / L.K;
+  L.state = 11 * pl;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t a = off;
+    off = round_up(off + bytes, kAlign);
+    return a;
+  };
+  L.ckpt = take((size_t)L.n_ck * L.state);
+  L.seg = take((size_t)L.K * L.state);
+  L.clk = take((size_t)(L.n_ck + L.K + 1) * sizeof(double));
+  for (int i = 0; i < 2; ++i) L.lam[i] = take(L.state);
+  L.mface = take(16 * pl);
+  L.lu = take(pl);
+  L.gacc = take(3 * (size_t)h->plane * sizeof(double));
+  L.partial = take(4 * (size_t)gpflbm::kRedMaxBlocks * sizeof(double));
+  L.tip = take(sizeof(double));
+  L.total = off;
+  return L;
+}
+
+gpflbm_status adj_check(gpflbm_t h, int H, int K) {
+  const int prec = h->grid.precision;
+  if (h->D != 2 || h->NP != 2 || h->NC != 1 || (prec != GPFLBM_FP64 && prec != GPFLBM_FP32))
+    return fail(h, GPFLBM_ERR_UNSUPPORTED,
+                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32");
+  if (H < 1 || K < 1) return fail(h, GPFLBM_ERR_ARG, "adjoint: need horizon >= 1 and ckpt_every >= 1");
+  return GPFLBM_OK;
+}
+
+gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const AdjLayout& L,
+                          unsigned char* ws, double* J, double* dparams, void* dmu0, int dst_is_device,
+                          cudaStream_t s) {
+  const gpflbm::AdjOps* A = gpflbm::adjoint_ops(h->grid.precision == GPFLBM_FP64);
+  const void* P = dev_params(h);
+  const size_t pl = (size_t)h->plane * h->ops->real_size;
+  const int K = L.K;
+  double* clk = reinterpret_cast<double*>(ws + L.clk);
+  cudaError_t e = cudaSuccess;
+  auto stored = [&](size_t base, int i) { return ws + base + (size_t)i * L.state; };
+
+  // forward pass through the handle's own buffers, keeping checkpoints
+  for (int c = 0; c < L.n_ck; ++c) {
+    unsigned char* ck = stored(L.ckpt, c);
+    e = cudaMemcpyAsync(ck, at(h, h->lay.phi[h->cur]), pl, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ck + pl, at(h, h->lay.mu[h->cur]), pl, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ck + 2 * pl, at(h, h->lay.f[h->cur]), 9 * pl, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(clk + c, reinterpret_cast<double*>(at(h, h->lay.clock)) + h->cur, sizeof(double),
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: checkpoint copy");
+    const int len = H - c * K < K ? H - c * K : K;
+    gpflbm_status st = gpflbm_step(h, len, s);
+    if (st != GPFLBM_OK) return st;
+  }
+
+  // objective of the final state and the adjoint state it seeds
+  unsigned char* lam[2] = {ws + L.lam[0], ws + L.lam[1]};
+  double* gacc = reinterpret_cast<double*>(ws + L.gacc);
+  double* partial = reinterpret_cast<double*>(ws + L.partial);
+  double* tip = reinterpret_cast<double*>(ws + L.tip);
+  const long long want = (h->cells + gpflbm::kRedThreads - 1) / gpflbm::kRedThreads;
+  const int blocks = (int)(want < gpflbm::kRedMaxBlocks ? want : gpflbm::kRedMaxBlocks);
+  const void* s_fin = at(h, h->lay.phi[h->cur]);
+  e = A->frac(P, s_fin, partial, blocks, s);
+  if (e == cudaSuccess) e = A->init(P, s_fin, obj->w_frac, lam[0], lam[0] + pl, lam[0] + 2 * pl, gacc, s);
+  if (e == cudaSuccess) e = A->tip(P, s_fin, obj->x0, obj->y0, obj->kappa, obj->w_tip, lam[0], tip, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: objective");
+
+  // backward: recompute each segment from its checkpoint, then step back
+  int cur = 0;
+  for (int c = L.n_ck - 1; c >= 0; --c) {
+    const int len = H - c * K < K ? H - c * K : K;
+    auto st_at = [&](int j) { return j == 0 ? stored(L.ckpt, c) : stored(L.seg, j - 1); };
+    auto clk_at = [&](int j) { return j == 0 ? clk + c : clk + L.n_ck + j; };
+    for (int j = 0; j < len; ++j) {
+      gpflbm::StepIO io;
+      io.phi_in = st_at(j);
+      io.mu_in = st_at(j) + pl;
+      io.f_in = st_at(j) + 2 * pl;
+      io.phi_out = st_at(j + 1);
+      io.mu_out = st_at(j + 1) + pl;
+      io.f_out = st_at(j + 1) + 2 * pl;
+      io.clock_in = clk_at(j);
+      io.clock_out = clk_at(j + 1);
+      io.err = reinterpret_cast<int*>(at(h, h->lay.err));
+      e = h->ops->step(P, io, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: recompute");
+    }
+    for (int j = len - 1; j >= 0; --j) {
+      gpflbm::AdjStepIO a;
+      a.s0 = st_at(j);
+      a.mu0 = st_at(j) + pl;
+      a.d0 = st_at(j) + 2 * pl;
+      a.s1 = st_at(j + 1);
+      a.mu1 = st_at(j + 1) + pl;
+      a.ls1 = lam[cur];
+      a.lmu1 = lam[cur] + pl;
+      a.ld1 = lam[cur] + 2 * pl;
+      a.ls0 = lam[1 - cur];
+      a.lmu0 = lam[1 - cur] + pl;
+      a.ld0 = lam[1 - cur] + 2 * pl;
+      a.mface = ws + L.mface;
+      a.lu = ws + L.lu;
+      a.gacc = gacc;
+      a.clock = clk_at(j);
+      e = A->step(P, a, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: step");
+      cur = 1 - cur;
+    }
+  }
+
+  // outputs
+  if (dmu0) {
+    void* target = dst_is_device ? dmu0 : at(h, h->lay.stage);
+    e = A->export_plane(P, lam[cur] + pl, target, s);
+    if (e == cudaSuccess && !dst_is_device)
+      e = cudaMemcpyAsync(dmu0, target, (size_t)h->cells * h->ops->real_size, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: dmu0");
+  }
+  for (int j = 0; j < 3 && e == cudaSuccess; ++j)
+    e = A->sum(P, gacc + (size_t)j * h->plane, partial + (size_t)(j + 1) * gpflbm::kRedMaxBlocks, blocks, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: parameter sums");
+  std::vector<double> host(4 * (size_t)gpflbm::kRedMaxBlocks + 1);
+  int err_word = 0;
+  e = cudaMemcpyAsync(host.data(), partial, 4 * (size_t)gpflbm::kRedMaxBlocks * sizeof(double),
+                      cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&host[4 * (size_t)gpflbm::kRedMaxBlocks], tip, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&err_word, at(h, h->lay.err), sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: results");
+  if (err_word != 0) return fail(h, GPFLBM_ERR_TIMEOUT, "a bounded device wait gave up during a step");
+  double sums[4];
+  for (int j = 0; j < 4; ++j) {
+    double t = 0.0;
+    for (int b = 0; b < blocks; ++b) t += host[(size_t)j * gpflbm::kRedMaxBlocks + b];
+    sums[j] = t;
+  }
+  const double tip_v = host[4 * (size_t)gpflbm::kRedMaxBlocks];
+  if (J) *J = obj->w_frac * (sums[0] / (double)h->cells) + obj->w_tip * tip_v / (double)h->grid.nx;
+  if (dparams)
+    for (int j = 0; j < 3; ++j) dparams[j] = sums[j + 1];
+  return GPFLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_every, size_t* bytes) {
+  if (!h || !bytes) return GPFLBM_ERR_ARG;
+  gpflbm_status st = adj_check(h, horizon, ckpt_every);
+  if (st != GPFLBM_OK) return st;
+  *bytes = adj_layout(h, horizon, ckpt_every).total;
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizon, int ckpt_every,
+                             void* workspace, size_t workspace_bytes, double* J, double* dparams,
+                             void* dmu0, int dst_is_device, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  gpflbm_status st = adj_check(h, horizon, ckpt_every);
+  if (st != GPFLBM_OK) return st;
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "adjoint: no state loaded");
+  if (!obj || obj->solid != 1 || obj->x0 < 0 || obj->x0 >= h->grid.nx || obj->y0 < 0 ||
+      obj->y0 >= h->grid.ny || !std::isfinite(obj->kappa) || !std::isfinite(obj->w_frac) ||
+      !std::isfinite(obj->w_tip))
+    return fail(h, GPFLBM_ERR_ARG, "adjoint: invalid objective (solid must be 1, (x0, y0) inside)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const AdjLayout L = adj_layout(h, horizon, ckpt_every);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  bool own = false;
+  if (ws) {
+    if (workspace_bytes < L.total) return fail(h, GPFLBM_ERR_OOM, "adjoint: workspace too small");
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign != 0)
+      return fail(h, GPFLBM_ERR_ARG, "adjoint: workspace not 256-byte aligned");
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GPFLBM_ERR_OOM, "adjoint: cudaMalloc of the workspace failed");
+    }
+    ws = static_cast<unsigned char*>(p);
+    own = true;
+  }
+  st = adjoint_run(h, obj, horizon, L, ws, J, dparams, dmu0, dst_is_device, s);
+  if (own) {
+    cudaStreamSynchronize(s);  // nothing may still use the block
+    cudaFree(ws);
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -42,6 +42,20 @@ class Params(ctypes.Structure):
     ]
 
 
+class Objective(ctypes.Structure):
+    """gpflbm_objective: J = w_frac mean h_1 + w_tip tip / nx."""
+    _fields_ = [("w_frac", ctypes.c_double), ("w_tip", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("x0", ctypes.c_int), ("y0", ctypes.c_int), ("z0", ctypes.c_int), ("solid", ctypes.c_int)]
+
+
+def objective_struct(obj):
+    o = Objective()
+    o.w_frac, o.w_tip, o.kappa = float(obj["w_frac"]), float(obj["w_tip"]), float(obj["kappa"])
+    o.x0, o.y0, o.z0 = int(obj["x0"]), int(obj["y0"]), int(obj.get("z0", 0))
+    o.solid = int(obj.get("solid", 1))
+    return o
+
+
 class GpflbmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("gpflbm status %d: %s" % (status, msg))
@@ -72,13 +86,16 @@ def lib():
         L.gpflbm_get_deviations.argtypes = [vp, vp, i, vp]
         L.gpflbm_invariants.argtypes = [vp, dp, dp, dp, vp]
         L.gpflbm_time.argtypes = [vp, ctypes.POINTER(ll)]
+        L.gpflbm_adjoint_workspace_bytes.argtypes = [vp, i, i, ctypes.POINTER(sz)]
+        L.gpflbm_adjoint.argtypes = [vp, ctypes.POINTER(Objective), i, i, vp, sz, dp, dp, vp, i, vp]
         L.gpflbm_last_error.argtypes = [vp]
         L.gpflbm_last_error.restype = ctypes.c_char_p
         L.gpflbm_destroy.argtypes = [vp]
         L.gpflbm_destroy.restype = None
         for name in ("gpflbm_workspace_bytes", "gpflbm_create", "gpflbm_set_params",
                      "gpflbm_set_state", "gpflbm_step", "gpflbm_step_timed", "gpflbm_get_fields",
-                     "gpflbm_get_deviations", "gpflbm_invariants", "gpflbm_time"):
+                     "gpflbm_get_deviations", "gpflbm_invariants", "gpflbm_time",
+                     "gpflbm_adjoint_workspace_bytes", "gpflbm_adjoint"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -255,3 +272,101 @@ class Sim:
         if not (allow_nonfinite and st == ERR_NONFINITE):
             self._check(st, "invariants")
         return m.value, np.array(s[: self.NC]), fr.value, st
+
+    def adjoint_workspace_bytes(self, horizon, ckpt_every):
+        n = ctypes.c_size_t()
+        self._check(lib().gpflbm_adjoint_workspace_bytes(self.h, int(horizon), int(ckpt_every),
+                                                         ctypes.byref(n)), "adjoint_workspace_bytes")
+        return n.value
+
+    def adjoint(self, obj, horizon, ckpt_every, device=False, workspace=None):
+        """Run `horizon` steps from the current state and the adjoint back.
+
+        Returns (J, dparams, dmu0): dparams = dJ/d(1/tau_phi, delta_01,
+        gbeta_c[0]) as a numpy array, dmu0 = dJ/dmu of the starting state (one
+        plane; a device tensor if device=True).  The state is left at
+        t0 + horizon.  workspace: optional uint8 device tensor of at least
+        adjoint_workspace_bytes() bytes (else the library allocates one).
+        """
+        torch = self.torch
+        o = objective_struct(obj)
+        J = ctypes.c_double()
+        dpar = (ctypes.c_double * 3)()
+        if device:
+            dmu = torch.empty(self.cells, dtype=self.tdtype, device="cuda")
+            dptr = ctypes.c_void_p(dmu.data_ptr())
+        else:
+            dmu = np.empty(self.cells, dtype=self.dtype)
+            dptr = ctypes.c_void_p(dmu.ctypes.data)
+        if workspace is not None:
+            wptr, wbytes = ctypes.c_void_p(workspace.data_ptr()), workspace.numel()
+        else:
+            wptr, wbytes = None, 0
+        self._check(lib().gpflbm_adjoint(self.h, ctypes.byref(o), int(horizon), int(ckpt_every), wptr,
+                                         wbytes, ctypes.byref(J), dpar, dptr, int(device),
+                                         _stream(torch)), "adjoint")
+        return J.value, np.array(dpar[:]), dmu
+
+
+def with_parameters(sc, mobility=None, delta=None, gbeta=None):
+    """Copy of a scenario with 1/tau_phi, delta_01 and g beta_c[0] replaced."""
+    import copy
+    sc = copy.deepcopy(sc)
+    pr = sc["params"]
+    if mobility is not None:
+        pr["tau_phi"] = 1.0 / float(mobility)
+    if delta is not None:
+        pr["delta"][0][1] = pr["delta"][1][0] = float(delta)
+    if gbeta is not None:
+        pr["gbeta_c"][0] = float(gbeta)
+    return sc
+
+
+def _make_function():
+    import torch
+
+    class GPFLBMFunction(torch.autograd.Function):
+        """J(mu0, 1/tau_phi, delta, g beta_c) after `horizon` steps from
+        (phi0, mu0), differentiable through the library's adjoint.
+
+        The adjoint runs inside forward (its forward pass produces J, so J
+        and all gradients cost two forward passes plus the adjoint steps);
+        backward scales the stored gradients by grad_output.
+        """
+
+        @staticmethod
+        def forward(ctx, mu0, mobility, delta, gbeta, sim, phi0, obj, horizon, ckpt_every):
+            sim.set_params(with_parameters(sim.sc, float(mobility), float(delta), float(gbeta)))
+            # phi0 and mu0 go in together: both device tensors or both host arrays
+            if mu0.is_cuda:
+                phi = torch.as_tensor(phi0).to(device=mu0.device, dtype=sim.tdtype)
+                sim.set_state(phi, mu0.detach())
+            else:
+                phi = phi0.numpy() if isinstance(phi0, torch.Tensor) else phi0
+                sim.set_state(phi, mu0.detach().numpy())
+            J, dpar, dmu = sim.adjoint(obj, horizon, ckpt_every, device=mu0.is_cuda)
+            if not mu0.is_cuda:
+                dmu = torch.from_numpy(dmu)
+            ctx.save_for_backward(dmu.to(mu0.dtype).reshape(mu0.shape),
+                                  torch.tensor(dpar, dtype=torch.float64))
+            return torch.tensor(J, dtype=torch.float64, device=mu0.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            dmu, dpar = ctx.saved_tensors
+            gd = g.to(torch.float64).cpu()
+            return ((g.to(dmu.dtype) * dmu), (gd * dpar[0]), (gd * dpar[1]), (gd * dpar[2]),
+                    None, None, None, None, None)
+
+    return GPFLBMFunction
+
+
+_function = None
+
+
+def GPFLBMFunction():
+    """The torch.autograd.Function class (created on first use)."""
+    global _function
+    if _function is None:
+        _function = _make_function()
+    return _function

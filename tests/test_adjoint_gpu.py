@@ -1,0 +1,199 @@
+"""Adjoint of the coupled step (gpflbm_adjoint) on the GPU.
+
+Pins, from independent sides:
+  * the oracle's forward-mode dual numbers: exact directional derivatives of
+    the same discrete map in FP64 (the oracle shares no code with the GPU);
+  * FP64 central finite differences of the GPU forward, step 1e-6, on a
+    64 x 64 crop: the gradient within 1e-4 relative;
+  * properties at the full 512 x 512, 500-step, K = 50 workload: the final
+    state equals plain stepping bit for bit, J equals the oracle's J of that
+    final state, dJ/dmu0 vanishes in the frozen wall rows.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2608_26908_gb300 import gpflbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(nx, ny, prec):
+    sc = inputs.scenario("adjoint2d", nx=nx, ny=ny, precision=prec)
+    sc["init"]["radius"] = 6.0
+    sc["params"]["gbeta_c"] = [2e-3, 0.0]  # a flow strong enough to matter
+    return sc
+
+
+def _obj(sc):
+    g = sc["grid"]
+    return {"w_frac": 1.0, "w_tip": 1.0, "kappa": 2.0, "x0": g["nx"] // 2, "y0": g["ny"] // 2,
+            "solid": 1}
+
+
+def _gpu_adjoint(sc, horizon, K):
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0)
+    J, dpar, dmu = sim.adjoint(_obj(sc), horizon, K)
+    return sim, J, dpar, dmu.astype(np.float64)
+
+
+def _oracle_directional(sc, horizon, dmu0=None, dcoef=None):
+    phi0, mu0 = inputs.initial_state(sc)
+    f0 = oracle.rest_populations(sc)
+    return oracle.objective(sc, _obj(sc), phi0, mu0, f0, horizon, dmu0=dmu0, dcoef=dcoef)
+
+
+def _close(a, b, rtol, scale):
+    return abs(a - b) <= rtol * max(abs(b), scale)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-8), ("fp32", 2e-4)])
+def test_adjoint_matches_oracle_dual_derivatives(prec, rtol):
+    """40 x 36 (ragged against 256-thread blocks), 23 steps, K = 5: four
+    full segments and a ragged one."""
+    sc = _case(40, 36, prec)
+    H, K = 23, 5
+    _, J, dpar, dmu = _gpu_adjoint(sc, H, K)
+    rng = np.random.default_rng(11)
+    v = rng.normal(size=dmu.shape)
+    Jo, dJo = _oracle_directional(sc, H, dmu0=v)
+    assert _close(J, Jo, rtol, 0.0)
+    g = float(np.dot(v, dmu))
+    assert _close(g, dJo, rtol, 1e-3 * float(np.abs(v * dmu).sum())), (g, dJo)
+    # single cells at the interface and in the bulk liquid
+    for cell in (18 * 40 + 26, 18 * 40 + 14, 3 * 40 + 5):
+        e = np.zeros_like(v)
+        e[cell] = 1.0
+        _, dJc = _oracle_directional(sc, H, dmu0=e)
+        assert _close(dmu[cell], dJc, rtol, 1e-3 * float(np.abs(dmu).max())), (cell, dmu[cell], dJc)
+    for j in range(3):
+        dc = np.zeros(3)
+        dc[j] = 1.0
+        _, dJp = _oracle_directional(sc, H, dcoef=dc)
+        assert _close(dpar[j], dJp, rtol, 0.0), (j, dpar[j], dJp)
+
+
+def test_adjoint_matches_central_differences_fp64():
+    """64 x 64 crop, 40 steps, K = 8; FP64 central differences of the GPU
+    forward with step 1e-6 (direction of unit RMS for mu0)."""
+    sc = _case(64, 64, "fp64")
+    H, K, h = 40, 8, 1e-6
+    phi0, mu0 = inputs.initial_state(sc)
+    sim, J, dpar, dmu = _gpu_adjoint(sc, H, K)
+    obj = _obj(sc)
+
+    def J_of(sc2, mu):
+        s = gpflbm.Sim(sc2)
+        s.set_state(phi0, mu)
+        return s.adjoint(obj, H, K)[0]
+
+    v = np.random.default_rng(3).normal(size=mu0.shape)
+    fd = (J_of(sc, mu0 + h * v) - J_of(sc, mu0 - h * v)) / (2 * h)
+    assert float(np.dot(v, dmu)) == pytest.approx(fd, rel=1e-4)
+    base = (1.0 / sc["params"]["tau_phi"], sc["params"]["delta"][0][1], sc["params"]["gbeta_c"][0])
+    for j in range(3):
+        vals = []
+        for sgn in (+1, -1):
+            p = list(base)
+            p[j] += sgn * h
+            vals.append(J_of(gpflbm.with_parameters(sc, *p), mu0))
+        fdp = (vals[0] - vals[1]) / (2 * h)
+        assert dpar[j] == pytest.approx(fdp, rel=1e-4), (j, dpar[j], fdp)
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient():
+    sc = _case(40, 36, "fp64")
+    H = 17
+    ref = None
+    for K in (1, 4, 17, 40):
+        _, J, dpar, dmu = _gpu_adjoint(sc, H, K)
+        if ref is None:
+            ref = (J, dpar, dmu)
+            continue
+        assert J == ref[0]  # same forward, same fixed-order sums
+        np.testing.assert_allclose(dpar, ref[1], rtol=1e-12)
+        np.testing.assert_allclose(dmu, ref[2], rtol=1e-10, atol=1e-14 * np.abs(ref[2]).max())
+
+
+def test_adjoint_leaves_the_state_of_plain_stepping():
+    sc = _case(48, 40, "fp32")
+    phi0, mu0 = inputs.initial_state(sc)
+    a = gpflbm.Sim(sc)
+    a.set_state(phi0, mu0)
+    a.adjoint(_obj(sc), 21, 6)
+    b = gpflbm.Sim(sc)
+    b.set_state(phi0, mu0)
+    b.step(21)
+    fa, fb = a.fields(("phi", "mu", "f")), b.fields(("phi", "mu", "f"))
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert a.time() == b.time() == 21
+
+
+def test_adjoint_rejects_unsupported_and_invalid():
+    sc = inputs.scenario("eutectic2d", nx=40, ny=30)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(*inputs.initial_state(sc))
+    with pytest.raises(gpflbm.GpflbmError) as e:
+        sim.adjoint(_obj(sc), 4, 2)
+    assert e.value.status == gpflbm.ERR_UNSUPPORTED
+    sc = _case(40, 36, "fp32")
+    sim = gpflbm.Sim(sc)
+    with pytest.raises(gpflbm.GpflbmError) as e:
+        sim.adjoint(_obj(sc), 4, 2)  # no state yet
+    assert e.value.status == gpflbm.ERR_STATE
+    sim.set_state(*inputs.initial_state(sc))
+    bad = dict(_obj(sc), x0=40)
+    with pytest.raises(gpflbm.GpflbmError) as e:
+        sim.adjoint(bad, 4, 2)
+    assert e.value.status == gpflbm.ERR_ARG
+    with pytest.raises(gpflbm.GpflbmError) as e:
+        sim.adjoint(_obj(sc), 0, 2)
+    assert e.value.status == gpflbm.ERR_ARG
+
+
+def test_autograd_function_returns_the_adjoint_gradients():
+    import torch
+    sc = _case(40, 36, "fp64")
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    mu = torch.tensor(mu0, dtype=torch.float64, device="cuda", requires_grad=True)
+    pr = sc["params"]
+    mob = torch.tensor(1.0 / pr["tau_phi"], dtype=torch.float64, requires_grad=True)
+    dl = torch.tensor(pr["delta"][0][1], dtype=torch.float64, requires_grad=True)
+    gb = torch.tensor(pr["gbeta_c"][0], dtype=torch.float64, requires_grad=True)
+    F = gpflbm.GPFLBMFunction()
+    J = F.apply(mu, mob, dl, gb, sim, phi0, _obj(sc), 11, 4)
+    (2.0 * J).backward()
+    _, J2, dpar, dmu = _gpu_adjoint(sc, 11, 4)
+    assert float(J) == J2
+    np.testing.assert_allclose(mu.grad.cpu().numpy(), 2.0 * dmu, rtol=1e-10, atol=1e-300)
+    np.testing.assert_allclose([mob.grad.item(), dl.grad.item(), gb.grad.item()], 2.0 * dpar,
+                               rtol=1e-10)
+
+
+def test_full_workload_properties():
+    """512 x 512 FP32, 500 steps, checkpoints every 50 (the differentiation
+    workload): final state as plain stepping, J from the oracle's objective
+    of that final state, finite gradients, none in the frozen wall rows."""
+    sc = inputs.scenario("adjoint2d")
+    H, K = 500, 50
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0)
+    J, dpar, dmu = sim.adjoint(_obj(sc), H, K)
+    ref = gpflbm.Sim(sc)
+    ref.set_state(phi0, mu0)
+    ref.step(H)
+    fa, fb = sim.fields(("phi", "mu")), ref.fields(("phi", "mu"))
+    assert np.array_equal(fa["phi"], fb["phi"]) and np.array_equal(fa["mu"], fb["mu"])
+    Jo = oracle.objective_value(sc, _obj(sc), fa["phi"].astype(np.float64))
+    assert J == pytest.approx(Jo, rel=1e-12)
+    assert np.all(np.isfinite(dmu)) and np.all(np.isfinite(dpar))
+    assert np.abs(dmu).max() > 0.0 and np.all(dpar != 0.0)
+    nx, ny = 512, 512
+    rows = dmu.reshape(ny, nx)
+    w = sc["grid"]["wall_rows"][1]
+    assert np.all(rows[:w] == 0.0) and np.all(rows[ny - w:] == 0.0)
