@@ -204,9 +204,9 @@ typedef struct {
 } gpflbm_objective;
 
 /* Device bytes gpflbm_adjoint needs for `horizon` steps and checkpoints
- * every `ckpt_every` steps: ceil(horizon/ckpt_every) checkpoints and
- * ckpt_every recomputed states (11 planes each), two adjoint states,
- * 17 scratch planes and 3 FP64 accumulator planes. */
+ * every `ckpt_every` steps: ceil(horizon/ckpt_every) checkpoints and two
+ * sets of ckpt_every recomputed states (11 planes each), two adjoint states
+ * and 3 FP64 accumulator planes. */
 gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_every, size_t* bytes);
 
 /* Reverse-mode derivative of the discrete map from the current state S^t0
@@ -215,18 +215,19 @@ gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_e
  * discrete step, with the simplex projection differentiated by its active
  * set: zero through a clamped phase value, the identity where one phase
  * fills the neighbourhood (the update is then phi^{n+1} = phi^n).
- * Checkpointing: a forward pass stores S every K = ckpt_every steps; then,
- * from the last segment back, each segment's states are recomputed from its
- * checkpoint and K adjoint steps run backwards through them.  Cost: two
- * forward passes plus H adjoint steps.
+ * Checkpointing: a forward pass stores S every K = ckpt_every steps and
+ * keeps the last segment whole; then, from the last segment back, K adjoint
+ * steps run backwards through each segment while the segment before it is
+ * recomputed from its checkpoint on a second stream (the library's own).
+ * Cost: H + (ceil(H/K) - 1)(K - 1) forward steps plus H adjoint steps.
  * Supported: 2D, D2Q9, two phases, one solute, GPFLBM_FP64 or GPFLBM_FP32
  * (anything else: GPFLBM_ERR_UNSUPPORTED).
  * Outputs (each may be NULL): *J; dparams[0] = dJ/d(1/tau_phi),
  * dparams[1] = dJ/d delta_01, dparams[2] = dJ/d gbeta_c[0] (FP64,
  * accumulated per cell in FP64 and summed in a fixed order); dmu0 =
  * dJ/dmu(S^t0) as one plane in the exchange layout and type, device or host
- * memory per dst_is_device.  Per-step contributions are summed with atomics,
- * so results agree run to run to rounding, not bit for bit.
+ * memory per dst_is_device.  Every contribution is gathered in a fixed
+ * order, so the results are the same from run to run.
  * The handle is left at S^{t0+H}, bit for bit as after gpflbm_step(h, H).
  * workspace: device memory of gpflbm_adjoint_workspace_bytes() bytes,
  * 256-byte aligned, or NULL for a cudaMalloc'd block freed before return.

@@ -38,7 +38,13 @@ struct AdjImpl {
     return cudaGetLastError();
   }
 
+  static cudaError_t configure() {
+    return cudaFuncSetAttribute(adj2d_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Adj2D<Real>::bytes);
+  }
+
   static cudaError_t step(const void* p, const AdjStepIO& v, cudaStream_t st) {
+    using S = Adj2D<Real>;
     const DevParams<Real>& P = par(p);
     AdjIO<Real> io;
     io.s0 = static_cast<const Real*>(v.s0);
@@ -52,16 +58,10 @@ struct AdjImpl {
     io.ls0 = static_cast<Real*>(v.ls0);
     io.lmu0 = static_cast<Real*>(v.lmu0);
     io.ld0 = static_cast<Real*>(v.ld0);
-    io.mface = static_cast<Real*>(v.mface);
-    io.lu = static_cast<Real*>(v.lu);
     io.gacc = v.gacc;
     io.clock = v.clock;
-    cudaError_t e = cudaMemsetAsync(v.ls0, 0, (size_t)P.plane * sizeof(Real), st);
-    if (e != cudaSuccess) return e;
-    const unsigned b = cell_blocks(P);
-    adj_mu_face_kernel<Real><<<b, kThreads, 0, st>>>(P, io);
-    adj_cell_kernel<Real><<<b, kThreads, 0, st>>>(P, io);
-    adj_pf_face_kernel<Real><<<b, kThreads, 0, st>>>(P, io);
+    const dim3 grid((P.n[0] + S::OX - 1) / S::OX, (P.n[1] + S::OY - 1) / S::OY);
+    adj2d_kernel<Real><<<grid, S::NT, S::bytes, st>>>(P, io);
     return cudaGetLastError();
   }
 
@@ -78,7 +78,7 @@ struct AdjImpl {
   }
 
   static const AdjOps* table() {
-    static const AdjOps t = {sizeof(Real), init, tip, frac, step, sum, export_plane};
+    static const AdjOps t = {sizeof(Real), configure, init, tip, frac, step, sum, export_plane};
     return &t;
   }
 };

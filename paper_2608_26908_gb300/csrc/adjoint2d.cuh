@@ -11,18 +11,24 @@
 // takes the derivative of exactly this piecewise map: zero through a clamped
 // cell (the active-set subgradient), the identity for single-phase cells.
 //
-// One backward step n+1 -> n (S^n, S^{n+1} recomputed and stored):
-//   adj_mu_face_kernel  per cell: the adjoint coefficients of its +x and +y
-//                       solute faces (diffusion, advection, antitrapping);
-//                       antitrapping's transverse terms go out by atomics;
-//   adj_cell_kernel     per cell: gathers its faces, the mu-stage terms
-//                       (chi', source), the BGK + Guo collision and moment
-//                       (drag, buoyancy) adjoint of its populations pulled
-//                       back along c_k, and the clamp; writes lambda_mu^n,
-//                       lambda_f^n, part of lambda_s^n and lambda_u;
-//   adj_pf_face_kernel  per cell: the phase-field faces (Hessian of A by dual
-//                       numbers) scattered to the six cells they read.
-// Parameter gradients (mobility, delta, g beta_c) accumulate per cell in FP64.
+// One backward step n+1 -> n is one launch of adj2d_kernel.  A CTA owns an
+// OX x OY tile of output cells and stages, for the tile plus a two-cell
+// halo, the per-cell values the faces read (s^n, s^{n+1}, mu^n,
+// A = lambda_mu^{n+1} / chi(s^{n+1}), the velocity U^n).  Then, in shared
+// memory:
+//   1. the adjoint coefficients of every solute face touching the tile plus
+//      a one-cell halo (diffusion, advection, antitrapping);
+//   2. per cell of the tile plus halo, lambda of the unclamped phase value
+//      (lu); per output cell, the faces gathered, the mu-stage terms (chi',
+//      source), and the BGK + Guo collision and moment (drag, buoyancy)
+//      adjoint of its populations pulled back along c_k;
+//   3. the phase-field faces (Hessian of A by tangent arithmetic), gathered
+//      by the output cells.
+// Every contribution is gathered by the cell that receives it, in a fixed
+// order, so the result is the same from run to run.  Where a wall mirrors
+// the transverse stencil of a face, the cell next to the wall collects the
+// mirrored terms explicitly.  Parameter gradients (mobility, delta,
+// g beta_c) accumulate per cell in FP64.
 #pragma once
 
 #include "gpflbm_kernels.cuh"
@@ -83,16 +89,12 @@ struct AdjIO {
   const Real* ls1;   // adjoint of S^{n+1}
   const Real* lmu1;
   const Real* ld1;
-  Real* ls0;         // adjoint of S^n (ls0 accumulates; zeroed before the step)
+  Real* ls0;         // adjoint of S^n (written)
   Real* lmu0;
   Real* ld0;
-  Real* mface;       // solute-face coefficients: 2 faces x 8 values per cell
-  Real* lu;          // lambda of the unclamped phase-field value u
   double* gacc;      // parameter-gradient accumulators: 3 planes (mob, delta, gbeta)
   const double* clock;  // time of step n (device)
 };
-
-constexpr int kMF = 8;  // per solute face: cmu_a, cmu_b, csp_a, csp_b, cU_a, cU_b, cs_a, cs_b
 
 // rho, U and F of a cell from S^n (the forward moment computation)
 template <class Real>
@@ -132,304 +134,361 @@ __device__ __forceinline__ long long off2(const DevParams<Real>& P, int x, int y
   return (long long)y * P.px + x;
 }
 
-// A(x) = lambda_mu^{n+1} / chi'(x) (0 in obstacle cells)
+// Shared-memory layout of the fused adjoint step.
 template <class Real>
-__device__ __forceinline__ Real adj_A(const DevParams<Real>& P, const AdjIO<Real>& io, long long o, bool obs) {
-  if (obs) return Real(0);
-  const Real e = P.inv2A[1] - P.inv2A[0];
-  const Real chi = P.inv2A[0] + Hs(io.s1[o]) * e;
-  return io.lmu1[o] / chi;
-}
+struct Adj2D {
+  static constexpr int BX = 32, BY = 16, NT = BX * BY;  // threads: tile + one-cell halo
+  static constexpr int OX = BX - 2, OY = BY - 2;        // output cells per CTA
+  static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;  // tile + two-cell halo
+  static constexpr int RING = 2 * W2 + 2 * BY;          // the outer ring of C2
+  static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 2 : 1;  // FP32: 64 registers, two CTAs per SM
+  enum { S0, S1, MU0, AA, UX, UY, NCELL };              // per-cell values
+  // per solute face: d/d mu_a, mu_b, s'_a, s'_b, U_a, U_b, s_a, s_b, and the
+  // transverse antitrapping coefficient T (+T to a+t, b+t; -T to a-t, b-t)
+  enum { F_MUA, F_MUB, F_SPA, F_SPB, F_UA, F_UB, F_SA, F_SB, F_T, NF };
+  static constexpr size_t cell = 0;
+  static constexpr size_t sface = cell + sizeof(Real) * NCELL * C2;  // [2][NF][C2] by a
+  static constexpr size_t lu = sface + sizeof(Real) * 2 * NF * C2;   // [NT]
+  static constexpr size_t mask = lu + sizeof(Real) * NT;             // [C2] bytes
+  static constexpr size_t bytes = mask + ((C2 + 15) / 16) * 16;
+  // the phase-field faces [2][cn, ct][NT] reuse the solute-face area
+};
 
 template <class Real>
-__global__ void __launch_bounds__(256) adj_mu_face_kernel(const DevParams<Real> P, const AdjIO<Real> io) {
-  const long long cells = (long long)P.n[0] * P.n[1];
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= cells) return;
-  int x, y;
-  cell_xy(P, c, &x, &y);
-  const long long oa = off2(P, x, y);
-  const bool walls = (P.wall[0] | P.wall[1]) != 0;
-  const bool obsA = walls && obstacle(P, x, y, 0);
+__global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_kernel(const DevParams<Real> P, const AdjIO<Real> io) {
+  using S = Adj2D<Real>;
+  using Lat = Lattice<9>;
+  constexpr int BX = S::BX, BY = S::BY, NT = S::NT, W2 = S::W2, C2 = S::C2, NF = S::NF;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Real* sc = reinterpret_cast<Real*>(smem + S::cell);
+  Real* sf = reinterpret_cast<Real*>(smem + S::sface);
+  Real* slu = reinterpret_cast<Real*>(smem + S::lu);
+  Real* spf = sf;
+  unsigned char* sm = smem + S::mask;
+
+  const int nx = P.n[0], ny = P.n[1];
+  const long long plane = P.plane;
+  const int tid = threadIdx.x, tx = tid % BX, ty = tid / BX;
+  const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY;
+  const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;  // this thread's cell, unfolded
+  // a tile whose two-cell halo lies inside the grid needs no folding
+  const bool inner_tile = x0 >= 2 && x0 - 2 + W2 <= nx && y0 >= 2 && y0 - 2 + S::H2 <= ny;
+  const int fx = inner_tile ? gx : fold_axis(P, gx, 0), fy = inner_tile ? gy : fold_axis(P, gy, 1);
+  const long long o = (long long)fy * P.px + fx;
+  const int h2 = (ty + 1) * W2 + tx + 1;  // this cell in the tile + two-cell halo
+  const bool inner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && gx < nx && gy < ny;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(io.clock[0]);
-  const Real A_a = adj_A(P, io, oa, obsA);
-  Real da[9];
+  const bool walls = (P.wall[0] | P.wall[1]) != 0;
+  const Real e = P.inv2A[1] - P.inv2A[0];
+  const Real mob = P.mob_eps * P.eps;  // 1 / tau_phi
+
+  // 0. per-cell values: own cell, then the outer ring
+  const Real s0 = __ldg(io.s0 + o), s1 = __ldg(io.s1 + o), mu0 = __ldg(io.mu0 + o);
+  const bool obs = walls && obstacle(P, fx, fy, 0);
+  Macro2<Real> m;
+  Real Aown;
+  {
+    Real dk[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) da[k] = io.d0[k * P.plane + oa];
-  const Macro2<Real> ma = macro2(P, da, io.s0[oa], io.mu0[oa], obsA, theta_base + P.G * Real(y));
+    for (int k = 0; k < 9; ++k) dk[k] = __ldg(io.d0 + k * plane + o);
+    m = macro2(P, dk, s0, mu0, obs, theta_base + P.G * Real(fy));
+    Aown = obs ? Real(0) : __ldg(io.lmu1 + o) / (P.inv2A[0] + Hs(s1) * e);
+    sc[S::S0 * C2 + h2] = s0;
+    sc[S::S1 * C2 + h2] = s1;
+    sc[S::MU0 * C2 + h2] = mu0;
+    sc[S::AA * C2 + h2] = Aown;
+    sc[S::UX * C2 + h2] = m.ux;
+    sc[S::UY * C2 + h2] = m.uy;
+    sm[h2] = (unsigned char)((s0 > Real(0) ? 2u : 0u) | (Real(1) - s0 > Real(0) ? 1u : 0u) | (obs ? 4u : 0u));
+  }
+  if (tid < S::RING) {
+    int ri, rj;
+    if (tid < W2) {
+      ri = tid;
+      rj = 0;
+    } else if (tid < 2 * W2) {
+      ri = tid - W2;
+      rj = S::H2 - 1;
+    } else if (tid < 2 * W2 + BY) {
+      ri = 0;
+      rj = tid - 2 * W2 + 1;
+    } else {
+      ri = W2 - 1;
+      rj = tid - 2 * W2 - BY + 1;
+    }
+    const int qx = inner_tile ? x0 - 2 + ri : fold_axis(P, x0 - 2 + ri, 0);
+    const int qy = inner_tile ? y0 - 2 + rj : fold_axis(P, y0 - 2 + rj, 1);
+    const long long q = (long long)qy * P.px + qx;
+    const Real rs0 = __ldg(io.s0 + q), rs1 = __ldg(io.s1 + q), rmu = __ldg(io.mu0 + q);
+    const bool robs = walls && obstacle(P, qx, qy, 0);
+    Real dk[9];
 #pragma unroll
-  for (int d = 0; d < 2; ++d) {
-    Real cf[kMF];
+    for (int k = 0; k < 9; ++k) dk[k] = __ldg(io.d0 + k * plane + q);
+    const Macro2<Real> rm = macro2(P, dk, rs0, rmu, robs, theta_base + P.G * Real(qy));
+    const int c = rj * W2 + ri;
+    sc[S::S0 * C2 + c] = rs0;
+    sc[S::S1 * C2 + c] = rs1;
+    sc[S::MU0 * C2 + c] = rmu;
+    sc[S::AA * C2 + c] = robs ? Real(0) : __ldg(io.lmu1 + q) / (P.inv2A[0] + Hs(rs1) * e);
+    sc[S::UX * C2 + c] = rm.ux;
+    sc[S::UY * C2 + c] = rm.uy;
+    sm[c] = (unsigned char)((rs0 > Real(0) ? 2u : 0u) | (Real(1) - rs0 > Real(0) ? 1u : 0u) | (robs ? 4u : 0u));
+  }
+  __syncthreads();
+
+  // 1. solute faces, by their lower cell a (tile + two-cell halo coordinates)
+  auto solute_face = [&](int ia, int ja, int d) {
+    Real cf[NF];
 #pragma unroll
-    for (int j = 0; j < kMF; ++j) cf[j] = Real(0);
-    const int bxr = d == 0 ? x + 1 : x, byr = d == 0 ? y : y + 1;
-    const int gbd = d == 0 ? bxr : byr;
-    bool closed = P.bc[d] == kWall && gbd == P.n[d];
-    const int bx = fold_axis(P, bxr, 0), by = fold_axis(P, byr, 1);
-    const bool obsB = walls && obstacle(P, bx, by, 0);
-    closed = closed || obsA || obsB;
+    for (int v = 0; v < NF; ++v) cf[v] = Real(0);
+    const int ca = ja * W2 + ia, cb = ca + (d == 0 ? 1 : W2), st = d == 0 ? W2 : 1;
+    const int gn = d == 0 ? x0 - 2 + ia : y0 - 2 + ja;  // a along the face normal
+    const int gt = d == 0 ? y0 - 2 + ja : x0 - 2 + ia;  // a across it
+    // the face exists only between two cells of the grid (walls do not wrap)
+    bool closed = P.bc[d] == kWall && (gn < 0 || gn >= P.n[d] - 1);
+    closed = closed || (P.bc[1 - d] == kWall && (gt < 0 || gt >= P.n[1 - d]));
+    closed = closed || ((sm[ca] | sm[cb]) & 4u);  // no solute crosses obstacle faces
     if (!closed) {
-      const long long ob = off2(P, bx, by);
-      const Real A_b = adj_A(P, io, ob, obsB);
-      const Real L = A_b - A_a;  // adjoint of the face flux
-      Real db[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) db[k] = io.d0[k * P.plane + ob];
-      const Macro2<Real> mb = macro2(P, db, io.s0[ob], io.mu0[ob], obsB, theta_base + P.G * Real(by));
-      const Real s0a = io.s0[oa], s0b = io.s0[ob], s1a = io.s1[oa], s1b = io.s1[ob];
-      const Real mua = io.mu0[oa], mub = io.mu0[ob];
-      const Real Mf = Real(0.5) * P.M0 * ((Real(1) - s1a) + (Real(1) - s1b));
+      const Real s0a = sc[S::S0 * C2 + ca], s0b = sc[S::S0 * C2 + cb];
+      const Real s1a = sc[S::S1 * C2 + ca], s1b = sc[S::S1 * C2 + cb];
+      const Real mua = sc[S::MU0 * C2 + ca], mub = sc[S::MU0 * C2 + cb];
+      const Real L = sc[S::AA * C2 + cb] - sc[S::AA * C2 + ca];  // adjoint of the face flux
+      const Real ua = sc[(d == 0 ? S::UX : S::UY) * C2 + ca], ub = sc[(d == 0 ? S::UX : S::UY) * C2 + cb];
       // diffusion -M_f (mu_b - mu_a), M = M0 (1 - s')
-      cf[0] += L * Mf;
-      cf[1] -= L * Mf;
-      cf[2] += L * Real(0.5) * P.M0 * (mub - mua);
-      cf[3] += L * Real(0.5) * P.M0 * (mub - mua);
-      // advection 1/2 [U_d h0' c0(mu)]_a + [...]_b, h0' = 1 - H(s')
-      const Real ua = d == 0 ? ma.ux : ma.uy, ub = d == 0 ? mb.ux : mb.uy;
+      const Real Mf = Real(0.5) * P.M0 * ((Real(1) - s1a) + (Real(1) - s1b));
+      const Real dM = L * Real(0.5) * P.M0 * (mub - mua);
+      cf[S::F_MUA] = L * Mf;
+      cf[S::F_MUB] = -L * Mf;
+      cf[S::F_SPA] = dM;
+      cf[S::F_SPB] = dM;
+      // advection 1/2 [U_d h0' c0(mu)]_a + [..]_b with h0' = 1 - H(s')
       const Real h0a = Real(1) - Hs(s1a), h0b = Real(1) - Hs(s1b);
       const Real c0a = P.ceq[0][0] + mua * P.inv2A[0], c0b = P.ceq[0][0] + mub * P.inv2A[0];
-      cf[4] += L * Real(0.5) * h0a * c0a;
-      cf[5] += L * Real(0.5) * h0b * c0b;
-      cf[0] += L * Real(0.5) * ua * h0a * P.inv2A[0];
-      cf[1] += L * Real(0.5) * ub * h0b * P.inv2A[0];
-      cf[2] -= L * Real(0.5) * ua * c0a * dHs(s1a);
-      cf[3] -= L * Real(0.5) * ub * c0b * dHs(s1b);
-      // antitrapping -a eps liq dc dphi nd
+      cf[S::F_UA] = L * Real(0.5) * h0a * c0a;
+      cf[S::F_UB] = L * Real(0.5) * h0b * c0b;
+      cf[S::F_MUA] += L * Real(0.5) * ua * h0a * P.inv2A[0];
+      cf[S::F_MUB] += L * Real(0.5) * ub * h0b * P.inv2A[0];
+      cf[S::F_SPA] -= L * Real(0.5) * ua * c0a * dHs(s1a);
+      cf[S::F_SPB] -= L * Real(0.5) * ub * c0b * dHs(s1b);
+      // antitrapping -a eps liq dc dphi n_d (liq, n at time n)
       if (P.at_eps != Real(0)) {
-        const int st_x = d == 0 ? 0 : 1, st_y = d == 0 ? 1 : 0;  // transverse unit step
-        const int ap_x = fold_axis(P, x + st_x, 0), ap_y = fold_axis(P, y + st_y, 1);
-        const int am_x = fold_axis(P, x - st_x, 0), am_y = fold_axis(P, y - st_y, 1);
-        const int bp_x = fold_axis(P, bxr + st_x, 0), bp_y = fold_axis(P, byr + st_y, 1);
-        const int bm_x = fold_axis(P, bxr - st_x, 0), bm_y = fold_axis(P, byr - st_y, 1);
-        const long long oap = off2(P, ap_x, ap_y), oam = off2(P, am_x, am_y);
-        const long long obp = off2(P, bp_x, bp_y), obm = off2(P, bm_x, bm_y);
-        const Real gn = s0b - s0a;
-        const Real gt = Real(0.25) * (io.s0[oap] + io.s0[obp] - io.s0[oam] - io.s0[obm]);
-        const Real g2 = gn * gn + gt * gt;
+        const Real g_n = s0b - s0a;
+        const Real g_t = Real(0.25) * (sc[S::S0 * C2 + ca + st] + sc[S::S0 * C2 + cb + st] -
+                                       sc[S::S0 * C2 + ca - st] - sc[S::S0 * C2 + cb - st]);
+        const Real g2 = g_n * g_n + g_t * g_t;
         if (g2 > Real(1e-12)) {
           const Real rg = Real(1) / sqrt(g2);
-          const Real nd = gn * rg;
+          const Real nd = g_n * rg;
           const Real liq = Real(1) - Real(0.5) * (s0a + s0b);
           const Real dinv = P.inv2A[0] - P.inv2A[1];
           const Real dc = (P.ceq[0][0] - P.ceq[1][0]) + Real(0.5) * (mua + mub) * dinv;
           const Real dphi = Real(0.5) * ((s1a - s0a) + (s1b - s0b));
           const Real k = -P.at_eps * L;
-          const Real jl = k * dc * dphi * nd;   // d/d liq
-          const Real jc = k * liq * dphi * nd;  // d/d dc
-          const Real jp = k * liq * dc * nd;    // d/d dphi
-          const Real jn = k * liq * dc * dphi;  // d/d nd
-          const Real dn_gn = gt * gt * rg * rg * rg;
-          const Real dn_gt = -gn * gt * rg * rg * rg;
-          cf[6] += -Real(0.5) * jl - Real(0.5) * jp - jn * dn_gn;
-          cf[7] += -Real(0.5) * jl - Real(0.5) * jp + jn * dn_gn;
-          cf[2] += Real(0.5) * jp;
-          cf[3] += Real(0.5) * jp;
-          cf[0] += Real(0.5) * dinv * jc;
-          cf[1] += Real(0.5) * dinv * jc;
-          const Real T = Real(0.25) * jn * dn_gt;
-          atomicAdd(io.ls0 + oap, T);
-          atomicAdd(io.ls0 + obp, T);
-          atomicAdd(io.ls0 + oam, -T);
-          atomicAdd(io.ls0 + obm, -T);
+          const Real jl = k * dc * dphi * nd;   // d / d liq
+          const Real jc = k * liq * dphi * nd;  // d / d dc
+          const Real jp = k * liq * dc * nd;    // d / d dphi
+          const Real jn = k * liq * dc * dphi;  // d / d n_d
+          const Real r3 = rg * rg * rg;
+          const Real dn_n = g_t * g_t * r3, dn_t = -g_n * g_t * r3;
+          cf[S::F_SA] += -Real(0.5) * jl - Real(0.5) * jp - jn * dn_n;
+          cf[S::F_SB] += -Real(0.5) * jl - Real(0.5) * jp + jn * dn_n;
+          cf[S::F_SPA] += Real(0.5) * jp;
+          cf[S::F_SPB] += Real(0.5) * jp;
+          cf[S::F_MUA] += Real(0.5) * dinv * jc;
+          cf[S::F_MUB] += Real(0.5) * dinv * jc;
+          cf[S::F_T] = Real(0.25) * jn * dn_t;
         }
       }
     }
 #pragma unroll
-    for (int j = 0; j < kMF; ++j) io.mface[(d * kMF + j) * P.plane + oa] = cf[j];
-  }
-}
+    for (int v = 0; v < NF; ++v) sf[(d * NF + v) * C2 + ca] = cf[v];
+  };
+  solute_face(tx + 1, ty + 1, 0);
+  solute_face(tx + 1, ty + 1, 1);
+  // the faces below the one-cell halo: a in the left column / bottom row
+  if (tid < BY) solute_face(0, tid + 1, 0);
+  else if (tid >= 32 && tid < 32 + BX) solute_face(tid - 32 + 1, 0, 1);
+  __syncthreads();
 
-template <class Real>
-__global__ void __launch_bounds__(256) adj_cell_kernel(const DevParams<Real> P, const AdjIO<Real> io) {
-  using Lat = Lattice<9>;
-  const long long cells = (long long)P.n[0] * P.n[1];
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= cells) return;
-  int x, y;
-  cell_xy(P, c, &x, &y);
-  const int nx = P.n[0], ny = P.n[1];
-  const long long o = off2(P, x, y);
-  const bool walls = (P.wall[0] | P.wall[1]) != 0;
-  const bool obs = walls && obstacle(P, x, y, 0);
-  const Real theta = Real(P.theta0) - Real(P.GV) * Real(io.clock[0]) + P.G * Real(y);
-  const Real s0 = io.s0[o], s1 = io.s1[o], mu0 = io.mu0[o], mu1 = io.mu1[o];
-  const Real e = P.inv2A[1] - P.inv2A[0];
-
-  Real lmu = Real(0), ls = Real(0), lsp = io.ls1[o], gUx = Real(0), gUy = Real(0);
-  // solute faces: this cell is a of its +x/+y faces and b of the faces below
+  // 2. lambda through the mu stage, the faces and the collision
+  auto F = [&](int d, int v, int c) { return sf[(d * NF + v) * C2 + c]; };
+  Real lsp = __ldg(io.ls1 + o) + F(0, S::F_SPA, h2) + F(1, S::F_SPA, h2) + F(0, S::F_SPB, h2 - 1) +
+             F(1, S::F_SPB, h2 - W2);
+  Real lmu = __ldg(io.lmu1 + o);
+  Real ls = Real(0);
+  const Real mu1 = __ldg(io.mu1 + o);
   if (!obs) {
-#pragma unroll
-    for (int d = 0; d < 2; ++d) {
-      const Real* fa = io.mface + (d * kMF) * P.plane;
-      lmu += fa[0 * P.plane + o];
-      lsp += fa[2 * P.plane + o];
-      ls += fa[6 * P.plane + o];
-      const Real ua = fa[4 * P.plane + o];
-      if (d == 0) gUx += ua; else gUy += ua;
-      const int lx = d == 0 ? x - 1 : x, ly = d == 0 ? y : y - 1;
-      const bool has_lower = P.bc[d] != kWall || (d == 0 ? x > 0 : y > 0);
-      if (has_lower) {
-        const long long ol = off2(P, fold_axis(P, lx, 0), fold_axis(P, ly, 1));
-        lmu += fa[1 * P.plane + ol];
-        lsp += fa[3 * P.plane + ol];
-        ls += fa[7 * P.plane + ol];
-        const Real ub = fa[5 * P.plane + ol];
-        if (d == 0) gUx += ub; else gUy += ub;
-      }
-    }
-  }
-  // mu update: mu' = mu + (-div J - src) / chi', src = (c1 - c0)(mu) (H(s') - H(s))
-  if (obs) {
-    lmu += io.lmu1[o];
-  } else {
-    const Real chi = P.inv2A[0] + Hs(s1) * e;
-    const Real A = io.lmu1[o] / chi;
-    const Real dH = Hs(s1) - Hs(s0);
-    lmu += io.lmu1[o] - A * e * dH;
+    // mu' = mu + (-div J - src) / chi', src = (c1 - c0)(mu) (H(s') - H(s))
     const Real c10 = (P.ceq[1][0] - P.ceq[0][0]) + mu0 * e;
-    lsp += -A * c10 * dHs(s1) + (-A * (mu1 - mu0)) * e * dHs(s1);
-    ls += A * c10 * dHs(s0);
+    lmu -= Aown * e * (Hs(s1) - Hs(s0));
+    lsp += -Aown * c10 * dHs(s1) - Aown * (mu1 - mu0) * e * dHs(s1);
+    ls += Aown * c10 * dHs(s0);
   }
-  // populations: pull transposed (bounce-back at walls), then BGK + Guo
-  Real dk[9], a[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    dk[k] = io.d0[k * P.plane + o];
-    const int cx = Lat::c(k, 0), cy = Lat::c(k, 1);
-    int tx = x + cx, ty = y + cy;
-    const bool bounce = (P.bc[0] == kWall && (tx < 0 || tx >= nx)) || (P.bc[1] == kWall && (ty < 0 || ty >= ny));
-    if (bounce) {
-      a[k] = io.ld1[Lat::opp(k) * P.plane + o];
-    } else {
-      tx = tx < 0 ? tx + nx : (tx >= nx ? tx - nx : tx);
-      ty = ty < 0 ? ty + ny : (ty >= ny ? ty - ny : ty);
-      a[k] = io.ld1[k * P.plane + off2(P, tx, ty)];
-    }
-  }
-  const Macro2<Real> m = macro2(P, dk, s0, mu0, obs, theta);
-  const Real omega = Real(1) - P.inv_tau_f, pre = P.force_pre, itau = P.inv_tau_f;
-  const Real uu = m.ux * m.ux + m.uy * m.uy;
-  Real gr = Real(0), gFx = Real(0), gFy = Real(0);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const Real cx = Real(Lat::c(k, 0)), cy = Real(Lat::c(k, 1)), wk = Real(Lat::w(k));
-    const Real cu = cx * m.ux + cy * m.uy, cF = cx * m.Fx + cy * m.Fy;
-    const Real ak = a[k];
-    // deq/tau: (w/tau)(drho - 1.5 rho U.U + rho cu (3 + 4.5 cu))
-    gr += ak * wk * itau * (Real(1) - Real(1.5) * uu + cu * (Real(3) + Real(4.5) * cu));
-    const Real gcu = ak * wk * (itau * m.rho * (Real(3) + Real(9) * cu) + pre * Real(9) * cF);
-    gUx += ak * wk * itau * (-Real(3) * m.rho * m.ux) + gcu * cx + ak * wk * (-Real(3) * pre * m.Fx);
-    gUy += ak * wk * itau * (-Real(3) * m.rho * m.uy) + gcu * cy + ak * wk * (-Real(3) * pre * m.Fy);
-    const Real gcF = ak * wk * pre * (Real(3) + Real(9) * cu);
-    gFx += ak * wk * (-Real(3) * pre * m.ux) + gcF * cx;
-    gFy += ak * wk * (-Real(3) * pre * m.uy) + gcF * cy;
-  }
-  // F = F_B e_y - rho kappa U;  U = (m + F_B/2 e_y) iv;  iv = 1/(rho (1 + kappa/2))
-  gUx += -m.rho * m.kappa * gFx;
-  gUy += -m.rho * m.kappa * gFy;
-  gr += -m.kappa * (m.ux * gFx + m.uy * gFy);
-  Real gk = -m.rho * (m.ux * gFx + m.uy * gFy);
-  Real gFB = gFy;
-  const Real gmx = gUx * m.iv, gmy = gUy * m.iv;
-  gFB += Real(0.5) * gUy * m.iv;
-  const Real giv = gUx * m.mx + gUy * (m.my + Real(0.5) * m.FB);
-  gr += giv * (-m.iv / m.rho);
-  gk += giv * (-Real(0.5) * m.rho * m.iv * m.iv);
-  // F_B = rho phil B
-  gr += gFB * m.phil * m.B;
-  const Real gphil = gFB * m.rho * m.B + gk * (-Real(2) * P.kappa0 * (Real(1) - m.phil));
-  const Real gB = gFB * m.rho * m.phil;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    const Real cx = Real(Lat::c(k, 0)), cy = Real(Lat::c(k, 1));
-    io.ld0[k * P.plane + o] = omega * a[k] + gr + cx * gmx + cy * gmy;
-  }
-  if (!obs) ls += -gphil;  // phil = 1 - s
-  lmu += gB * P.gbeta_c[0] * P.inv2A[0];
-  io.gacc[2 * P.plane + o] += (double)(gB * (P.dcl_ref[0] + mu0 * P.inv2A[0]));
-
-  // phase field: s' = clamp(u) where both phases are present, s' = s elsewhere
   bool multi = false;
   if (!obs) {
     unsigned act = 0;
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const Real v = io.s0[off2(P, fold_axis(P, x + dx, 0), fold_axis(P, y + dy, 1))];
-        if (v > Real(0)) act |= 2u;
-        if (Real(1) - v > Real(0)) act |= 1u;
-      }
-    multi = act == 3u;
+      for (int dx = -1; dx <= 1; ++dx) act |= sm[h2 + dy * W2 + dx];
+    multi = (act & 3u) == 3u;
   }
-  Real lu = Real(0);
-  if (multi) {
-    if (s1 > Real(0) && s1 < Real(1)) {
-      lu = lsp;
-      const Real mob = P.mob_eps * P.eps;  // 1 / tau_phi
-      const Real dpsi = -mu0 * mu0 * (P.inv4A[1] - P.inv4A[0]) - mu0 * (P.ceq[1][0] - P.ceq[0][0]) +
-                        (P.S[1] - P.S[0]) * theta;
-      const Real dpsi_dmu = -mu0 * e - (P.ceq[1][0] - P.ceq[0][0]);
-      const Real cob = P.obst * P.gamma[0][1] / P.eps;  // 16 gamma / (pi^2 eps^2)
-      ls += lu * (Real(1) + Real(0.5) * mob *
-                                (Real(2) * cob - (Real(6) / P.eps) * (Real(1) - Real(2) * s0) * dpsi));
-      lmu += lu * Real(0.5) * mob * (-(Real(6) / P.eps) * s0 * (Real(1) - s0) * dpsi_dmu);
-      io.gacc[0 * P.plane + o] += (double)(lu * (s1 - s0) / mob);
-    }
-  } else {
-    ls += lsp;
-  }
-  io.lu[o] = lu;
-  io.lmu0[o] = lmu;
-  io.ls0[o] += ls;
-}
+  const Real lu = (multi && s1 > Real(0) && s1 < Real(1)) ? lsp : Real(0);
+  slu[tid] = lu;
 
-// Phase-field faces: lambda_V = (mob/2) gamma (lu(a) - lu(b)) through
-// V_d = dA/dq_d(grad_f s) to the six cells of the face stencil.
-template <class Real>
-__global__ void __launch_bounds__(256) adj_pf_face_kernel(const DevParams<Real> P, const AdjIO<Real> io) {
-  const long long cells = (long long)P.n[0] * P.n[1];
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= cells) return;
-  int x, y;
-  cell_xy(P, c, &x, &y);
-  const long long oa = off2(P, x, y);
-  const Real mob = P.mob_eps * P.eps;
-  const Real gam = P.gamma[0][1];
-  const Real lua = io.lu[oa];
-#pragma unroll
-  for (int d = 0; d < 2; ++d) {
-    const int bxr = d == 0 ? x + 1 : x, byr = d == 0 ? y : y + 1;
-    const int gbd = d == 0 ? bxr : byr;
-    if (P.bc[d] == kWall && gbd == P.n[d]) continue;  // closed face
-    const long long ob = off2(P, fold_axis(P, bxr, 0), fold_axis(P, byr, 1));
-    const Real lV = Real(0.5) * mob * gam * (lua - io.lu[ob]);
-    if (lV == Real(0)) continue;
-    const int st_x = d == 0 ? 0 : 1, st_y = d == 0 ? 1 : 0;
-    const long long oap = off2(P, fold_axis(P, x + st_x, 0), fold_axis(P, y + st_y, 1));
-    const long long oam = off2(P, fold_axis(P, x - st_x, 0), fold_axis(P, y - st_y, 1));
-    const long long obp = off2(P, fold_axis(P, bxr + st_x, 0), fold_axis(P, byr + st_y, 1));
-    const long long obm = off2(P, fold_axis(P, bxr - st_x, 0), fold_axis(P, byr - st_y, 1));
-    const Real gn = io.s0[ob] - io.s0[oa];
-    const Real gt = Real(0.25) * (io.s0[oap] + io.s0[obp] - io.s0[oam] - io.s0[obm]);
-    // q[d] = gn, q[1-d] = gt; tangents of V_d along q_d, q_{1-d} and delta
-    Real dV[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      Tan<Real> q[2];
-      q[d] = Tan<Real>(gn, j == 0 ? Real(1) : Real(0));
-      q[1 - d] = Tan<Real>(gt, j == 1 ? Real(1) : Real(0));
-      const Tan<Real> dl(P.delta[0][1], j == 2 ? Real(1) : Real(0));
-      dV[j] = dAdq_tan<Real>(q, dl, P.q_floor, d).d;
+  if (inner) {
+    lmu += F(0, S::F_MUA, h2) + F(1, S::F_MUA, h2) + F(0, S::F_MUB, h2 - 1) + F(1, S::F_MUB, h2 - W2);
+    ls += F(0, S::F_SA, h2) + F(1, S::F_SA, h2) + F(0, S::F_SB, h2 - 1) + F(1, S::F_SB, h2 - W2);
+    // antitrapping across x-faces (transverse y) and y-faces (transverse x)
+    ls += F(0, S::F_T, h2 - W2) + F(0, S::F_T, h2 - W2 - 1) - F(0, S::F_T, h2 + W2) - F(0, S::F_T, h2 + W2 - 1);
+    ls += F(1, S::F_T, h2 - 1) + F(1, S::F_T, h2 - 1 - W2) - F(1, S::F_T, h2 + 1) - F(1, S::F_T, h2 + 1 - W2);
+    if (P.bc[1] == kWall) {  // the wall mirrors a-t / a+t onto the row next to it
+      if (gy == 0) ls -= F(0, S::F_T, h2) + F(0, S::F_T, h2 - 1);
+      if (gy == ny - 1) ls += F(0, S::F_T, h2) + F(0, S::F_T, h2 - 1);
     }
-    const Real cn = lV * dV[0], ct = Real(0.25) * lV * dV[1];
-    atomicAdd(io.ls0 + ob, cn);
-    atomicAdd(io.ls0 + oa, -cn);
-    atomicAdd(io.ls0 + oap, ct);
-    atomicAdd(io.ls0 + obp, ct);
-    atomicAdd(io.ls0 + oam, -ct);
-    atomicAdd(io.ls0 + obm, -ct);
-    io.gacc[1 * P.plane + oa] += (double)(lV * dV[2]);
+    if (P.bc[0] == kWall) {
+      if (gx == 0) ls -= F(1, S::F_T, h2) + F(1, S::F_T, h2 - W2);
+      if (gx == nx - 1) ls += F(1, S::F_T, h2) + F(1, S::F_T, h2 - W2);
+    }
+    Real gUx = F(0, S::F_UA, h2) + F(0, S::F_UB, h2 - 1);
+    Real gUy = F(1, S::F_UA, h2) + F(1, S::F_UB, h2 - W2);
+
+    // populations: pull transposed (bounce-back at walls), then BGK + Guo
+    Real a[9];
+    if (fx >= 1 && fx <= nx - 2 && fy >= 1 && fy <= ny - 2) {  // no wall or wrap in reach
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a[k] = __ldg(io.ld1 + k * plane + o + Lat::c(k, 0) + Lat::c(k, 1) * P.px);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        int qx = fx + Lat::c(k, 0), qy = fy + Lat::c(k, 1);
+        const bool bounce = (P.bc[0] == kWall && (qx < 0 || qx >= nx)) || (P.bc[1] == kWall && (qy < 0 || qy >= ny));
+        if (bounce) {
+          a[k] = __ldg(io.ld1 + Lat::opp(k) * plane + o);
+        } else {
+          qx = qx < 0 ? qx + nx : (qx >= nx ? qx - nx : qx);
+          qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
+          a[k] = __ldg(io.ld1 + k * plane + (long long)qy * P.px + qx);
+        }
+      }
+    }
+    // f*_k = omega d_k + (feq_k - w_k) / tau + G_k is a quadratic in U and
+    // linear in F and rho, so its transpose needs only the moments of
+    // a_k w_k: S0 = sum, S1 = sum c_k, S2 = sum c_k c_k.
+    Real S0 = Real(0), S1x = Real(0), S1y = Real(0), Sxx = Real(0), Sxy = Real(0), Syy = Real(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const Real aw = a[k] * Real(Lat::w(k));
+      const int cx = Lat::c(k, 0), cy = Lat::c(k, 1);
+      S0 += aw;
+      if (cx) S1x += cx > 0 ? aw : -aw;
+      if (cy) S1y += cy > 0 ? aw : -aw;
+      if (cx) Sxx += aw;
+      if (cy) Syy += aw;
+      if (cx && cy) Sxy += cx * cy > 0 ? aw : -aw;
+    }
+    const Real omega = Real(1) - P.inv_tau_f, pre = P.force_pre, itau = P.inv_tau_f;
+    const Real uu = m.ux * m.ux + m.uy * m.uy;
+    const Real SUx = Sxx * m.ux + Sxy * m.uy, SUy = Sxy * m.ux + Syy * m.uy;  // S2 U
+    const Real SFx = Sxx * m.Fx + Sxy * m.Fy, SFy = Sxy * m.Fx + Syy * m.Fy;  // S2 F
+    // V = -3 U S0 + 3 S1 + 9 S2 U: d/dF = pre V, d/dU = rho V / tau - 3 pre F S0 + 9 pre S2 F
+    const Real Vx = Real(-3) * m.ux * S0 + Real(3) * S1x + Real(9) * SUx;
+    const Real Vy = Real(-3) * m.uy * S0 + Real(3) * S1y + Real(9) * SUy;
+    Real gr = itau * (S0 * (Real(1) - Real(1.5) * uu) + Real(3) * (m.ux * S1x + m.uy * S1y) +
+                      Real(4.5) * (m.ux * SUx + m.uy * SUy));
+    gUx += itau * m.rho * Vx + pre * (Real(-3) * m.Fx * S0 + Real(9) * SFx);
+    gUy += itau * m.rho * Vy + pre * (Real(-3) * m.Fy * S0 + Real(9) * SFy);
+    const Real gFx = pre * Vx, gFy = pre * Vy;
+    // F = F_B e_y - rho kappa U;  U = (m + F_B/2 e_y) iv;  iv = 1/(rho (1 + kappa/2))
+    gUx += -m.rho * m.kappa * gFx;
+    gUy += -m.rho * m.kappa * gFy;
+    gr += -m.kappa * (m.ux * gFx + m.uy * gFy);
+    Real gk = -m.rho * (m.ux * gFx + m.uy * gFy);
+    Real gFB = gFy + Real(0.5) * gUy * m.iv;
+    const Real gmx = gUx * m.iv, gmy = gUy * m.iv;
+    const Real giv = gUx * m.mx + gUy * (m.my + Real(0.5) * m.FB);
+    gr += giv * (-m.iv / m.rho);
+    gk += giv * (-Real(0.5) * m.rho * m.iv * m.iv);
+    gr += gFB * m.phil * m.B;  // F_B = rho phil B
+    const Real gphil = gFB * m.rho * m.B + gk * (-Real(2) * P.kappa0 * (Real(1) - m.phil));
+    const Real gB = gFB * m.rho * m.phil;
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+      io.ld0[k * plane + o] = omega * a[k] + gr + Real(Lat::c(k, 0)) * gmx + Real(Lat::c(k, 1)) * gmy;
+    if (!obs) ls -= gphil;  // phil = 1 - s
+    lmu += gB * P.gbeta_c[0] * P.inv2A[0];
+    io.gacc[2 * plane + o] += (double)(gB * (P.dcl_ref[0] + mu0 * P.inv2A[0]));
+
+    // phase field: s' = clamp(u) where both phases are present, s' = s elsewhere
+    if (multi) {
+      if (lu != Real(0)) {
+        const Real dpsi = -mu0 * mu0 * (P.inv4A[1] - P.inv4A[0]) - mu0 * (P.ceq[1][0] - P.ceq[0][0]) +
+                          (P.S[1] - P.S[0]) * (theta_base + P.G * Real(fy));
+        const Real dpsi_dmu = -mu0 * e - (P.ceq[1][0] - P.ceq[0][0]);
+        const Real cob = P.obst * P.gamma[0][1] / P.eps;  // 16 gamma / (pi^2 eps^2)
+        ls += lu * (Real(1) + Real(0.5) * mob * (Real(2) * cob - (Real(6) / P.eps) * (Real(1) - Real(2) * s0) * dpsi));
+        lmu += lu * Real(0.5) * mob * (-(Real(6) / P.eps) * s0 * (Real(1) - s0) * dpsi_dmu);
+        io.gacc[0 * plane + o] += (double)(lu * (s1 - s0) / mob);
+      }
+    } else {
+      ls += lsp;
+    }
+    io.lmu0[o] = lmu;
+  }
+  __syncthreads();
+
+  // 3. phase-field faces: lambda_V = (mob/2) gamma (lu(a) - lu(b)) through
+  //    V_d = dA/dq_d(grad_f s) to the six cells of the face stencil
+  {
+    const Real gam = P.gamma[0][1];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      Real cn = Real(0), ct = Real(0);
+      const bool has = d == 0 ? tx <= BX - 2 : ty <= BY - 2;  // b inside the one-cell halo
+      const int gn = d == 0 ? gx : gy, gt = d == 0 ? gy : gx;
+      const bool closed = (P.bc[d] == kWall && (gn < 0 || gn >= P.n[d] - 1)) ||
+                          (P.bc[1 - d] == kWall && (gt < 0 || gt >= P.n[1 - d]));
+      if (has && !closed) {
+        const Real lV = Real(0.5) * mob * gam * (lu - slu[tid + (d == 0 ? 1 : BX)]);
+        if (lV != Real(0)) {
+          const int ca = h2, cb = h2 + (d == 0 ? 1 : W2), st = d == 0 ? W2 : 1;
+          const Real g_n = sc[S::S0 * C2 + cb] - sc[S::S0 * C2 + ca];
+          const Real g_t = Real(0.25) * (sc[S::S0 * C2 + ca + st] + sc[S::S0 * C2 + cb + st] -
+                                         sc[S::S0 * C2 + ca - st] - sc[S::S0 * C2 + cb - st]);
+          Real dV[3];
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            Tan<Real> q[2];
+            q[d] = Tan<Real>(g_n, j == 0 ? Real(1) : Real(0));
+            q[1 - d] = Tan<Real>(g_t, j == 1 ? Real(1) : Real(0));
+            const Tan<Real> dl(P.delta[0][1], j == 2 ? Real(1) : Real(0));
+            dV[j] = dAdq_tan<Real>(q, dl, P.q_floor, d).d;
+          }
+          cn = lV * dV[0];
+          ct = Real(0.25) * lV * dV[1];
+          if (inner) io.gacc[1 * plane + o] += (double)(lV * dV[2]);
+        }
+      }
+      spf[(d * 2 + 0) * NT + tid] = cn;
+      spf[(d * 2 + 1) * NT + tid] = ct;
+    }
+  }
+  __syncthreads();
+  if (inner) {
+    auto CN = [&](int d, int t) { return spf[(d * 2 + 0) * NT + t]; };
+    auto CT = [&](int d, int t) { return spf[(d * 2 + 1) * NT + t]; };
+    ls += CN(0, tid - 1) - CN(0, tid) + CN(1, tid - BX) - CN(1, tid);
+    ls += CT(0, tid - BX) + CT(0, tid - BX - 1) - CT(0, tid + BX) - CT(0, tid + BX - 1);
+    ls += CT(1, tid - 1) + CT(1, tid - 1 - BX) - CT(1, tid + 1) - CT(1, tid + 1 - BX);
+    if (P.bc[1] == kWall) {
+      if (gy == 0) ls -= CT(0, tid) + CT(0, tid - 1);
+      if (gy == ny - 1) ls += CT(0, tid) + CT(0, tid - 1);
+    }
+    if (P.bc[0] == kWall) {
+      if (gx == 0) ls -= CT(1, tid) + CT(1, tid - BX);
+      if (gx == nx - 1) ls += CT(1, tid) + CT(1, tid - BX);
+    }
+    io.ls0[o] = ls;
   }
 }
 

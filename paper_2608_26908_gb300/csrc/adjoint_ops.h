@@ -21,14 +21,14 @@ struct AdjStepIO {
   void* ls0;        // adjoint of S^n (written)
   void* lmu0;
   void* ld0;
-  void* mface;      // scratch: 16 planes
-  void* lu;         // scratch: 1 plane
   double* gacc;     // 3 FP64 planes, accumulated
   const double* clock;  // time of step n (device)
 };
 
 struct AdjOps {
   size_t real_size;
+  // opts the step kernel in to its dynamic shared memory
+  cudaError_t (*configure)();
   // lambda of the final state from w_frac mean h_1; clears gacc
   cudaError_t (*init)(const void* P, const void* s, double w_frac, void* ls, void* lmu, void* ld,
                       double* gacc, cudaStream_t st);
@@ -37,7 +37,7 @@ struct AdjOps {
                      double* tip, cudaStream_t st);
   // fixed-order partial sums of h_1 over the cells (blocks partials)
   cudaError_t (*frac)(const void* P, const void* s, double* partial, int blocks, cudaStream_t st);
-  // one adjoint step lambda^{n+1} -> lambda^n (four launches)
+  // one adjoint step lambda^{n+1} -> lambda^n (one launch)
   cudaError_t (*step)(const void* P, const AdjStepIO& io, cudaStream_t st);
   // fixed-order partial sums of an FP64 plane over the cells
   cudaError_t (*sum)(const void* P, const double* v, double* partial, int blocks, cudaStream_t st);

@@ -49,6 +49,9 @@ struct gpflbm_s {
   long long t;        // step counter of the current state
   bool has_state;
   cudaStream_t capture;
+  // adjoint: the stream that recomputes segments, and its events
+  cudaStream_t aux;
+  cudaEvent_t ev_fwd, ev_aux_end, ev_rec[2], ev_adj[2];
   cudaGraphExec_t chunk_graph[2];
   cudaGraphExec_t pair_graph[2];
   // device parameters in the arithmetic type (only one is used)
@@ -586,6 +589,15 @@ void gpflbm_destroy(gpflbm_t h) {
   if (!h) return;
   drop_graphs(h);
   if (h->capture) cudaStreamDestroy(h->capture);
+  if (h->aux) {
+    cudaStreamDestroy(h->aux);
+    cudaEventDestroy(h->ev_fwd);
+    cudaEventDestroy(h->ev_aux_end);
+    for (int i = 0; i < 2; ++i) {
+      cudaEventDestroy(h->ev_rec[i]);
+      cudaEventDestroy(h->ev_adj[i]);
+    }
+  }
   if (h->owns_ws) cudaFree(h->ws);
   delete h;
 }
@@ -682,18 +694,27 @@ extern "C" gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, dou
 // ---------------------------------------------------------------------------
 // Adjoint with checkpointing (2D, two phases, one solute).
 //
-// Workspace: ceil(H/K) checkpoints, K recomputed states of one segment (the
-// segment's first state is its checkpoint), one clock per stored state, two
-// adjoint states (ping-pong), 16 solute-face and 1 phase-field scratch
-// planes, 3 FP64 accumulator planes and the reduction partials.  A stored
-// state is 11 planes: phi_1, mu, f - w (9).
+// Workspace: ceil(H/K) checkpoints, two sets of K segment states, one clock
+// per stored state, two adjoint states (ping-pong), 3 FP64 accumulator
+// planes and the reduction partials.  A stored state is 11 planes: phi_1,
+// mu, f - w (9).
+//
+// Schedule.  The forward pass steps from checkpoint to checkpoint through
+// the segment slots (segment c: ckpt[c] -> seg[c % 2][0] -> ... ->
+// ckpt[c+1]); the last segment stays in its slots, so the backward pass
+// starts without a recompute.  Every earlier segment is recomputed from its
+// checkpoint (K - 1 steps) on a second stream into the other set of slots
+// while the adjoint steps of the segment after it run: the two kernels
+// share the SMs and fill each other's idle tail.  Events order a recompute
+// after the adjoint that last read its slots, and an adjoint after its
+// recompute.  Forward steps in total: H + (ceil(H/K) - 1) (K - 1).
 
 namespace {
 
 struct AdjLayout {
   size_t state;  // bytes of one stored state
   int n_ck, K;
-  size_t ckpt, seg, clk, lam[2], mface, lu, gacc, partial, tip, total;
+  size_t ckpt, seg[2], clk, lam[2], gacc, partial, tip, total;
 };
 
 AdjLayout adj_layout(gpflbm_t h, int H, int K) {
@@ -709,11 +730,9 @@ AdjLayout adj_layout(gpflbm_t h, int H, int K) {
     return a;
   };
   L.ckpt = take((size_t)L.n_ck * L.state);
-  L.seg = take((size_t)L.K * L.state);
-  L.clk = take((size_t)(L.n_ck + L.K + 1) * sizeof(double));
+  for (int i = 0; i < 2; ++i) L.seg[i] = take((size_t)L.K * L.state);
+  L.clk = take((size_t)(L.n_ck + 2 * L.K) * sizeof(double));
   for (int i = 0; i < 2; ++i) L.lam[i] = take(L.state);
-  L.mface = take(16 * pl);
-  L.lu = take(pl);
   L.gacc = take(3 * (size_t)h->plane * sizeof(double));
   L.partial = take(4 * (size_t)gpflbm::kRedMaxBlocks * sizeof(double));
   L.tip = take(sizeof(double));
@@ -736,27 +755,69 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
   const gpflbm::AdjOps* A = gpflbm::adjoint_ops(h->grid.precision == GPFLBM_FP64);
   const void* P = dev_params(h);
   const size_t pl = (size_t)h->plane * h->ops->real_size;
-  const int K = L.K;
+  const int K = L.K, n_ck = L.n_ck;
   double* clk = reinterpret_cast<double*>(ws + L.clk);
-  cudaError_t e = cudaSuccess;
-  auto stored = [&](size_t base, int i) { return ws + base + (size_t)i * L.state; };
-
-  // forward pass through the handle's own buffers, keeping checkpoints
-  for (int c = 0; c < L.n_ck; ++c) {
-    unsigned char* ck = stored(L.ckpt, c);
-    e = cudaMemcpyAsync(ck, at(h, h->lay.phi[h->cur]), pl, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ck + pl, at(h, h->lay.mu[h->cur]), pl, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ck + 2 * pl, at(h, h->lay.f[h->cur]), 9 * pl, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(clk + c, reinterpret_cast<double*>(at(h, h->lay.clock)) + h->cur, sizeof(double),
-                          cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: checkpoint copy");
-    const int len = H - c * K < K ? H - c * K : K;
-    gpflbm_status st = gpflbm_step(h, len, s);
-    if (st != GPFLBM_OK) return st;
+  int* err = reinterpret_cast<int*>(at(h, h->lay.err));
+  cudaError_t e = A->configure();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: configure");
+  if (!h->aux) {
+    e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
+    cudaEvent_t* evs[6] = {&h->ev_fwd, &h->ev_aux_end, &h->ev_rec[0], &h->ev_rec[1], &h->ev_adj[0], &h->ev_adj[1]};
+    for (int i = 0; i < 6 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(evs[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: stream and events");
   }
+  auto ckpt = [&](int c) { return ws + L.ckpt + (size_t)c * L.state; };
+  auto seg_len = [&](int c) { return H - c * K < K ? H - c * K : K; };
+  // state j (0..len) of segment c and its clock slot
+  auto st_at = [&](int c, int j) {
+    if (j == 0) return ckpt(c);
+    if (j == seg_len(c) && c + 1 < n_ck) return ckpt(c + 1);
+    return ws + L.seg[c & 1] + (size_t)(j - 1) * L.state;
+  };
+  auto clk_at = [&](int c, int j) {
+    if (j == 0) return clk + c;
+    if (j == seg_len(c) && c + 1 < n_ck) return clk + c + 1;
+    return clk + n_ck + (c & 1) * K + (j - 1);
+  };
+  auto step = [&](int c, int j, cudaStream_t st) {
+    gpflbm::StepIO io;
+    unsigned char* in = st_at(c, j);
+    unsigned char* out = st_at(c, j + 1);
+    io.phi_in = in;
+    io.mu_in = in + pl;
+    io.f_in = in + 2 * pl;
+    io.phi_out = out;
+    io.mu_out = out + pl;
+    io.f_out = out + 2 * pl;
+    io.clock_in = clk_at(c, j);
+    io.clock_out = clk_at(c, j + 1);
+    io.err = err;
+    return h->ops->step(P, io, st);
+  };
+  // copies of one stored state: handle -> slot, or slot -> handle
+  auto copy_state = [&](unsigned char* slot, double* slot_clk, bool to_slot) {
+    void* hp[4] = {at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]), at(h, h->lay.f[h->cur]),
+                   reinterpret_cast<double*>(at(h, h->lay.clock)) + h->cur};
+    void* sp[4] = {slot, slot + pl, slot + 2 * pl, slot_clk};
+    const size_t n[4] = {pl, pl, 9 * pl, sizeof(double)};
+    cudaError_t r = cudaSuccess;
+    for (int i = 0; i < 4 && r == cudaSuccess; ++i)
+      r = cudaMemcpyAsync(to_slot ? sp[i] : hp[i], to_slot ? hp[i] : sp[i], n[i], cudaMemcpyDeviceToDevice, s);
+    return r;
+  };
+
+  // forward pass: checkpoints, and the last segment kept whole
+  e = copy_state(ckpt(0), clk, true);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: checkpoint copy");
+  for (int c = 0; c < n_ck; ++c)
+    for (int j = 0; j < seg_len(c); ++j) {
+      e = step(c, j, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: forward step");
+    }
+  const int last = n_ck - 1;
+  e = copy_state(st_at(last, seg_len(last)), clk_at(last, seg_len(last)), false);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: final state");
+  h->t += H;
 
   // objective of the final state and the adjoint state it seeds
   unsigned char* lam[2] = {ws + L.lam[0], ws + L.lam[1]};
@@ -765,54 +826,57 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
   double* tip = reinterpret_cast<double*>(ws + L.tip);
   const long long want = (h->cells + gpflbm::kRedThreads - 1) / gpflbm::kRedThreads;
   const int blocks = (int)(want < gpflbm::kRedMaxBlocks ? want : gpflbm::kRedMaxBlocks);
-  const void* s_fin = at(h, h->lay.phi[h->cur]);
+  const void* s_fin = st_at(last, seg_len(last));
   e = A->frac(P, s_fin, partial, blocks, s);
   if (e == cudaSuccess) e = A->init(P, s_fin, obj->w_frac, lam[0], lam[0] + pl, lam[0] + 2 * pl, gacc, s);
   if (e == cudaSuccess) e = A->tip(P, s_fin, obj->x0, obj->y0, obj->kappa, obj->w_tip, lam[0], tip, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: objective");
 
-  // backward: recompute each segment from its checkpoint, then step back
+  // backward: segment c's adjoint steps on `s` while segment c-1 is
+  // recomputed on the auxiliary stream
+  e = cudaEventRecord(h->ev_fwd, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_fwd, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: stream order");
   int cur = 0;
-  for (int c = L.n_ck - 1; c >= 0; --c) {
-    const int len = H - c * K < K ? H - c * K : K;
-    auto st_at = [&](int j) { return j == 0 ? stored(L.ckpt, c) : stored(L.seg, j - 1); };
-    auto clk_at = [&](int j) { return j == 0 ? clk + c : clk + L.n_ck + j; };
-    for (int j = 0; j < len; ++j) {
-      gpflbm::StepIO io;
-      io.phi_in = st_at(j);
-      io.mu_in = st_at(j) + pl;
-      io.f_in = st_at(j) + 2 * pl;
-      io.phi_out = st_at(j + 1);
-      io.mu_out = st_at(j + 1) + pl;
-      io.f_out = st_at(j + 1) + 2 * pl;
-      io.clock_in = clk_at(j);
-      io.clock_out = clk_at(j + 1);
-      io.err = reinterpret_cast<int*>(at(h, h->lay.err));
-      e = h->ops->step(P, io, s);
+  for (int c = last; c >= 0; --c) {
+    if (c >= 1) {
+      // segment c-1 reuses the slots segment c+1 was read from
+      if (c + 1 <= last) e = cudaStreamWaitEvent(h->aux, h->ev_adj[(c + 1) & 1], 0);
+      for (int j = 0; j + 1 < seg_len(c - 1) && e == cudaSuccess; ++j) e = step(c - 1, j, h->aux);
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev_rec[(c - 1) & 1], h->aux);
       if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: recompute");
     }
-    for (int j = len - 1; j >= 0; --j) {
+    if (c < last) {
+      e = cudaStreamWaitEvent(s, h->ev_rec[c & 1], 0);
+      if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: stream order");
+    }
+    for (int j = seg_len(c) - 1; j >= 0; --j) {
       gpflbm::AdjStepIO a;
-      a.s0 = st_at(j);
-      a.mu0 = st_at(j) + pl;
-      a.d0 = st_at(j) + 2 * pl;
-      a.s1 = st_at(j + 1);
-      a.mu1 = st_at(j + 1) + pl;
+      unsigned char* s0 = st_at(c, j);
+      unsigned char* s1 = st_at(c, j + 1);
+      a.s0 = s0;
+      a.mu0 = s0 + pl;
+      a.d0 = s0 + 2 * pl;
+      a.s1 = s1;
+      a.mu1 = s1 + pl;
       a.ls1 = lam[cur];
       a.lmu1 = lam[cur] + pl;
       a.ld1 = lam[cur] + 2 * pl;
       a.ls0 = lam[1 - cur];
       a.lmu0 = lam[1 - cur] + pl;
       a.ld0 = lam[1 - cur] + 2 * pl;
-      a.mface = ws + L.mface;
-      a.lu = ws + L.lu;
       a.gacc = gacc;
-      a.clock = clk_at(j);
+      a.clock = clk_at(c, j);
       e = A->step(P, a, s);
       if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: step");
       cur = 1 - cur;
     }
+    e = cudaEventRecord(h->ev_adj[c & 1], s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: stream order");
   }
+  e = cudaEventRecord(h->ev_aux_end, h->aux);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_aux_end, 0);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: stream order");
 
   // outputs
   if (dmu0) {
