@@ -15,6 +15,8 @@ Prints one JSON line (rank 0):
               measured HBM copy bandwidth
   cpu_baseline the FP64 CPU oracle timed on the host cores on a sample
   clocks      nvidia-smi samples taken during the timed region
+  adjoint     the adjoint/forward time ratio on the 512 x 512 differentiation
+              workload (500 steps, checkpoints every 50)
 
 --impl reference times the FP64 CPU oracle on the same workload instead.
 Under torchrun every rank runs its own replica of the workload (the path has
@@ -54,6 +56,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--adjoint-horizon", type=int, default=500)
+    ap.add_argument("--adjoint-ckpt", type=int, default=50)
+    ap.add_argument("--adjoint-reps", type=int, default=5)
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -188,11 +194,75 @@ def cpu_baseline(sc, seconds):
                 steps, sc["name"], cells)}
 
 
+def adjoint_ratio(args):
+    """Adjoint/forward time ratio on the differentiation workload: 2D
+    dendrite 512 x 512, D2Q9, two phases, one solute, FP32, J = solid
+    fraction + soft-argmax tip after a 500-step horizon, checkpoints every
+    50 steps.  forward_ms: gpflbm_step(500); adjoint_ms: one gpflbm_adjoint
+    call (its own forward pass with checkpoints, the recompute of every
+    earlier segment and the 500 adjoint steps) giving dJ/d(mu0, 1/tau_phi,
+    delta, g beta_c).  Both start from the same state; the 23 MB state fits
+    in L2, so neither flushes it."""
+    import statistics as st
+
+    import torch
+
+    from paper_2608_26908_gb300 import gpflbm
+
+    sc = inputs.scenario("adjoint2d")
+    H, K = args.adjoint_horizon, args.adjoint_ckpt
+    nx, ny, _ = inputs.dims(sc)
+    obj = {"w_frac": 1.0, "w_tip": 1.0, "kappa": 2.0, "x0": nx // 2, "y0": ny // 2, "solid": 1}
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    ws = torch.empty(sim.adjoint_workspace_bytes(H, K), dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        sim.set_state(phi0, mu0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    fwd = lambda: sim.step(H)  # noqa: E731
+    adj = lambda: sim.adjoint(obj, H, K, device=True, workspace=ws)  # noqa: E731
+    for _ in range(2):
+        timed(fwd)
+        timed(adj)
+    f_ms = [timed(fwd) for _ in range(args.adjoint_reps)]
+    a_ms = [timed(adj) for _ in range(args.adjoint_reps)]
+    f, a = st.median(f_ms), st.median(a_ms)
+    sim.close()
+    return {"workload": "adjoint2d %dx%d D2Q9 N=2 K-1=1 fp32" % (nx, ny), "horizon": H, "ckpt_every": K,
+            "forward_ms": f, "adjoint_ms": a, "ratio": a / f, "target_max": 4.0,
+            "reps": args.adjoint_reps, "workspace_mb": ws.numel() / 1e6,
+            "gradient": "dJ/d(mu0 plane, 1/tau_phi, delta, gbeta_c)"}
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(seconds, pg, device="cpu"):
+    """The largest of every rank's time (the job ends with its slowest rank)."""
+    if pg is None:
+        return seconds
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, cells, steps, seconds):
+    """Whole-job throughput: every replica advanced `cells` cells `steps` times."""
+    return world * cells * steps / seconds / 1e6
 
 
 def reference_arm(args):
@@ -277,15 +347,11 @@ def our_arm(args):
     pf_ms = [row[0].elapsed_time(row[1]) for row in ev]
     tr_ms = [row[1].elapsed_time(row[2]) for row in ev]
     step_ms = [a + b for a, b in zip(pf_ms, tr_ms)]
-    total_s = sum(step_ms) / 1e3
-    if pg:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, pg, "cuda")
     mass, solute, frac, st = sim.invariants(allow_nonfinite=True)
     if st != gpflbm.OK:
         raise RuntimeError("state is not finite after the timed steps")
-    value = world * cells * args.steps / total_s / 1e6
+    value = job_mlups(world, cells, args.steps, total_s)
 
     # end to end through the public API with pinned host buffers
     NP, NC, Q = sc["n_phases"], sc["n_solutes"], sim.Q
@@ -323,18 +389,15 @@ def our_arm(args):
     for _ in range(args.e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if pg:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
     esz = 8 if sc["precision"] == "fp64" else 4
-    e2e = {"value": world * cells * args.e2e_steps / e2e_s / 1e6, "unit": "MLUPS",
+    e2e = {"value": job_mlups(world, cells, args.e2e_steps, e2e_s), "unit": "MLUPS",
            "h2d_bytes_per_step": (NP + NC + Q) * cells * esz,
            "d2h_bytes_per_step": (NP + NC) * cells * esz,
            "steps": args.e2e_steps,
            "path": "gpflbm_set_state(pinned host) + gpflbm_step(1) + gpflbm_get_fields(pinned host)"}
 
+    adjoint = None if args.no_adjoint else adjoint_ratio(args)
     if rank != 0:
         pg.destroy_process_group() if pg else None
         return 0
@@ -368,6 +431,8 @@ def our_arm(args):
         "clocks": clocks.summary(),
         "invariants": {"mass": mass, "solute": list(solute), "solid_frac": frac},
     }
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
     print(json.dumps(line), flush=True)

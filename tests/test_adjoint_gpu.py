@@ -103,18 +103,23 @@ def test_adjoint_matches_central_differences_fp64():
         assert dpar[j] == pytest.approx(fdp, rel=1e-4), (j, dpar[j], fdp)
 
 
-def test_checkpoint_spacing_does_not_change_the_gradient():
-    sc = _case(40, 36, "fp64")
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_checkpoint_spacing_and_reruns_give_identical_gradients(prec):
+    """Every contribution is gathered in a fixed order and the recomputed
+    states equal the stored ones bit for bit, so neither the checkpoint
+    spacing (K = 1, K not dividing H, K = H, K > H) nor a rerun changes a
+    bit of J or of the gradients."""
+    sc = _case(40, 36, prec)
     H = 17
     ref = None
-    for K in (1, 4, 17, 40):
+    for K in (1, 4, 17, 40, 4):
         _, J, dpar, dmu = _gpu_adjoint(sc, H, K)
         if ref is None:
             ref = (J, dpar, dmu)
             continue
-        assert J == ref[0]  # same forward, same fixed-order sums
-        np.testing.assert_allclose(dpar, ref[1], rtol=1e-12)
-        np.testing.assert_allclose(dmu, ref[2], rtol=1e-10, atol=1e-14 * np.abs(ref[2]).max())
+        assert J == ref[0]
+        assert np.array_equal(dpar, ref[1])
+        assert np.array_equal(dmu, ref[2])
 
 
 def test_adjoint_leaves_the_state_of_plain_stepping():
@@ -168,7 +173,7 @@ def test_autograd_function_returns_the_adjoint_gradients():
     J = F.apply(mu, mob, dl, gb, sim, phi0, _obj(sc), 11, 4)
     (2.0 * J).backward()
     _, J2, dpar, dmu = _gpu_adjoint(sc, 11, 4)
-    assert float(J) == J2
+    assert float(J.detach()) == J2
     np.testing.assert_allclose(mu.grad.cpu().numpy(), 2.0 * dmu, rtol=1e-10, atol=1e-300)
     np.testing.assert_allclose([mob.grad.item(), dl.grad.item(), gb.grad.item()], 2.0 * dpar,
                                rtol=1e-10)
@@ -197,3 +202,21 @@ def test_full_workload_properties():
     rows = dmu.reshape(ny, nx)
     w = sc["grid"]["wall_rows"][1]
     assert np.all(rows[:w] == 0.0) and np.all(rows[ny - w:] == 0.0)
+
+
+def test_full_workload_fp32_gradients_match_fp64():
+    """At the full differentiation workload the FP32 gradients agree with the
+    FP64 ones (themselves equal to the oracle's on crops) to the 1e-4 the
+    gradients are held to against finite differences."""
+    res = {}
+    for prec in ("fp32", "fp64"):
+        sc = inputs.scenario("adjoint2d", precision=prec)
+        phi0, mu0 = inputs.initial_state(sc)
+        sim = gpflbm.Sim(sc)
+        sim.set_state(phi0, mu0)
+        J, dpar, dmu = sim.adjoint(_obj(sc), 500, 50)
+        res[prec] = (J, dpar, dmu.astype(np.float64))
+    (J32, p32, m32), (J64, p64, m64) = res["fp32"], res["fp64"]
+    assert J32 == pytest.approx(J64, rel=1e-6)
+    np.testing.assert_allclose(p32, p64, rtol=1e-4)
+    assert np.abs(m32 - m64).max() <= 1e-4 * np.abs(m64).max()
