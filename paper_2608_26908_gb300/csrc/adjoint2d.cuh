@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(kRedThreads) adj_frac_kernel(const DevParams<R
        c += (long long)gridDim.x * kRedThreads) {
     int x, y;
     cell_xy(P, c, &x, &y);
-    acc += (double)Hs(s[off2(P, x, y)]);
+    acc += Hs((double)s[off2(P, x, y)]);  // J in FP64 from the stored state
   }
   __shared__ double s_w[kRedThreads / 32];
   const double w = warp_sum_butterfly(acc);

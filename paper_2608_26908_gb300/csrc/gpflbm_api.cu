@@ -185,6 +185,7 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
     }
     P.inv2A[a] = (Real)(1.0 / (2.0 * p.A[a]));
     P.inv4A[a] = (Real)(1.0 / (4.0 * p.A[a]));
+    P.chi_pure[a] = Real(1) / P.inv2A[a];  // IEEE division in Real, as on the device
     for (int i = 0; i < 2; ++i) P.ceq[a][i] = (Real)p.ceq[a][i];
     P.S[a] = (Real)p.S[a];
   }

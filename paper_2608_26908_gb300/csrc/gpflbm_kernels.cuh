@@ -120,6 +120,7 @@ struct DevParams {
   Real gamma[4][4], delta[4][4];
   Real inv2A[4];       // 1 / (2 A_a)
   Real inv4A[4];       // 1 / (4 A_a)
+  Real chi_pure[4];    // 1 / inv2A[a], rounded as the device rounds 1 / chi (chi of a pure cell)
   Real ceq[4][2];
   Real S[4];
   Real dcl_ref[2];     // ceq_liquid - c_ref
@@ -203,6 +204,55 @@ __device__ __forceinline__ Real dAdq(const Real* q, Real delta, Real q_floor, in
   const Real qj = q[j];
   const Real dac = Real(16) * delta * (qj * qj * qj - qj * s4 * inv2) * inv2 * inv2;
   return Real(2) * ac * (ac * qj + s2 * dac);
+}
+
+// BGK collision with Guo forcing, in deviations: for every k,
+//   f*_k - w_k = omega d_k + w_k [alpha + c_k.v + (c_k.U)(c_k.z)],
+//   alpha = (drho - 1.5 rho U.U) / tau - 3 pre U.F,
+//   v = 3 (rho U / tau + pre F),  z = 4.5 rho U / tau + 9 pre F,
+// with omega = 1 - 1/tau and pre = 1 - 1/(2 tau): the second-order
+// equilibrium over tau plus the discrete force, collected by powers of c_k.
+// Opposite directions share alpha and the quadratic term and flip the linear
+// one, so each pair costs one evaluation.  put(k, value) stores a result.
+template <int Q, class Real, class Put>
+__device__ __forceinline__ void collide(const DevParams<Real>& P, const Real* dk, Real drho, Real rho,
+                                        const Real* u, const Real* F, Put&& put) {
+  using Lat = Lattice<Q>;
+  constexpr int D = Lat::D;
+  const Real itau = P.inv_tau_f, pre = P.force_pre, omega = Real(1) - itau;
+  Real uu = Real(0), uF = Real(0), v[D], z[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    uu += u[a] * u[a];
+    uF += u[a] * F[a];
+    const Real ru = itau * rho * u[a];
+    v[a] = Real(3) * (ru + pre * F[a]);
+    z[a] = Real(4.5) * ru + Real(9) * pre * F[a];
+  }
+  const Real alpha = itau * (drho - Real(1.5) * rho * uu) - Real(3) * pre * uF;
+  put(0, omega * dk[0] + Real(Lat::w(0)) * alpha);
+#pragma unroll
+  for (int k = 1; k < Q; ++k) {
+    if (Lat::opp(k) < k) continue;  // each pair once, at its first index
+    const int kb = Lat::opp(k);
+    Real cu = Real(0), cz = Real(0), cv = Real(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (Lat::c(k, a) > 0) {
+        cu += u[a];
+        cz += z[a];
+        cv += v[a];
+      } else if (Lat::c(k, a) < 0) {
+        cu -= u[a];
+        cz -= z[a];
+        cv -= v[a];
+      }
+    }
+    const Real wk = Real(Lat::w(k));
+    const Real wq = wk * (alpha + cu * cz), wl = wk * cv;
+    put(k, omega * dk[k] + (wq + wl));
+    put(kb, omega * dk[kb] + (wq - wl));
+  }
 }
 
 // Full vector dA/dq (for the centre term).

@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, 2)
   const double t_now = io.clock_in[0];
   if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
-  const bool obs = obstacle(P, fx, fy, 0);
+  const bool obs = (P.wall[0] | P.wall[1]) != 0 && obstacle(P, fx, fy, 0);
 
   // 0. own cell: phases present, mu; ring cells (phi only); collision
   Real ph[NP];
@@ -173,22 +173,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, 2)
     const Real Fx = -rho * kappa * ux, Fy = FB - rho * kappa * uy;
     s_u[tid] = ux;
     s_u[NT + tid] = uy;
-    // f*_k - w_k = (1 - 1/tau) d_k + (feq_k - w_k)/tau + G_k with
-    // feq_k - w_k = w_k [(drho - 1.5 rho U.U) + rho cu (3 + 4.5 cu)],
-    // G_k = w_k (1 - 1/2tau) [-3 U.F + cF (3 + 9 cu)]
-    const Real A0 = drho - Real(1.5) * rho * (ux * ux + uy * uy);
-    const Real B0 = Real(-3) * P.force_pre * (ux * Fx + uy * Fy);
-    const Real omega = Real(1) - P.inv_tau_f;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      const int cx = Lat::c(k, 0), cy = Lat::c(k, 1);
-      const Real cu = Real(cx) * ux + Real(cy) * uy;
-      const Real cF = Real(cx) * Fx + Real(cy) * Fy;
-      const Real wk = Real(Lat::w(k));
-      const Real deq = wk * (A0 + rho * cu * (Real(3) + Real(4.5) * cu));
-      const Real Gk = wk * (B0 + P.force_pre * cF * (Real(3) + Real(9) * cu));
-      s_fs[k * NT + tid] = Codec<Store>::put(omega * dk[k] + P.inv_tau_f * deq + Gk);
-    }
+    const Real uv2[2] = {ux, uy}, Fv2[2] = {Fx, Fy};
+    collide<Q>(P, dk, drho, rho, uv2, Fv2,
+               [&](int k, Real val) { s_fs[k * NT + tid] = Codec<Store>::put(val); });
   }
   __syncthreads();
 
@@ -323,13 +310,25 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, 2)
     }
   }
   bool changed = false;
+  int pure = -1;  // the phase at exactly 1 when every other phase is exactly 0
+  {
+    int n1 = 0, n0 = 0;
 #pragma unroll
-  for (int a = 0; a < NP; ++a) {
-    s_pn[a * NT + tid] = out[a];
-    changed = changed || out[a] != ph[a];
+    for (int a = 0; a < NP; ++a) {
+      s_pn[a * NT + tid] = out[a];
+      changed = changed || out[a] != ph[a];
+      if (out[a] == Real(1)) {
+        pure = a;
+        ++n1;
+      } else if (out[a] == Real(0)) {
+        ++n0;
+      }
+    }
+    if (n1 != 1 || n0 != NP - 1) pure = -1;
   }
   s_chg[tid] = changed ? 1 : 0;
-  s_hl[tid] = interp_h<NP>(out, 0);
+  // h of a pure cell is the unit vector of its phase, exactly
+  s_hl[tid] = pure >= 0 ? (pure == 0 ? Real(1) : Real(0)) : interp_h<NP>(out, 0);
   const bool any_changed = __syncthreads_or(changed);
 
   // 2. solute flux through the +x face (slot tid) and the +y face (slot NT +
@@ -402,6 +401,18 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, 2)
   if (obs) {
 #pragma unroll
     for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = mu[i];
+  } else if (!changed && pure >= 0) {
+    // unchanged pure cell: source term exactly 0, chi = 1 / (2 A_pure)
+    Real ichi = P.chi_pure[0];
+#pragma unroll
+    for (int a = 1; a < NP; ++a)
+      if (pure == a) ichi = P.chi_pure[a];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const Real* Ji = s_flux + i * 2 * NT;
+      const Real div = (Ji[tid] - Ji[tid - 1]) + (Ji[NT + tid] - Ji[NT + tid - BX]);
+      mu_out[i * P.plane + g] = mu[i] + (-div - Real(0)) * ichi;
+    }
   } else {
     Real chi = Real(0), hn[NP], ho[NP];
 #pragma unroll
@@ -416,8 +427,10 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, 2)
       const Real* Ji = s_flux + i * 2 * NT;
       const Real div = (Ji[tid] - Ji[tid - 1]) + (Ji[NT + tid] - Ji[NT + tid - BX]);
       Real src = Real(0);
+      if (changed) {
 #pragma unroll
-      for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu[i] * P.inv2A[a]) * (hn[a] - ho[a]);
+        for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu[i] * P.inv2A[a]) * (hn[a] - ho[a]);
+      }
       mu_out[i * P.plane + g] = mu[i] + (-div - src) * ichi;
     }
   }

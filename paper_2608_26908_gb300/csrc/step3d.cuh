@@ -109,7 +109,6 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
   const double t_now = io.clock_in[0];
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
-  const Real omega = Real(1) - P.inv_tau_f;
   const bool has_walls = (P.wall[0] | P.wall[1] | P.wall[2]) != 0;  // obstacle rows
 
   int rx = 0, ry = 0;  // ring column held by threads tid < RING
@@ -276,18 +275,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
         s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
       }
       if (owner && C >= z0 && C < z0 + ZS && C < nz) {
-        const Real A0 = drho - Real(1.5) * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        const Real B0 = Real(-3) * P.force_pre * (u[0] * F[0] + u[1] * F[1] + u[2] * F[2]);
         const bool inner_z = C >= 1 && C + 1 < nz;
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
+        collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
+          const Store v = Codec<Store>::put(val);
           const int cx = Lat::c(k, 0), cy = Lat::c(k, 1), cz = Lat::c(k, 2);
-          const Real cu = Real(cx) * u[0] + Real(cy) * u[1] + Real(cz) * u[2];
-          const Real cF = Real(cx) * F[0] + Real(cy) * F[1] + Real(cz) * F[2];
-          const Real wk = Real(Lat::w(k));
-          const Real deq = wk * (A0 + rho * cu * (Real(3) + Real(4.5) * cu));
-          const Real Gk = wk * (B0 + P.force_pre * cF * (Real(3) + Real(9) * cu));
-          const Store v = Codec<Store>::put(omega * dk[k] + P.inv_tau_f * deq + Gk);
           // push to x + c_k; across a wall the population returns reversed
           int tx_ = gx + cx, ty_ = gy + cy, tz_ = C + cz, kk = k;
           long long dst;
@@ -310,7 +301,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
             dst = (long long)tz_ * zst + (long long)ty_ * px + tx_;
           }
           f_out[kk * P.plane + dst] = v;
-        }
+        });
       }
     }
     __syncthreads();
