@@ -28,13 +28,15 @@ namespace gpflbm {
 
 template <class Real>
 struct Block2D;
+// MIN_CTAS: resident CTAs per SM the register budget is cut for (FP32: three,
+// 40 registers a thread, 48 warps; FP64 needs twice the shared memory).
 template <>
 struct Block2D<float> {
-  static constexpr int BX = 32, BY = 16;
+  static constexpr int BX = 32, BY = 16, MIN_CTAS = 3;
 };
 template <>
 struct Block2D<double> {
-  static constexpr int BX = 32, BY = 16;
+  static constexpr int BX = 32, BY = 16, MIN_CTAS = 2;
 };
 
 template <int NP, int NC, class Real, class Store>
@@ -72,7 +74,7 @@ struct Step2DIO {
 };
 
 template <int NP, int NC, class Real, class Store>
-__global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, 2)
+__global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>::MIN_CTAS)
     step2d_kernel(const DevParams<Real> P, const Step2DIO io) {
   using S = Step2D<NP, NC, Real, Store>;
   using Lat = Lattice<9>;

@@ -26,13 +26,14 @@ namespace gpflbm {
 
 template <class Real>
 struct Block3D;
+// MIN_CTAS: resident CTAs per SM the register budget is cut for.
 template <>
 struct Block3D<float> {
-  static constexpr int BX = 32, BY = 16, ZS = 16;
+  static constexpr int BX = 32, BY = 16, ZS = 16, MIN_CTAS = 2;
 };
 template <>
 struct Block3D<double> {
-  static constexpr int BX = 32, BY = 8, ZS = 16;
+  static constexpr int BX = 32, BY = 8, ZS = 16, MIN_CTAS = 1;
 };
 
 template <int NP, int NC, class Real, class Store>
@@ -70,7 +71,7 @@ struct Step3DIO {
 };
 
 template <int NP, int NC, class Real, class Store>
-__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT)
+__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
   using S = Step3D<NP, NC, Real, Store>;
   using Lat = Lattice<19>;
