@@ -141,7 +141,7 @@ struct Adj2D {
   static constexpr int OX = BX - 2, OY = BY - 2;        // output cells per CTA
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;  // tile + two-cell halo
   static constexpr int RING = 2 * W2 + 2 * BY;          // the outer ring of C2
-  static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 2 : 1;  // FP32: 64 registers, two CTAs per SM
+  static constexpr int MIN_CTAS = sizeof(Real) == 4 ? 3 : 1;  // FP32: 40 registers, three CTAs per SM
   enum { S0, S1, MU0, AA, UX, UY, NCELL };              // per-cell values
   // per solute face: d/d mu_a, mu_b, s'_a, s'_b, U_a, U_b, s_a, s_b, and the
   // transverse antitrapping coefficient T (+T to a+t, b+t; -T to a-t, b-t)
