@@ -125,6 +125,15 @@ gpflbm_status check_grid(const gpflbm_grid* g, int NP, int NC, int* D, const Ops
       return GPFLBM_ERR_ARG;
     }
   }
+  {
+    // kernels index a cell within a field plane with 32 bits
+    const long long px = ((long long)g->nx + 7) / 8 * 8;
+    const long long nz = *D == 3 ? g->nz : 1;
+    if (px * g->ny * nz + 64 > 0x7fffffffLL) {
+      *why = "a field plane must hold fewer than 2^31 cells";
+      return GPFLBM_ERR_UNSUPPORTED;
+    }
+  }
   if (g->precision < GPFLBM_FP64 || g->precision > GPFLBM_FP32_BF16STORE) {
     *why = "unknown precision";
     return GPFLBM_ERR_ARG;

@@ -318,15 +318,32 @@ struct PhiStore {
   static constexpr int NS = NP == 2 ? 1 : NP;
 };
 
+// The phase at exactly 1 when every other phase is exactly 0 (its h is then
+// the unit vector of that phase, exactly), else -1.
 template <int NP, class Real>
-__device__ __forceinline__ void load_phases(const Real* __restrict__ phi, long long g,
+__device__ __forceinline__ int pure_phase(const Real* v) {
+  int pa = -1, n1 = 0, n0 = 0;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    if (v[a] == Real(1)) {
+      pa = a;
+      ++n1;
+    } else if (v[a] == Real(0)) {
+      ++n0;
+    }
+  }
+  return (n1 == 1 && n0 == NP - 1) ? pa : -1;
+}
+
+template <int NP, class Real, class Index>
+__device__ __forceinline__ void load_phases(const Real* __restrict__ phi, Index g,
                                             long long plane, Real* v) {
   if (NP == 2) {
     v[1] = phi[g];
     v[0] = Real(1) - v[1];
   } else {
 #pragma unroll
-    for (int a = 0; a < NP; ++a) v[a] = phi[a * plane + g];
+    for (int a = 0; a < NP; ++a) v[a] = (phi + a * plane)[g];
   }
 }
 

@@ -65,16 +65,17 @@ struct Impl {
   using S3 = Step3D<NP, NC, Real, Store>;
 
   static cudaError_t configure() {
-    if (D == 2)
+    if constexpr (D == 2)
       return cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
-    return cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
+    else
+      return cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
   }
 
   static cudaError_t step_fused(const void* params, const StepIO& io, cudaStream_t s) {
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
-    if (D == 2) {
+    if constexpr (D == 2) {
       const dim3 grid((P.n[0] + SZ::OX - 1) / SZ::OX, (P.n[1] + SZ::OY - 1) / SZ::OY);
       const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};

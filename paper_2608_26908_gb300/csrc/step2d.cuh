@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   const bool inner_tile = x0 >= 2 && x0 - 2 + W2 <= nx && y0 >= 2 && y0 - 2 + H2 <= ny;
   const int fx = inner_tile ? gx : fold_axis(P, gx, 0);
   const int fy = inner_tile ? gy : fold_axis(P, gy, 1);
-  const long long g = (long long)fy * px + fx;
+  const int g = fy * px + fx;  // a plane holds fewer than 2^31 cells
   const int r2 = (ty + 1) * W2 + tx + 1;  // this cell in the R1-plus-ring layout
   const double t_now = io.clock_in[0];
   if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     const int qx = inner_tile ? x0 - 2 + rx : fold_axis(P, x0 - 2 + rx, 0);
     const int qy = inner_tile ? y0 - 2 + ry : fold_axis(P, y0 - 2 + ry, 1);
     Real v[NP];
-    load_phases<NP>(phi_in, (long long)qy * px + qx, P.plane, v);
+    load_phases<NP>(phi_in, qy * px + qx, P.plane, v);
     unsigned m = 0;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
@@ -152,13 +152,13 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   Real mu[NC];
 #pragma unroll
   for (int i = 0; i < NC; ++i) {
-    mu[i] = mu_in[i * P.plane + g];
+    mu[i] = (mu_in + i * P.plane)[g];
     s_mu[i * NT + tid] = mu[i];
   }
   {
     Real dk[Q];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(f_in[k * P.plane + g]);
+    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[g]);
     const Real drho = ((dk[0] + dk[1]) + (dk[2] + dk[3])) + ((dk[4] + dk[5]) + (dk[6] + dk[7])) + dk[8];
     const Real mx = (dk[1] - dk[3]) + (dk[5] - dk[6]) + (dk[8] - dk[7]);
     const Real my = (dk[2] - dk[4]) + (dk[5] + dk[6]) - (dk[7] + dk[8]);
@@ -399,10 +399,10 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   Real* __restrict__ mu_out = static_cast<Real*>(io.mu_out);
   Store* __restrict__ f_out = static_cast<Store*>(io.f_out);
 #pragma unroll
-  for (int sidx = 0; sidx < NS; ++sidx) phi_out[sidx * P.plane + g] = out[NP == 2 ? 1 : sidx];
+  for (int sidx = 0; sidx < NS; ++sidx) (phi_out + sidx * P.plane)[g] = out[NP == 2 ? 1 : sidx];
   if (obs) {
 #pragma unroll
-    for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = mu[i];
+    for (int i = 0; i < NC; ++i) (mu_out + i * P.plane)[g] = mu[i];
   } else if (!changed && pure >= 0) {
     // unchanged pure cell: source term exactly 0, chi = 1 / (2 A_pure)
     Real ichi = P.chi_pure[0];
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     for (int i = 0; i < NC; ++i) {
       const Real* Ji = s_flux + i * 2 * NT;
       const Real div = (Ji[tid] - Ji[tid - 1]) + (Ji[NT + tid] - Ji[NT + tid - BX]);
-      mu_out[i * P.plane + g] = mu[i] + (-div - Real(0)) * ichi;
+      (mu_out + i * P.plane)[g] = mu[i] + (-div - Real(0)) * ichi;
     }
   } else {
     Real chi = Real(0), hn[NP], ho[NP];
@@ -433,13 +433,13 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
 #pragma unroll
         for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu[i] * P.inv2A[a]) * (hn[a] - ho[a]);
       }
-      mu_out[i * P.plane + g] = mu[i] + (-div - src) * ichi;
+      (mu_out + i * P.plane)[g] = mu[i] + (-div - src) * ichi;
     }
   }
   if (inner_tile) {
 #pragma unroll
     for (int k = 0; k < Q; ++k)
-      f_out[k * P.plane + g] = s_fs[k * NT + tid - Lat::c(k, 0) - Lat::c(k, 1) * BX];
+      (f_out + k * P.plane)[g] = s_fs[k * NT + tid - Lat::c(k, 0) - Lat::c(k, 1) * BX];
   } else {
     const bool wx = P.bc[0] == kWall, wy = P.bc[1] == kWall;
 #pragma unroll
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
       const bool bounce =
           (wx && (gx - cx < 0 || gx - cx >= nx)) || (wy && (gy - cy < 0 || gy - cy >= ny));
       const Store v = bounce ? s_fs[Lat::opp(k) * NT + tid] : s_fs[k * NT + tid - cx - cy * BX];
-      f_out[k * P.plane + g] = v;
+      (f_out + k * P.plane)[g] = v;
     }
   }
 }

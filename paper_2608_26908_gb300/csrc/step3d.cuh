@@ -26,14 +26,13 @@ namespace gpflbm {
 
 template <class Real>
 struct Block3D;
-// MIN_CTAS: resident CTAs per SM the register budget is cut for.
 template <>
 struct Block3D<float> {
-  static constexpr int BX = 32, BY = 16, ZS = 16, MIN_CTAS = 2;
+  static constexpr int BX = 32, BY = 16, ZS = 16;
 };
 template <>
 struct Block3D<double> {
-  static constexpr int BX = 32, BY = 8, ZS = 16, MIN_CTAS = 1;
+  static constexpr int BX = 32, BY = 8, ZS = 16;
 };
 
 template <int NP, int NC, class Real, class Store>
@@ -41,6 +40,10 @@ struct Step3D {
   static constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZS;
   static constexpr int NT = BX * BY, Q = 19;
   static constexpr int NS = PhiStore<NP>::NS;
+  // resident CTAs per SM the register budget is cut for: two (64 registers)
+  // for two phases in FP32; with more phases the phase-field registers
+  // spill at 64, and one CTA of 128 registers runs faster
+  static constexpr int MIN_CTAS = (sizeof(Real) == 4 && NP == 2) ? 2 : 1;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;
   static constexpr int RING = C2 - NT;
@@ -71,7 +74,7 @@ struct Step3DIO {
 };
 
 template <int NP, int NC, class Real, class Store>
-__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>::MIN_CTAS)
+__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Step3D<NP, NC, Real, Store>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
   using S = Step3D<NP, NC, Real, Store>;
   using Lat = Lattice<19>;
@@ -97,13 +100,13 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2], px = P.px;
-  const long long zst = (long long)px * ny;  // plane stride
+  const int zst = px * ny;  // plane stride (a plane holds fewer than 2^31 cells)
   const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY, z0 = blockIdx.z * ZS;
   const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
   const bool inner_xy = x0 >= 2 && x0 - 2 + W2 <= nx && y0 >= 2 && y0 - 2 + H2 <= ny;
   const int fx = inner_xy ? gx : fold_axis(P, gx, 0);
   const int fy = inner_xy ? gy : fold_axis(P, gy, 1);
-  const long long gxy = (long long)fy * px + fx;
+  const int gxy = fy * px + fx;
   const int r2 = (ty + 1) * W2 + tx + 1;
   // inner columns of the tile write the tile's cells
   const bool owner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && gx < nx && gy < ny;
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
   const bool has_walls = (P.wall[0] | P.wall[1] | P.wall[2]) != 0;  // obstacle rows
 
   int rx = 0, ry = 0;  // ring column held by threads tid < RING
-  long long gring = 0;
+  int gring = 0;
   if (tid < S::RING) {
     if (tid < W2) {
       rx = tid;
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
     }
     const int qx = inner_xy ? x0 - 2 + rx : fold_axis(P, x0 - 2 + rx, 0);
     const int qy = inner_xy ? y0 - 2 + ry : fold_axis(P, y0 - 2 + ry, 1);
-    gring = (long long)qy * px + qx;
+    gring = qy * px + qx;
   }
   const int rr2 = ry * W2 + rx;
 
@@ -148,6 +151,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
     return b[a * C2 + i];
   };
   auto MK = [&](int p, int i) -> unsigned { return s_mask[slot3(p) * C2 + i]; };
+
+  // OR of the phase masks over the 3x3 in-plane neighbourhood of this
+  // column, for planes C-1 and C (carried) and L (new)
+  unsigned xy_m1 = 0, xy_0 = 0;
 
   // phase-field z-face fluxes of this column: (C-1, C) carried, (C, C+1) new
   Real pfz_lo[NP], pfz_hi[NP];
@@ -212,7 +219,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
     const int C = L - 1, M = L - 2;
     // A. phi^n of plane L
     {
-      const long long zo = (long long)fold_axis(P, L, 2) * zst;
+      const int zo = fold_axis(P, L, 2) * zst;
       Real* b = s_phi + slot4(L) * NS * C2;
       unsigned m = 0;
       Real v[NP];
@@ -238,17 +245,17 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
     const bool doC = C >= z0 - 1 && C <= z0 + ZS;
     if (doC) {
       const int fzc = fold_axis(P, C, 2);
-      const long long g = (long long)fzc * zst + gxy;
+      const int gi = fzc * zst + gxy;  // a plane holds fewer than 2^31 cells
       const bool obs = has_walls && obstacle(P, fx, fy, fzc);
       Real mu[NC];
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
-        mu[i] = mu_in[i * P.plane + g];
+        mu[i] = (mu_in + i * P.plane)[gi];
         s_mu[(slot2(C) * NC + i) * NT + tid] = mu[i];
       }
       Real dk[Q];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(f_in[k * P.plane + g]);
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
       Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
@@ -277,15 +284,20 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
       }
       if (owner && C >= z0 && C < z0 + ZS && C < nz) {
         const bool inner_z = C >= 1 && C + 1 < nz;
+        if (inner_xy && inner_z) {
+          // x + c_k is inside the grid: population k lands at gi + c_k . (1, px, zst)
+          collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
+            const int off = Lat::c(k, 0) + Lat::c(k, 1) * px + Lat::c(k, 2) * zst;
+            (f_out + k * P.plane + off)[gi] = Codec<Store>::put(val);
+          });
+        } else {
         collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
           const Store v = Codec<Store>::put(val);
           const int cx = Lat::c(k, 0), cy = Lat::c(k, 1), cz = Lat::c(k, 2);
           // push to x + c_k; across a wall the population returns reversed
           int tx_ = gx + cx, ty_ = gy + cy, tz_ = C + cz, kk = k;
           long long dst;
-          if (inner_xy && inner_z) {
-            dst = (long long)tz_ * zst + (long long)ty_ * px + tx_;
-          } else {
+          {
             const bool bx = P.bc[0] == kWall && (tx_ < 0 || tx_ >= nx);
             const bool by = P.bc[1] == kWall && (ty_ < 0 || ty_ >= ny);
             const bool bz = P.bc[2] == kWall && (tz_ < 0 || tz_ >= nz);
@@ -303,6 +315,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
           }
           f_out[kk * P.plane + dst] = v;
         });
+        }
       }
     }
     __syncthreads();
@@ -312,14 +325,16 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
     Real out[NP];
     bool mixed = false, multi = false;
     unsigned act = 0;
+    unsigned xy_l = 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) xy_l |= MK(L, r2 + dy * W2 + dx);
+    act = xy_m1 | xy_0 | xy_l;  // the 3x3x3 neighbourhood of plane C
+    xy_m1 = xy_0;
+    xy_0 = xy_l;
     if (pfC) {
       const int fzc = fold_axis(P, C, 2);
-#pragma unroll
-      for (int dz = -1; dz <= 1; ++dz)
-#pragma unroll
-        for (int dy = -1; dy <= 1; ++dy)
-#pragma unroll
-          for (int dx = -1; dx <= 1; ++dx) act |= MK(C + dz, r2 + dy * W2 + dx);
       mixed = __popc(act) >= 2;
       multi = mixed && !(has_walls && obstacle(P, fx, fy, fzc));
 #pragma unroll
@@ -545,7 +560,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
     __syncthreads();
     if (outM && M >= z0 && owner) {
       const int fzm = M;  // owned planes lie inside the grid
-      const long long g = (long long)fzm * zst + gxy;
+      const int g = fzm * zst + gxy;
       Real po[NP], pn[NP];
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
@@ -557,6 +572,21 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
       if (has_walls && obstacle(P, fx, fy, fzm)) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = s_mu[(slot2(M) * NC + i) * NT + tid];
+      } else if (s_chg[slot2(M) * NT + tid] == 0 && pure_phase<NP>(pn) >= 0) {
+        // unchanged pure cell: source term exactly 0, chi = 1 / (2 A_pure)
+        const int pa = pure_phase<NP>(pn);
+        Real ichi = P.chi_pure[0];
+#pragma unroll
+        for (int a = 1; a < NP; ++a)
+          if (pa == a) ichi = P.chi_pure[a];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          const Real* Jx = s_flux + (i * 2 + 0) * NT;
+          const Real* Jy = s_flux + (i * 2 + 1) * NT;
+          const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
+          const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
+          mu_out[i * P.plane + g] = mu + (-div - Real(0)) * ichi;
+        }
       } else {
         Real chi = Real(0), hn[NP], ho[NP];
         const bool changed = s_chg[slot2(M) * NT + tid] != 0;
@@ -574,8 +604,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Block3D<Real>
           const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
           const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
           Real src = Real(0);
+          if (changed) {
 #pragma unroll
-          for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu * P.inv2A[a]) * (hn[a] - ho[a]);
+            for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu * P.inv2A[a]) * (hn[a] - ho[a]);
+          }
           mu_out[i * P.plane + g] = mu + (-div - src) * ichi;
         }
       }
