@@ -69,6 +69,7 @@ typedef struct {
   double undercool;    // T = T_E - undercool + G (v - v0 - V t)
   double G, V, v0;
   double q_floor;      // |q|^2 at or below which the anisotropy is dropped
+  double eta[4];       // shrinkage (rho_a - rho_liq) / rho_liq per phase, Eq. shrinkage
 } OracleProblem;
 
 // Objective for the gradient checks: J = w_frac * mean_x sum_{a>0} h_a(phi)
@@ -367,10 +368,13 @@ struct Macro {
 // Density, implicit-force velocity and total force at every cell from S^n
 // [R5]-[R8]:  rho = sum f, m = sum c f, kappa = 2 nu h (1 - phil~)^2 / W0^2,
 // F_B = rho phil~ [sum_i gbeta_i (c_l,i(mu) - c_ref,i) + gbeta_T (T - T_ref)]
-// along +v, U = (m + F_B/2) / (rho (1 + kappa/2)), F = F_B - rho kappa U.
+// along +v, the shrinkage force of Eq. shrinkage [R26]
+// F_S = sum_a eta_a (phi_a^{n+1} - phi_a^n) grad phi_a^n / |grad phi_a^n|
+// (central gradient; zero where |grad|^2 <= 1e-12; absent without phi_new),
+// U = (m + (F_B + F_S)/2) / (rho (1 + kappa/2)), F = F_B + F_S - rho kappa U.
 template <class R>
 void macroscopic(const Grid& g, const Lattice& L, const Coeffs<R>& k, const State<R>& s,
-                 double t, Macro<R>& m) {
+                 const std::vector<R>* phi_new, double t, Macro<R>& m) {
   const OracleProblem* p = g.p;
   const int D = p->dim, N = p->n_phases, NC = p->n_solutes;
   const long cells = g.cells;
@@ -397,12 +401,26 @@ void macroscopic(const Grid& g, const Lattice& L, const Coeffs<R>& k, const Stat
     R drive = p->gbeta_T * (temperature(p, g.vertical(c), t) - p->T_ref);
     for (int i = 0; i < NC; ++i) drive += k.gbeta_c[i] * (c_phase(p, 0, i, mu) - p->c_ref[i]);
     R FB = rho * phil * drive;
+    R FS[3] = {R(0.0), R(0.0), R(0.0)};
+    if (phi_new) {
+      for (int al = 0; al < N; ++al) {
+        if (p->eta[al] == 0.0) continue;
+        R gr[3];
+        centre_grad(g, &s.phi[al * cells], c, gr);
+        R g2 = 0.0;
+        for (int a = 0; a < D; ++a) g2 += gr[a] * gr[a];
+        if (val(g2) <= 1e-12) continue;
+        const R rate = (*phi_new)[al * cells + x] - s.phi[al * cells + x];
+        const R inv = 1.0 / sqrt(g2);
+        for (int a = 0; a < D; ++a) FS[a] += p->eta[al] * rate * gr[a] * inv;
+      }
+    }
     m.rho[x] = rho;
     for (int a = 0; a < D; ++a) {
-      R num = mom[a] + (a == vax ? 0.5 * FB : R(0.0));
+      R num = mom[a] + 0.5 * ((a == vax ? FB : R(0.0)) + FS[a]);
       R u = num / (rho * (1.0 + 0.5 * kappa));
       m.u[a * cells + x] = u;
-      m.F[a * cells + x] = (a == vax ? FB : R(0.0)) - rho * kappa * u;
+      m.F[a * cells + x] = (a == vax ? FB : R(0.0)) + FS[a] - rho * kappa * u;
     }
     (void)N;
   }
@@ -691,7 +709,7 @@ void step(const Grid& g, const Lattice& L, const Coeffs<R>& k, State<R>& s, long
       f_new((long)L.q * cells);
   Macro<R> m;
   phase_field_update(g, k, s, t, phi_new);
-  macroscopic(g, L, k, s, t, m);
+  macroscopic(g, L, k, s, &phi_new, t, m);
   chemical_potential_update(g, s, phi_new, m, mu_new);
   lattice_boltzmann_update(g, L, s, m, f_new);
   s.phi.swap(phi_new);
@@ -809,7 +827,7 @@ int oracle_derived(const OracleProblem* p, long n, const double* phi, const doub
   s.mu.assign(mu, mu + (long)p->n_solutes * g.cells);
   s.f.assign(f, f + (long)L.q * g.cells);
   Macro<double> m;
-  macroscopic(g, L, k, s, (double)n, m);
+  macroscopic(g, L, k, s, static_cast<const std::vector<double>*>(nullptr), (double)n, m);
   for (long x = 0; x < g.cells; ++x) {
     double ph[4], mm[2];
     for (int a = 0; a < p->n_phases; ++a) ph[a] = phi[a * g.cells + x];

@@ -73,6 +73,7 @@ def _blank_params():
         "gbeta_c": [0.0, 0.0], "c_ref": [0.0, 0.0], "gbeta_T": 0.0, "T_ref": 1.0,
         "T_E": 1.0, "undercool": 0.0, "G": 0.0, "V": 0.0, "v0": 0.0,
         "q_floor": 1e-12,
+        "eta_rho": [0.0] * 4,  # shrinkage (rho_a - rho_l) / rho_l per phase; off unless set
     }
 
 

@@ -620,3 +620,45 @@ def test_frozen_temperature_gradient_sets_the_front():
     assert abs(b - a) < 0.02
     a, b = _directional(-4.0, n0=4000, V=1e-3, steps=100)  # at v0: 4 cells below it
     assert b > a + 0.04
+
+
+# ----------------------------------------------------------------- shrinkage
+@pytest.mark.parametrize("dim", [2, 3])
+def test_shrinkage_momentum_balances_the_solidified_volume(dim):
+    """Eq. shrinkage, one step from rest, planar front normal to x between
+    walls, no drag (h = 0) and no buoyancy: Guo forcing adds exactly sum_x F
+    to the total momentum, and F = F_S, whose x-sum is eta times the solid
+    gained with the sign of the normal (the solid lies at low x, so the
+    liquid is pulled towards it, -x).  Nothing moves across x = const."""
+    if dim == 2:
+        sc = inputs.scenario("dendrite2d", nx=40, ny=6)
+        sc["grid"]["bc"] = [inputs.WALL, inputs.PERIODIC, inputs.PERIODIC]
+        sc["grid"]["wall_rows"] = [0, 0, 0]
+    else:
+        sc = inputs.scenario("dendrite3d", nx=40, ny=5, nz=4)
+        sc["grid"]["bc"] = [inputs.WALL, inputs.PERIODIC, inputs.PERIODIC]
+    pr = sc["params"]
+    pr["h_drag"] = 0.0
+    pr["gbeta_c"] = [0.0, 0.0]
+    pr["gbeta_T"] = 0.0
+    eta = 0.2
+    pr["eta_rho"] = [0.0, eta, 0.0, 0.0]
+    nx, ny, nz = inputs.dims(sc)
+    x = np.tile(np.arange(nx), ny * nz)
+    s = inputs._seed_profile(x + 0.5, 14.0, pr["eps"])  # solid for x < 14
+    phi = np.concatenate([1.0 - s, s])
+    mu = np.zeros(nx * ny * nz)
+    f0 = oracle.rest_populations(sc)
+    phi1, mu1, f1 = oracle.run(sc, phi, mu, f0, 1)
+    w, c = oracle.lattice(19 if dim == 3 else 9)
+    Q, cells = len(w), nx * ny * nz
+    f1 = f1.reshape(Q, cells)
+    mom = np.array([(c[:, a][:, None] * f1).sum() for a in range(3)])
+    grown = phi1[cells:].sum() - s.sum()
+    assert grown > 1e-3  # the undercooled front advances
+    assert mom[0] == pytest.approx(-eta * grown, rel=1e-10)
+    assert abs(mom[1]) < 1e-13 and abs(mom[2]) < 1e-13
+    # eta = 0 leaves the fluid at rest
+    pr["eta_rho"] = [0.0] * 4
+    _, _, f2 = oracle.run(sc, phi, mu, f0, 1)
+    assert np.abs(f2 - f0).max() < 1e-15
