@@ -69,7 +69,9 @@ enum {
   GPFLBM_FIELD_C = 4,    /* K-1 planes: c_i = sum_a h_a(phi) c_a,i(mu) */
   GPFLBM_FIELD_F = 8,    /* Q planes, full populations f_k */
   GPFLBM_FIELD_RHO = 16, /* 1 plane: sum_k f_k */
-  GPFLBM_FIELD_U = 32    /* d planes: force-corrected velocity of the current state */
+  GPFLBM_FIELD_U = 32    /* d planes: force-corrected velocity of the current state (with drag
+                            and buoyancy; the shrinkage force needs the next phase field and is
+                            not included) */
 };
 
 #define GPFLBM_MAX_PHASES 4
@@ -106,6 +108,9 @@ typedef struct {
   double gbeta_T, T_ref;           /* thermal buoyancy g beta_T (T - T_ref), upward */
   double T_E, undercool, G, V, v0; /* T(v, t) = T_E - undercool + G (v - v0 - V t) */
   double q_floor;                  /* |q|^2 at or below which the anisotropy is dropped */
+  double eta_rho[4];               /* shrinkage (rho_a - rho_0) / rho_0 per phase (Eq. shrinkage):
+                                      G_S = sum_a eta_a (phi_a^{n+1} - phi_a^n) grad phi_a / |grad phi_a|
+                                      joins the buoyancy in U and F; all 0 = no shrinkage */
 } gpflbm_params;
 
 /* Device bytes the library needs for a problem (state ping-pong buffers,
@@ -220,8 +225,8 @@ gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_e
  * steps run backwards through each segment while the segment before it is
  * recomputed from its checkpoint on a second stream (the library's own).
  * Cost: H + (ceil(H/K) - 1)(K - 1) forward steps plus H adjoint steps.
- * Supported: 2D, D2Q9, two phases, one solute, GPFLBM_FP64 or GPFLBM_FP32
- * (anything else: GPFLBM_ERR_UNSUPPORTED).
+ * Supported: 2D, D2Q9, two phases, one solute, GPFLBM_FP64 or GPFLBM_FP32,
+ * no shrinkage (eta_rho all 0); anything else: GPFLBM_ERR_UNSUPPORTED.
  * Outputs (each may be NULL): *J; dparams[0] = dJ/d(1/tau_phi),
  * dparams[1] = dJ/d delta_01, dparams[2] = dJ/d gbeta_c[0] (FP64,
  * accumulated per cell in FP64 and summed in a fixed order); dmu0 =

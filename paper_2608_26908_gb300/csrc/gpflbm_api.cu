@@ -195,6 +195,8 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
     P.inv2A[a] = (Real)(1.0 / (2.0 * p.A[a]));
     P.inv4A[a] = (Real)(1.0 / (4.0 * p.A[a]));
     P.chi_pure[a] = Real(1) / P.inv2A[a];  // IEEE division in Real, as on the device
+    P.eta[a] = a < h->NP ? (Real)p.eta_rho[a] : Real(0);
+    if (P.eta[a] != Real(0)) P.shrink = 1;
     for (int i = 0; i < 2; ++i) P.ceq[a][i] = (Real)p.ceq[a][i];
     P.S[a] = (Real)p.S[a];
   }
@@ -226,6 +228,11 @@ gpflbm_status check_params(const gpflbm_params* p, int NP, std::string* why) {
   for (int a = 0; a < NP; ++a)
     if (!(p->A[a] > 0.0)) {
       *why = "need A_a > 0 for every phase";
+      return GPFLBM_ERR_ARG;
+    }
+  for (int a = 0; a < NP; ++a)
+    if (!std::isfinite(p->eta_rho[a])) {
+      *why = "eta_rho must be finite";
       return GPFLBM_ERR_ARG;
     }
   if (!(p->D_liq >= 0.0) || !(p->q_floor >= 0.0)) {
@@ -752,9 +759,10 @@ AdjLayout adj_layout(gpflbm_t h, int H, int K) {
 
 gpflbm_status adj_check(gpflbm_t h, int H, int K) {
   const int prec = h->grid.precision;
-  if (h->D != 2 || h->NP != 2 || h->NC != 1 || (prec != GPFLBM_FP64 && prec != GPFLBM_FP32))
+  if (h->D != 2 || h->NP != 2 || h->NC != 1 || (prec != GPFLBM_FP64 && prec != GPFLBM_FP32) ||
+      h->pf.shrink || h->pd.shrink)
     return fail(h, GPFLBM_ERR_UNSUPPORTED,
-                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32");
+                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage");
   if (H < 1 || K < 1) return fail(h, GPFLBM_ERR_ARG, "adjoint: need horizon >= 1 and ckpt_every >= 1");
   return GPFLBM_OK;
 }

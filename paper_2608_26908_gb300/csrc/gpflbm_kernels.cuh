@@ -135,6 +135,9 @@ struct DevParams {
   Real q_floor;
   double theta0;       // -undercool - G v0: theta(v, t) = theta0 - G V t + G v
   double GV;           // G * V
+  // appended last: earlier fields keep their parameter-bank offsets
+  Real eta[4];         // shrinkage (rho_a - rho_0) / rho_0 per phase
+  int shrink;          // 1 if any eta of the problem's phases is nonzero
 };
 
 template <class Real>

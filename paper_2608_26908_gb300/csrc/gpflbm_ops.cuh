@@ -65,12 +65,21 @@ struct Impl {
   using S3 = Step3D<NP, NC, Real, Store>;
 
   static cudaError_t configure() {
-    if constexpr (D == 2)
-      return cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
-    else
-      return cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
+    cudaError_t e;
+    if constexpr (D == 2) {
+      e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
+    } else {
+      e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
+    }
+    return e;
   }
 
   static cudaError_t step_fused(const void* params, const StepIO& io, cudaStream_t s) {
@@ -79,13 +88,19 @@ struct Impl {
       const dim3 grid((P.n[0] + SZ::OX - 1) / SZ::OX, (P.n[1] + SZ::OY - 1) / SZ::OY);
       const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
-      step2d_kernel<NP, NC, Real, Store><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+      if (P.shrink)
+        step2d_kernel<NP, NC, Real, Store, true><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+      else
+        step2d_kernel<NP, NC, Real, Store, false><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
     } else {
       const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
                       (P.n[2] + S3::ZS - 1) / S3::ZS);
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
-      step3d_kernel<NP, NC, Real, Store><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+      if (P.shrink)
+        step3d_kernel<NP, NC, Real, Store, true><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+      else
+        step3d_kernel<NP, NC, Real, Store, false><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
     }
     return cudaGetLastError();
   }

@@ -73,7 +73,9 @@ struct Step2DIO {
   double* clock_out;
 };
 
-template <int NP, int NC, class Real, class Store>
+// SHRINK: the shrinkage force needs phi^{n+1}, so the collision moves after
+// the phase-field update (the raw populations wait in the collision buffer).
+template <int NP, int NC, class Real, class Store, bool SHRINK = false>
 __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>::MIN_CTAS)
     step2d_kernel(const DevParams<Real> P, const Step2DIO io) {
   using S = Step2D<NP, NC, Real, Store>;
@@ -155,10 +157,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     mu[i] = (mu_in + i * P.plane)[g];
     s_mu[i * NT + tid] = mu[i];
   }
-  {
-    Real dk[Q];
-#pragma unroll
-    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[g]);
+  // moments, U, F (drag, buoyancy and, with SHRINK, the shrinkage force fs)
+  // and the collision of this cell's populations into shared memory
+  auto lbm_cell = [&](const Real* dk, Real fsx, Real fsy) {
     const Real drho = ((dk[0] + dk[1]) + (dk[2] + dk[3])) + ((dk[4] + dk[5]) + (dk[6] + dk[7])) + dk[8];
     const Real mx = (dk[1] - dk[3]) + (dk[5] - dk[6]) + (dk[8] - dk[7]);
     const Real my = (dk[2] - dk[4]) + (dk[5] + dk[6]) - (dk[7] + dk[8]);
@@ -171,13 +172,34 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     for (int i = 0; i < NC; ++i) drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
     const Real FB = rho * phil * drive;
     const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
-    const Real ux = mx * inv, uy = (my + Real(0.5) * FB) * inv;
-    const Real Fx = -rho * kappa * ux, Fy = FB - rho * kappa * uy;
+    Real ux, uy, Fx, Fy;
+    if constexpr (SHRINK) {
+      ux = (mx + Real(0.5) * fsx) * inv;
+      uy = (my + Real(0.5) * (FB + fsy)) * inv;
+      Fx = fsx - rho * kappa * ux;
+      Fy = FB + fsy - rho * kappa * uy;
+    } else {
+      ux = mx * inv;
+      uy = (my + Real(0.5) * FB) * inv;
+      Fx = -rho * kappa * ux;
+      Fy = FB - rho * kappa * uy;
+    }
     s_u[tid] = ux;
     s_u[NT + tid] = uy;
     const Real uv2[2] = {ux, uy}, Fv2[2] = {Fx, Fy};
     collide<Q>(P, dk, drho, rho, uv2, Fv2,
                [&](int k, Real val) { s_fs[k * NT + tid] = Codec<Store>::put(val); });
+  };
+  {
+    Real dk[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[g]);
+    if constexpr (SHRINK) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) s_fs[k * NT + tid] = Codec<Store>::put(dk[k]);  // exact round trip
+    } else {
+      lbm_cell(dk, Real(0), Real(0));
+    }
   }
   __syncthreads();
 
@@ -331,6 +353,29 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   s_chg[tid] = changed ? 1 : 0;
   // h of a pure cell is the unit vector of its phase, exactly
   s_hl[tid] = pure >= 0 ? (pure == 0 ? Real(1) : Real(0)) : interp_h<NP>(out, 0);
+  if constexpr (SHRINK) {
+    // F_S = sum_a eta_a (phi_a^{n+1} - phi_a^n) grad phi_a^n / |grad phi_a^n|
+    Real fsx = Real(0), fsy = Real(0);
+    if (changed) {
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        if (P.eta[a] == Real(0)) continue;
+        const Real* sp = s_phi + a * C2;
+        const Real gxa = Real(0.5) * (sp[r2 + 1] - sp[r2 - 1]);
+        const Real gya = Real(0.5) * (sp[r2 + W2] - sp[r2 - W2]);
+        const Real g2 = gxa * gxa + gya * gya;
+        if (g2 <= Real(1e-12)) continue;
+        const Real ig = Real(1) / sqrt(g2);
+        const Real rate = out[a] - ph[a];
+        fsx += P.eta[a] * rate * gxa * ig;
+        fsy += P.eta[a] * rate * gya * ig;
+      }
+    }
+    Real dk[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(s_fs[k * NT + tid]);
+    lbm_cell(dk, fsx, fsy);
+  }
   const bool any_changed = __syncthreads_or(changed);
 
   // 2. solute flux through the +x face (slot tid) and the +y face (slot NT +

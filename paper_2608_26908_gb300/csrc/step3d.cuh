@@ -73,7 +73,9 @@ struct Step3DIO {
   double* clock_out;
 };
 
-template <int NP, int NC, class Real, class Store>
+// SHRINK: the shrinkage force needs phi^{n+1}, so the collision of a plane
+// moves after its phase-field update (its populations are read again then).
+template <int NP, int NC, class Real, class Store, bool SHRINK = false>
 __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Step3D<NP, NC, Real, Store>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
   using S = Step3D<NP, NC, Real, Store>;
@@ -253,6 +255,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Step3D<NP, NC
         mu[i] = (mu_in + i * P.plane)[gi];
         s_mu[(slot2(C) * NC + i) * NT + tid] = mu[i];
       }
+      if constexpr (!SHRINK) {
       Real dk[Q];
 #pragma unroll
       for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
@@ -317,6 +320,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Step3D<NP, NC
         });
         }
       }
+      }  // !SHRINK
     }
     __syncthreads();
 
@@ -465,6 +469,79 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Step3D<NP, NC
       for (int a = 0; a < NP; ++a) {
         s_pn[(slot3(C) * NP + a) * NT + tid] = out[a];
         changed = changed || out[a] != PH(C, a, r2);
+      }
+      if constexpr (SHRINK) {
+        // F_S = sum_a eta_a (phi_a^{n+1} - phi_a^n) grad phi_a^n / |grad phi_a^n|
+        Real fs[3] = {Real(0), Real(0), Real(0)};
+        if (changed) {
+#pragma unroll
+          for (int a = 0; a < NP; ++a) {
+            if (P.eta[a] == Real(0)) continue;
+            Real gr[3];
+            gr[0] = Real(0.5) * (PH(C, a, r2 + 1) - PH(C, a, r2 - 1));
+            gr[1] = Real(0.5) * (PH(C, a, r2 + W2) - PH(C, a, r2 - W2));
+            gr[2] = Real(0.5) * (PH(C + 1, a, r2) - PH(C - 1, a, r2));
+            const Real g2 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+            if (g2 <= Real(1e-12)) continue;
+            const Real ig = Real(1) / sqrt(g2);
+            const Real rate = out[a] - PH(C, a, r2);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) fs[t] += P.eta[a] * rate * gr[t] * ig;
+          }
+        }
+        // moments, U and F with the shrinkage force, collision + push (as phase B)
+        const int fzc = fold_axis(P, C, 2);
+        const int gi = fzc * zst + gxy;
+        const bool obs = has_walls && obstacle(P, fx, fy, fzc);
+        Real dk[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
+        Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+          drho += dk[k];
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+            if (Lat::c(k, a) != 0) m3[a] += Real(Lat::c(k, a)) * dk[k];
+        }
+        const Real rho = Real(1) + drho;
+        const Real phl = obs ? Real(0) : PH(C, 0, r2);
+        const Real sl = Real(1) - phl;
+        const Real kappa = P.kappa0 * sl * sl;
+        Real drive = P.gbeta_T * (theta_base + P.G * Real(fzc) + P.dT_ref);
+#pragma unroll
+        for (int i = 0; i < NC; ++i)
+          drive += P.gbeta_c[i] * (P.dcl_ref[i] + s_mu[(slot2(C) * NC + i) * NT + tid] * P.inv2A[0]);
+        const Real FB = rho * phl * drive;
+        const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
+        Real u[3], F[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const Real fb = a == 2 ? FB : Real(0);
+          u[a] = (m3[a] + Real(0.5) * (fb + fs[a])) * inv;
+          F[a] = fb + fs[a] - rho * kappa * u[a];
+          s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
+        }
+        if (owner && C >= z0 && C < z0 + ZS && C < nz) {
+          collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
+            const Store v = Codec<Store>::put(val);
+            int tx_ = gx + Lat::c(k, 0), ty_ = gy + Lat::c(k, 1), tz_ = C + Lat::c(k, 2), kk = k;
+            const bool bx = P.bc[0] == kWall && (tx_ < 0 || tx_ >= nx);
+            const bool by = P.bc[1] == kWall && (ty_ < 0 || ty_ >= ny);
+            const bool bz = P.bc[2] == kWall && (tz_ < 0 || tz_ >= nz);
+            if (bx || by || bz) {  // across a wall the population returns reversed
+              kk = Lat::opp(k);
+              tx_ = gx;
+              ty_ = gy;
+              tz_ = C;
+            } else {
+              tx_ = tx_ < 0 ? tx_ + nx : (tx_ >= nx ? tx_ - nx : tx_);
+              ty_ = ty_ < 0 ? ty_ + ny : (ty_ >= ny ? ty_ - ny : ty_);
+              tz_ = tz_ < 0 ? tz_ + nz : (tz_ >= nz ? tz_ - nz : tz_);
+            }
+            f_out[kk * P.plane + (long long)tz_ * zst + (long long)ty_ * px + tx_] = v;
+          });
+        }
       }
       s_chg[slot2(C) * NT + tid] = changed ? 1 : 0;
       s_hl[slot2(C) * NT + tid] = interp_h<NP>(out, 0);

@@ -39,6 +39,7 @@ class Params(ctypes.Structure):
         ("T_E", ctypes.c_double), ("undercool", ctypes.c_double),
         ("G", ctypes.c_double), ("V", ctypes.c_double), ("v0", ctypes.c_double),
         ("q_floor", ctypes.c_double),
+        ("eta_rho", ctypes.c_double * 4),
     ]
 
 
@@ -130,6 +131,8 @@ def params_struct(sc):
     for i in range(2):
         p.gbeta_c[i] = pr["gbeta_c"][i]
         p.c_ref[i] = pr["c_ref"][i]
+    for a in range(4):
+        p.eta_rho[a] = pr.get("eta_rho", [0.0] * 4)[a]
     return p
 
 
