@@ -45,7 +45,7 @@ extern "C" {
 typedef struct {
   int nx, ny, nz;      // cells per axis (nz == 1 in 2D)
   int dim;             // 2 or 3
-  int q;               // 9 (D2Q9) or 19 (D3Q19)
+  int q;               // 9 (D2Q9), 19 (D3Q19) or 27 (D3Q27)
   int n_phases;        // N; phase 0 is the liquid
   int n_solutes;       // K-1 independent chemical potentials
   int bc[3];           // per axis: 0 periodic, 1 wall
@@ -116,12 +116,13 @@ using std::sqrt;
 
 // ---------------------------------------------------------------- lattices
 // D2Q9 in the numbering of the paper's lattice figure; D3Q19 rest, the six
-// faces and the twelve edges, each direction followed by its opposite.
+// faces and the twelve edges, each direction followed by its opposite;
+// D3Q27 adds the eight corners after them.
 struct Lattice {
   int q;
-  int c[19][3];
-  double w[19];
-  int opp[19];
+  int c[27][3];
+  double w[27];
+  int opp[27];
 };
 
 Lattice make_lattice(int q) {
@@ -137,13 +138,20 @@ Lattice make_lattice(int q) {
       L.w[k] = k == 0 ? 4.0 / 9.0 : (k < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     }
   } else {
-    const int c[19][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+    // rest, the 6 faces, the 12 edges (D3Q19), then for D3Q27 the 8
+    // corners (+-1, +-1, +-1), as the classes of the paper's lattice table
+    const int c[27][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
                           {0, 0, 1},  {0, 0, -1}, {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
                           {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
-                          {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
-    for (int k = 0; k < 19; ++k) {
+                          {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1},
+                          {1, 1, 1},  {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1},
+                          {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+    for (int k = 0; k < q; ++k) {
       for (int a = 0; a < 3; ++a) L.c[k][a] = c[k][a];
-      L.w[k] = k == 0 ? 1.0 / 3.0 : (k < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+      if (q == 19)
+        L.w[k] = k == 0 ? 1.0 / 3.0 : (k < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+      else
+        L.w[k] = k == 0 ? 8.0 / 27.0 : (k < 7 ? 2.0 / 27.0 : (k < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
     }
   }
   for (int k = 0; k < q; ++k)
@@ -749,7 +757,7 @@ R objective(const Grid& g, const OracleObjective* o, const State<R>& s) {
 int check(const OracleProblem* p) {
   if (!p) return -1;
   if (p->dim != 2 && p->dim != 3) return -1;
-  if ((p->dim == 2 && p->q != 9) || (p->dim == 3 && p->q != 19)) return -1;
+  if ((p->dim == 2 && p->q != 9) || (p->dim == 3 && p->q != 19 && p->q != 27)) return -1;
   if (p->n_phases < 2 || p->n_phases > 4 || p->n_solutes < 1 || p->n_solutes > 2) return -1;
   if (p->nx < 3 || p->ny < 3 || (p->dim == 3 && p->nz < 3)) return -1;
   return 0;
@@ -788,7 +796,7 @@ int oracle_gradient_energy(const double* q, int dim, double delta, double q_floo
 // Lattice weights w_k and velocities c_k (3 ints per direction) of the
 // lattice with q directions; f = w_k is the fluid at rest with rho = 1.
 int oracle_lattice(int q, double* w, int* c) {
-  if (q != 9 && q != 19) return -1;
+  if (q != 9 && q != 19 && q != 27) return -1;
   Lattice L = make_lattice(q);
   for (int k = 0; k < q; ++k) {
     if (w) w[k] = L.w[k];

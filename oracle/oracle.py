@@ -107,7 +107,7 @@ def problem(sc):
     p = OracleProblem()
     p.nx, p.ny, p.nz = g["nx"], g["ny"], g.get("nz", 1)
     p.dim = 3 if g.get("nz", 1) > 1 else 2
-    p.q = 19 if p.dim == 3 else 9
+    p.q = g.get("lattice") or (19 if p.dim == 3 else 9)
     p.n_phases, p.n_solutes = sc["n_phases"], sc["n_solutes"]
     for a in range(3):
         p.bc[a] = g["bc"][a]

@@ -22,7 +22,7 @@ def reference(sc, steps, phi0=None, mu0=None, f0=None):
     phi, mu, f = oracle.run(sc, phi0, mu0, f0, steps)
     c, rho, u = oracle.derived(sc, phi, mu, f, steps)
     NP, NC = sc["n_phases"], sc["n_solutes"]
-    q = 19 if sc["grid"].get("nz", 1) > 1 else 9
+    q = sc["grid"].get("lattice") or (19 if sc["grid"].get("nz", 1) > 1 else 9)
     w, _ = oracle.lattice(q)
     f = f.reshape(q, -1)
     return {"phi": phi.reshape(NP, -1), "mu": mu.reshape(NC, -1), "c": c.reshape(NC, -1),

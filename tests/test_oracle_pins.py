@@ -71,7 +71,23 @@ def test_d2q9_weights_and_numbering_match_paper_table():
         assert (c[k, 0], c[k, 1], c[k, 2]) == (cx, cy, 0)
 
 
-@pytest.mark.parametrize("q", [9, 19])
+def test_d3q27_weights_match_paper_table():
+    """Classes of the paper's lattice table: k = 0 rest, 1-6 faces, 7-18
+    edges, 19-26 corners, weights 8/27, 2/27, 1/54, 1/216."""
+    w, c = oracle.lattice(27)
+    ranges = {0: range(0, 1), 1: range(1, 7), 2: range(7, 19), 3: range(19, 27)}
+    for row in _golden("lattice_weights.txt"):
+        if row[0] != "D3Q27":
+            continue
+        c2, count, num, den = int(row[1]), int(row[2]), int(row[3]), int(row[4])
+        sel = [k for k in range(27) if (c[k] ** 2).sum() == c2]
+        assert sel == list(ranges[c2]) and len(sel) == count
+        for k in sel:
+            assert w[k] == pytest.approx(num / den, abs=0, rel=1e-15)
+    assert len({tuple(v) for v in c}) == 27
+
+
+@pytest.mark.parametrize("q", [9, 19, 27])
 def test_lattice_moments_are_isotropic(q):
     w, c = oracle.lattice(q)
     D = 2 if q == 9 else 3
@@ -442,11 +458,15 @@ def test_quiescent_isothermal_melt_stays_exactly_at_rest():
 
 
 # ----------------------------------------------------------------- conservation
-@pytest.mark.parametrize("case", ["dendrite2d", "eutectic2d", "dendrite3d", "eutectic3d"])
+@pytest.mark.parametrize("case", ["dendrite2d", "eutectic2d", "dendrite3d", "eutectic3d",
+                                  "dendrite3d/D3Q27", "eutectic3d/D3Q27"])
 def test_mass_and_solute_are_conserved(case):
+    case, _, lat = case.partition("/")
     sizes = {"dendrite2d": dict(nx=40, ny=36), "eutectic2d": dict(nx=48, ny=40),
              "dendrite3d": dict(nx=14, ny=16, nz=18), "eutectic3d": dict(nx=16, ny=14, nz=20)}
     sc = inputs.scenario(case, **sizes[case])
+    if lat:
+        sc["grid"]["lattice"] = 27
     if case == "eutectic3d":
         sc["init"]["height"] = 8
     if case == "eutectic2d":
@@ -567,13 +587,14 @@ def test_implicit_drag_decay_factor():
     np.testing.assert_allclose(u1, u0 * r ** steps, rtol=1e-12)
 
 
-@pytest.mark.parametrize("q", [9, 19])
+@pytest.mark.parametrize("q", [9, 19, 27])
 def test_streaming_moves_population_k_along_c_k(q):
     """tau = 1 makes f* = f^eq; a density excess at one cell then arrives
     one cell along c_k in population k (Eq. LBMEq_1)."""
     dim = 2 if q == 9 else 3
     n = 5
     sc, phi, mu = _liquid_box(n, n, n if dim == 3 else 1, tau_f=1.0)
+    sc["grid"]["lattice"] = q
     w, c = oracle.lattice(q)
     cells = n ** dim
     rho = np.ones(cells)
@@ -662,3 +683,31 @@ def test_shrinkage_momentum_balances_the_solidified_volume(dim):
     pr["eta_rho"] = [0.0] * 4
     _, _, f2 = oracle.run(sc, phi, mu, f0, 1)
     assert np.abs(f2 - f0).max() < 1e-15
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_3d_shear_wave_decays_at_the_bgk_viscosity(q):
+    """u_x = U sin(k z) in a periodic 3D liquid box decays as exp(-nu k^2 t),
+    nu = (tau - 1/2)/3, to second order in k, on D3Q19 and D3Q27."""
+    def rate(n, tau=0.8, U=1e-4, t0=20, t1=220):
+        sc, phi, mu = _liquid_box(4, 4, n, tau_f=tau)
+        sc["grid"]["lattice"] = q
+        w, c = oracle.lattice(q)
+        cells = 16 * n
+        k = 2 * math.pi / n
+        z = np.repeat(np.arange(n), 16)
+        u = np.zeros((3, cells))
+        u[0] = U * np.sin(k * (z + 0.5))
+        cu = c.astype(float) @ u
+        f = (w[:, None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (u * u).sum(0)[None, :])).reshape(-1)
+        amps = []
+        for tt in (t0, t1):
+            _, _, ff = oracle.run(sc, phi, mu, f, tt)
+            _, _, uu = oracle.derived(sc, phi, mu, ff, tt)
+            ux = uu.reshape(3, cells)[0]
+            amps.append((ux * np.sin(k * (z + 0.5))).sum())
+        nu = (tau - 0.5) / 3
+        return -math.log(amps[1] / amps[0]) / (t1 - t0) / (nu * k * k)
+    r16, r32 = rate(16), rate(32)
+    assert abs(r32 - 1) < 3e-3
+    assert abs(r16 - 1) / abs(r32 - 1) > 3.0  # second order in k
