@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--adjoint-ckpt", type=int, default=50)
     ap.add_argument("--adjoint-reps", type=int, default=5)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--lattice", type=int, default=None, choices=[None, 19, 27],
+                    help="3D velocity set (default D3Q19)")
     ap.add_argument("--eta", type=float, default=0.0,
                     help="shrinkage density ratio (rho_solid - rho_liquid) / rho_liquid of every solid phase")
     return ap.parse_args()
@@ -76,11 +78,17 @@ def workload(args):
     if args.eta:
         sc["params"]["eta_rho"] = [0.0] + [args.eta if a < sc["n_phases"] else 0.0 for a in range(1, 4)]
     nx, ny, nz = inputs.dims(sc)
+    if args.lattice and nz > 1:
+        sc["grid"]["lattice"] = args.lattice
     desc = "%s %s D%dQ%d N=%d K-1=%d %s%s" % (
         args.workload, "x".join(str(n) for n in (nx, ny, nz) if n > 1),
-        3 if nz > 1 else 2, 19 if nz > 1 else 9, sc["n_phases"], sc["n_solutes"], sc["precision"],
+        3 if nz > 1 else 2, lattice_q(sc), sc["n_phases"], sc["n_solutes"], sc["precision"],
         " shrinkage eta=%g" % args.eta if args.eta else "")
     return sc, desc
+
+
+def lattice_q(sc):
+    return sc["grid"].get("lattice") or (19 if sc["grid"].get("nz", 1) > 1 else 9)
 
 
 def dtype_name(sc):
@@ -92,7 +100,7 @@ def kernel_bytes_per_cell(sc):
     """Algorithmic bytes per cell of each kernel and of the whole step."""
     NP, NC = sc["n_phases"], sc["n_solutes"]
     NS = 1 if NP == 2 else NP
-    Q = 19 if sc["grid"].get("nz", 1) > 1 else 9
+    Q = lattice_q(sc)
     r = 8 if sc["precision"] == "fp64" else 4
     s = {"fp64": 8, "fp32": 4, "fp32_f16": 2, "fp32_bf16": 2}[sc["precision"]]
     pf = (NS + NC + NS) * r                            # phi^n, mu^n -> phi^{n+1}

@@ -28,6 +28,9 @@
  *    D3Q19 numbering: 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (+1,+1,0),
  *    (-1,-1,0), (+1,-1,0), (-1,+1,0), (+1,0,+1), (-1,0,-1), (+1,0,-1),
  *    (-1,0,+1), (0,+1,+1), (0,-1,-1), (0,+1,-1), (0,-1,+1).
+ *    D3Q27 (the paper's 3D set; weights 8/27, 2/27, 1/54, 1/216 by class):
+ *    the D3Q19 directions, then 19..26 = (+1,+1,+1), (-1,-1,-1), (+1,+1,-1),
+ *    (-1,-1,+1), (+1,-1,+1), (-1,+1,-1), (-1,+1,+1), (+1,-1,-1).
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *    stream-ordered and asynchronous unless stated otherwise.
  *  - Every call returns a gpflbm_status; nothing aborts.  After a failure
@@ -56,7 +59,7 @@ typedef enum {
 } gpflbm_status;
 
 enum { GPFLBM_PERIODIC = 0, GPFLBM_WALL = 1 };
-enum { GPFLBM_D2Q9 = 9, GPFLBM_D3Q19 = 19 };
+enum { GPFLBM_D2Q9 = 9, GPFLBM_D3Q19 = 19, GPFLBM_D3Q27 = 27 };
 enum {
   GPFLBM_FP64 = 0,           /* FP64 arithmetic and storage */
   GPFLBM_FP32 = 1,           /* FP32 arithmetic and storage */
@@ -84,7 +87,8 @@ enum {
  * solid (drag with phi_l = 0, no buoyancy). */
 typedef struct {
   int nx, ny, nz;    /* cells per axis; nz == 1 selects 2D */
-  int lattice;       /* GPFLBM_D2Q9 (2D) or GPFLBM_D3Q19 (3D) */
+  int lattice;       /* GPFLBM_D2Q9 (2D); GPFLBM_D3Q19 or GPFLBM_D3Q27 (3D; D3Q27 with
+                        FP64 or FP32 precision only, else GPFLBM_ERR_UNSUPPORTED) */
   int bc[3];
   int wall_rows[3];
   int precision;     /* GPFLBM_FP64 ... GPFLBM_FP32_BF16STORE */

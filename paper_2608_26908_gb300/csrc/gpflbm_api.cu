@@ -73,8 +73,15 @@ gpflbm_status cuda_fail(gpflbm_t h, cudaError_t e, const char* where) {
   return fail(h, GPFLBM_ERR_CUDA, m);
 }
 
-const Ops* find_ops(int D, int precision, int NP, int NC) {
+const Ops* find_ops(int D, int lattice, int precision, int NP, int NC) {
   using namespace gpflbm;
+  if (lattice == GPFLBM_D3Q27) {
+    switch (precision) {
+      case GPFLBM_FP64: return ops_d3q27_fp64(NP, NC);
+      case GPFLBM_FP32: return ops_d3q27_fp32(NP, NC);
+    }
+    return nullptr;
+  }
   if (D == 2) {
     switch (precision) {
       case GPFLBM_FP64: return ops_d2_fp64(NP, NC);
@@ -110,8 +117,9 @@ gpflbm_status check_grid(const gpflbm_grid* g, int NP, int NC, int* D, const Ops
     return GPFLBM_ERR_ARG;
   }
   *D = g->nz == 1 ? 2 : 3;
-  if ((*D == 2 && g->lattice != GPFLBM_D2Q9) || (*D == 3 && g->lattice != GPFLBM_D3Q19)) {
-    *why = "lattice must be D2Q9 for nz == 1 and D3Q19 otherwise";
+  if ((*D == 2 && g->lattice != GPFLBM_D2Q9) ||
+      (*D == 3 && g->lattice != GPFLBM_D3Q19 && g->lattice != GPFLBM_D3Q27)) {
+    *why = "lattice must be D2Q9 for nz == 1 and D3Q19 or D3Q27 otherwise";
     return GPFLBM_ERR_UNSUPPORTED;
   }
   for (int a = 0; a < 3; ++a) {
@@ -142,7 +150,7 @@ gpflbm_status check_grid(const gpflbm_grid* g, int NP, int NC, int* D, const Ops
     *why = "n_phases must be 2..4 and n_components 1..2";
     return GPFLBM_ERR_UNSUPPORTED;
   }
-  *ops = find_ops(*D, g->precision, NP, NC);
+  *ops = find_ops(*D, g->lattice, g->precision, NP, NC);
   if (!*ops) {
     *why = "configuration not built";
     return GPFLBM_ERR_UNSUPPORTED;

@@ -68,15 +68,22 @@ struct Lattice<19> {
   }
 };
 
-template <int D>
-struct LatticeOf;
+// D3Q27: the D3Q19 directions, then the eight corners (+-1, +-1, +-1):
+// c = sign * (+,+,+), (+,+,-), (+,-,+), (-,+,+) for corner pair p = 0..3,
+// sign + for the first of the pair and - for its opposite.
 template <>
-struct LatticeOf<2> {
-  using type = Lattice<9>;
-};
-template <>
-struct LatticeOf<3> {
-  using type = Lattice<19>;
+struct Lattice<27> {
+  static constexpr int D = 3;
+  __host__ __device__ static constexpr int c(int k, int a) {
+    return k < 19 ? Lattice<19>::c(k, a) : corner_c(k - 19, a);
+  }
+  __host__ __device__ static constexpr int corner_c(int e, int a) {
+    return ((e / 2 != 0 && a == 3 - e / 2) ? -1 : 1) * ((e & 1) ? -1 : 1);
+  }
+  __host__ __device__ static constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+  __host__ __device__ static constexpr double w(int k) {
+    return k == 0 ? 8.0 / 27.0 : (k < 7 ? 2.0 / 27.0 : (k < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
+  }
 };
 
 // ------------------------------------------------------------------ storage codec
@@ -405,15 +412,14 @@ __global__ void load_f_kernel(long long cells, int nx, int px, long long plane,
 // Exchange-format fields of the current state; any output may be null.
 // phi: N planes (liquid first); c_i = sum_a h_a (ceq_a,i + mu_i / (2 A_a));
 // f = w + d; rho = 1 + sum d; U as in the step (force-corrected); dev = d.
-template <int D, int NP, int NC, class Real, class Store, class Out>
+template <int D, int Q, int NP, int NC, class Real, class Store, class Out>
 __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ phi,
                               const Real* __restrict__ mu_in, const Store* __restrict__ f,
                               const double* __restrict__ clock, Out* __restrict__ o_phi,
                               Out* __restrict__ o_mu, Out* __restrict__ o_c, Out* __restrict__ o_f,
                               Out* __restrict__ o_rho, Out* __restrict__ o_u,
                               Out* __restrict__ o_dev) {
-  using Lat = typename LatticeOf<D>::type;
-  constexpr int Q = D == 2 ? 9 : 19;
+  using Lat = Lattice<Q>;
   const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
   const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (x >= cells) return;

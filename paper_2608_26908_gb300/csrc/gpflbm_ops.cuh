@@ -57,12 +57,13 @@ struct Ops {
                             double* partial, int blocks, double* out, cudaStream_t s);
 };
 
-template <int D, int NP, int NC, class Real, class Store>
+// QQ: lattice size (0 = D2Q9 in 2D, D3Q19 in 3D; 27 = D3Q27)
+template <int D, int NP, int NC, class Real, class Store, int QQ = 0>
 struct Impl {
-  static constexpr int Q = D == 2 ? 9 : 19;
+  static constexpr int Q = QQ ? QQ : (D == 2 ? 9 : 19);
 
   using SZ = Step2D<NP, NC, Real, Store>;
-  using S3 = Step3D<NP, NC, Real, Store>;
+  using S3 = Step3D<NP, NC, Real, Store, (D == 3 ? Q : 19)>;
 
   static cudaError_t configure() {
     cudaError_t e;
@@ -73,10 +74,10 @@ struct Impl {
         e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
     } else {
-      e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false>,
+      e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false, Q>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true>,
+        e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
     }
     return e;
@@ -98,9 +99,9 @@ struct Impl {
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
       if (P.shrink)
-        step3d_kernel<NP, NC, Real, Store, true><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, true, Q><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
       else
-        step3d_kernel<NP, NC, Real, Store, false><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, false, Q><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
     }
     return cudaGetLastError();
   }
@@ -137,7 +138,7 @@ struct Impl {
     const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
     const int threads = 256;
     const unsigned blocks = (unsigned)((cells + threads - 1) / threads);
-    fields_kernel<D, NP, NC, Real, Store, Real><<<blocks, threads, 0, s>>>(
+    fields_kernel<D, Q, NP, NC, Real, Store, Real><<<blocks, threads, 0, s>>>(
         P, static_cast<const Real*>(io.phi), static_cast<const Real*>(io.mu),
         static_cast<const Store*>(io.f), io.clock, static_cast<Real*>(io.o_phi),
         static_cast<Real*>(io.o_mu), static_cast<Real*>(io.o_c), static_cast<Real*>(io.o_f),
@@ -183,16 +184,19 @@ const Ops* ops_d3_fp64(int NP, int NC);
 const Ops* ops_d3_fp32(int NP, int NC);
 const Ops* ops_d3_f16(int NP, int NC);
 const Ops* ops_d3_bf16(int NP, int NC);
+const Ops* ops_d3q27_fp64(int NP, int NC);  // D3Q27 (FP64 and FP32 arithmetic and storage)
+const Ops* ops_d3q27_fp32(int NP, int NC);
 
-#define GPFLBM_DEFINE_OPS(NAME, DIM, REAL, STORE)                            \
-  const Ops* NAME(int NP, int NC) {                                          \
-    if (NP == 2 && NC == 1) return Impl<DIM, 2, 1, REAL, STORE>::table();    \
-    if (NP == 2 && NC == 2) return Impl<DIM, 2, 2, REAL, STORE>::table();    \
-    if (NP == 3 && NC == 1) return Impl<DIM, 3, 1, REAL, STORE>::table();    \
-    if (NP == 3 && NC == 2) return Impl<DIM, 3, 2, REAL, STORE>::table();    \
-    if (NP == 4 && NC == 1) return Impl<DIM, 4, 1, REAL, STORE>::table();    \
-    if (NP == 4 && NC == 2) return Impl<DIM, 4, 2, REAL, STORE>::table();    \
-    return nullptr;                                                          \
+#define GPFLBM_DEFINE_OPS_Q(NAME, DIM, QQ, REAL, STORE)                        \
+  const Ops* NAME(int NP, int NC) {                                            \
+    if (NP == 2 && NC == 1) return Impl<DIM, 2, 1, REAL, STORE, QQ>::table();  \
+    if (NP == 2 && NC == 2) return Impl<DIM, 2, 2, REAL, STORE, QQ>::table();  \
+    if (NP == 3 && NC == 1) return Impl<DIM, 3, 1, REAL, STORE, QQ>::table();  \
+    if (NP == 3 && NC == 2) return Impl<DIM, 3, 2, REAL, STORE, QQ>::table();  \
+    if (NP == 4 && NC == 1) return Impl<DIM, 4, 1, REAL, STORE, QQ>::table();  \
+    if (NP == 4 && NC == 2) return Impl<DIM, 4, 2, REAL, STORE, QQ>::table();  \
+    return nullptr;                                                            \
   }
+#define GPFLBM_DEFINE_OPS(NAME, DIM, REAL, STORE) GPFLBM_DEFINE_OPS_Q(NAME, DIM, 0, REAL, STORE)
 
 }  // namespace gpflbm

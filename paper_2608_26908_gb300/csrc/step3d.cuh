@@ -35,15 +35,15 @@ struct Block3D<double> {
   static constexpr int BX = 32, BY = 8, ZS = 16;
 };
 
-template <int NP, int NC, class Real, class Store>
+template <int NP, int NC, class Real, class Store, int QQ = 19>
 struct Step3D {
   static constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZS;
-  static constexpr int NT = BX * BY, Q = 19;
+  static constexpr int NT = BX * BY, Q = QQ;  // D3Q19 or D3Q27
   static constexpr int NS = PhiStore<NP>::NS;
   // resident CTAs per SM the register budget is cut for: two (64 registers)
-  // for two phases in FP32; with more phases the phase-field registers
-  // spill at 64, and one CTA of 128 registers runs faster
-  static constexpr int MIN_CTAS = (sizeof(Real) == 4 && NP == 2) ? 2 : 1;
+  // for two phases on D3Q19 in FP32; with more phases, or 27 populations,
+  // the registers spill at 64 and one CTA of 128 registers runs faster
+  static constexpr int MIN_CTAS = (sizeof(Real) == 4 && NP == 2 && QQ == 19) ? 2 : 1;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;
   static constexpr int RING = C2 - NT;
@@ -75,12 +75,12 @@ struct Step3DIO {
 
 // SHRINK: the shrinkage force needs phi^{n+1}, so the collision of a plane
 // moves after its phase-field update (its populations are read again then).
-template <int NP, int NC, class Real, class Store, bool SHRINK = false>
-__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store>::NT, Step3D<NP, NC, Real, Store>::MIN_CTAS)
+template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19>
+__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
-  using S = Step3D<NP, NC, Real, Store>;
-  using Lat = Lattice<19>;
-  constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = 19;
+  using S = Step3D<NP, NC, Real, Store, QQ>;
+  using Lat = Lattice<QQ>;
+  constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
   constexpr int W2 = S::W2, H2 = S::H2, C2 = S::C2, NS = S::NS;
   extern __shared__ __align__(16) unsigned char smem[];
   Real* s_phi = reinterpret_cast<Real*>(smem + S::phi);

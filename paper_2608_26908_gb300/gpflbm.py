@@ -16,7 +16,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = (
     -1, -2, -3, -4, -5, -6, -7)
 PERIODIC, WALL = 0, 1
-D2Q9, D3Q19 = 9, 19
+D2Q9, D3Q19, D3Q27 = 9, 19, 27
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_f16": 2, "fp32_bf16": 3}
 FIELD = {"phi": 1, "mu": 2, "c": 4, "f": 8, "rho": 16, "u": 32}
 
@@ -106,7 +106,7 @@ def grid_struct(sc):
     g = sc["grid"]
     s = Grid()
     s.nx, s.ny, s.nz = g["nx"], g["ny"], g.get("nz", 1)
-    s.lattice = D3Q19 if s.nz > 1 else D2Q9
+    s.lattice = g.get("lattice") or (D3Q19 if s.nz > 1 else D2Q9)
     for a in range(3):
         s.bc[a] = g["bc"][a]
         s.wall_rows[a] = g["wall_rows"][a] if (a < 2 or s.nz > 1) else 0
@@ -161,7 +161,7 @@ class Sim:
         self.nx, self.ny, self.nz = sc["grid"]["nx"], sc["grid"]["ny"], sc["grid"].get("nz", 1)
         self.cells = self.nx * self.ny * self.nz
         self.dim = 3 if self.nz > 1 else 2
-        self.Q = 19 if self.dim == 3 else 9
+        self.Q = sc["grid"].get("lattice") or (19 if self.dim == 3 else 9)
         self.NP, self.NC = sc["n_phases"], sc["n_solutes"]
         self.dtype = np.float64 if sc["precision"] == "fp64" else np.float32
         self.tdtype = torch.float64 if sc["precision"] == "fp64" else torch.float32

@@ -87,12 +87,17 @@ def host_invariants(sim, sc):
 CASES = [("dendrite2d", dict(), "fp64"), ("eutectic2d", dict(nx=200, ny=90), "fp32"),
          ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp32"),
          ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp32_f16"),
-         ("eutectic3d", dict(nx=36, ny=34, nz=40), "fp32")]
+         ("eutectic3d", dict(nx=36, ny=34, nz=40), "fp32"),
+         ("dendrite3d", dict(nx=40, ny=36, nz=33, lattice=27), "fp32")]
 
 
 @pytest.mark.parametrize("name,size,prec", CASES)
 def test_invariants_match_host_resummation_bit_for_bit(name, size, prec):
+    size = dict(size)
+    lattice = size.pop("lattice", None)
     sc = inputs.scenario(name, precision=prec, **size)
+    if lattice:
+        sc["grid"]["lattice"] = lattice
     if name == "eutectic3d":
         sc["init"]["height"] = 12
     phi0, mu0 = inputs.initial_state(sc)
@@ -110,7 +115,11 @@ def test_invariants_match_host_resummation_bit_for_bit(name, size, prec):
 
 @pytest.mark.parametrize("name,size,prec", CASES)
 def test_conservation_drift_over_100_steps(name, size, prec):
+    size = dict(size)
+    lattice = size.pop("lattice", None)
     sc = inputs.scenario(name, precision=prec, **size)
+    if lattice:
+        sc["grid"]["lattice"] = lattice
     if name == "eutectic3d":
         sc["init"]["height"] = 12
     sc["params"]["gbeta_c"] = [2e-3, 1e-3]  # stronger flow than the default

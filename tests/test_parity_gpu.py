@@ -173,3 +173,31 @@ def test_state_round_trip_is_exact():
         np.testing.assert_array_equal(got["mu"].reshape(-1), mu0.astype(dt))
         if prec == "fp64":
             np.testing.assert_allclose(got["f"].reshape(-1), f0, rtol=0, atol=1e-16)
+
+
+# ------------------------------------------------------------------ D3Q27
+@pytest.mark.parametrize("name,size,prec", [
+    ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp64"),
+    ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp32"),
+    ("eutectic3d", dict(nx=36, ny=34, nz=40), "fp32"),
+])
+def test_parity_d3q27_100_steps(name, size, prec):
+    """The paper's own 3D velocity set, same tolerances as D3Q19."""
+    sc = inputs.scenario(name, precision=prec, **size)
+    sc["grid"]["lattice"] = 27
+    if name == "eutectic3d":
+        sc["init"]["height"] = 12
+    sc["params"]["gbeta_c"] = [2e-3, 1e-3]  # a flow that exercises the corners
+    errs, sim, got, ref = errors(sc, 100)
+    _report(name + "/D3Q27", prec, errs)
+    for k, e in errs.items():
+        assert e <= _tol(prec, k), (k, e)
+
+
+def test_d3q27_needs_fp64_or_fp32():
+    from paper_2608_26908_gb300 import gpflbm
+    sc = inputs.scenario("dendrite3d", nx=16, ny=16, nz=16, precision="fp32_f16")
+    sc["grid"]["lattice"] = 27
+    with pytest.raises(gpflbm.GpflbmError) as e:
+        gpflbm.workspace_bytes(sc)
+    assert e.value.status == gpflbm.ERR_UNSUPPORTED

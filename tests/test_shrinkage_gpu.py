@@ -24,11 +24,16 @@ CASES = [
     ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp32"),
     ("dendrite3d", dict(nx=40, ny=36, nz=33), "fp64"),
     ("eutectic3d", dict(nx=36, ny=34, nz=40), "fp32"),
+    ("dendrite3d", dict(nx=40, ny=36, nz=33, lattice=27), "fp32"),
 ]
 
 
 def _case(name, size, prec, eta=ETA):
+    size = dict(size)
+    lattice = size.pop("lattice", None)
     sc = inputs.scenario(name, precision=prec, **size)
+    if lattice:
+        sc["grid"]["lattice"] = lattice
     if name == "eutectic3d":
         sc["init"]["height"] = 12
     sc["params"]["eta_rho"] = [0.0] + [eta if a < sc["n_phases"] else 0.0 for a in range(1, 4)]
