@@ -70,6 +70,7 @@ typedef struct {
   double G, V, v0;
   double q_floor;      // |q|^2 at or below which the anisotropy is dropped
   double eta[4];       // shrinkage (rho_a - rho_liq) / rho_liq per phase, Eq. shrinkage
+  double tilt[4][4];   // crystal axes of a pair turned by this angle about z (radians)
 } OracleProblem;
 
 // Objective for the gradient checks: J = w_frac * mean_x sum_{a>0} h_a(phi)
@@ -294,6 +295,26 @@ void dA_dq(const R* q, int dim, const R& delta, double q_floor, R* out) {
   }
 }
 
+// dA/dq of a pair whose crystal axes are turned by theta about the z axis
+// (a tilted seed, the misorientation of the paper's dendrites): the cubic
+// anisotropy is a function of the crystal components
+// q' = (c qx + s qy, -s qx + c qy, qz), c = cos theta, s = sin theta, and
+// dA/dq = R^T dA/dq' by the chain rule.
+template <class R>
+void dA_dq_tilted(const R* q, int dim, const R& delta, double theta, double q_floor, R* out) {
+  if (theta == 0.0) {
+    dA_dq(q, dim, delta, q_floor, out);
+    return;
+  }
+  const double c = std::cos(theta), sn = std::sin(theta);
+  R qr[3] = {c * q[0] + sn * q[1], -sn * q[0] + c * q[1], dim == 3 ? q[2] : R(0.0)};
+  R d[3];
+  dA_dq(qr, dim, delta, q_floor, d);
+  out[0] = c * d[0] - sn * d[1];
+  out[1] = sn * d[0] + c * d[1];
+  if (dim == 3) out[2] = d[2];
+}
+
 // A(q) itself (same floor rule as dA_dq).
 double A_value(const double* q, int dim, double delta, double q_floor) {
   double s2 = 0.0, s4 = 0.0;
@@ -462,7 +483,7 @@ void phase_field_update(const Grid& g, const Coeffs<R>& k, const State<R>& s, do
           if (b == a) continue;
           R qv[3], dA[3];
           for (int j = 0; j < D; ++j) qv[j] = pf[a] * gr[b][j] - pf[b] * gr[a][j];
-          dA_dq(qv, D, k.delta[a][b], p->q_floor, dA);
+          dA_dq_tilted(qv, D, k.delta[a][b], p->tilt[a][b], p->q_floor, dA);
           acc -= p->gamma[a][b] * pf[b] * dA[d];
         }
         flux[((long)d * N + a) * cells + x] = acc;
@@ -503,7 +524,7 @@ void phase_field_update(const Grid& g, const Coeffs<R>& k, const State<R>& s, do
         if (b == a) continue;
         R qv[3], dA[3];
         for (int j = 0; j < D; ++j) qv[j] = ph[a] * gc[b][j] - ph[b] * gc[a][j];
-        dA_dq(qv, D, k.delta[a][b], p->q_floor, dA);
+        dA_dq_tilted(qv, D, k.delta[a][b], p->tilt[a][b], p->q_floor, dA);
         for (int j = 0; j < D; ++j) dadphi[a] += p->gamma[a][b] * dA[j] * gc[b][j];
       }
     }
@@ -783,13 +804,16 @@ int oracle_max_threads(void) {
 #endif
 }
 
-// Gradient-energy density A(q) of one pair and its derivative dA/dq.
-int oracle_gradient_energy(const double* q, int dim, double delta, double q_floor, double* A,
-                           double* dA) {
+// Gradient-energy density A(q) of one pair and its derivative dA/dq, with
+// the crystal axes turned by theta about z.
+int oracle_gradient_energy(const double* q, int dim, double delta, double theta, double q_floor,
+                           double* A, double* dA) {
   if (dim != 2 && dim != 3) return -1;
-  *A = A_value(q, dim, delta, q_floor);
+  const double c = std::cos(theta), sn = std::sin(theta);
+  const double qr[3] = {c * q[0] + sn * q[1], -sn * q[0] + c * q[1], dim == 3 ? q[2] : 0.0};
+  *A = A_value(theta == 0.0 ? q : qr, dim, delta, q_floor);
   double d = delta;
-  dA_dq(q, dim, d, q_floor, dA);
+  dA_dq_tilted(q, dim, d, theta, q_floor, dA);
   return 0;
 }
 

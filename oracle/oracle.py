@@ -52,6 +52,7 @@ class OracleProblem(ctypes.Structure):
         ("G", ctypes.c_double), ("V", ctypes.c_double), ("v0", ctypes.c_double),
         ("q_floor", ctypes.c_double),
         ("eta", ctypes.c_double * 4),
+        ("tilt", (ctypes.c_double * 4) * 4),
     ]
 
 
@@ -79,7 +80,8 @@ def lib():
         L.oracle_objective.argtypes = [P, O, ctypes.c_long, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
         L.oracle_objective_value.argtypes = [P, O, dp, dp]
         L.oracle_lattice.argtypes = [ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]
-        L.oracle_gradient_energy.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp,
+        L.oracle_gradient_energy.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                             ctypes.c_double, dp,
                                              dp]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_max_threads.restype = ctypes.c_int
@@ -128,6 +130,8 @@ def problem(sc):
         p.c_ref[i] = pr["c_ref"][i]
     for a in range(4):
         p.eta[a] = pr.get("eta_rho", [0.0] * 4)[a]
+        for b in range(4):
+            p.tilt[a][b] = pr.get("tilt", [[0.0] * 4] * 4)[a][b]
     return p
 
 
@@ -138,12 +142,13 @@ def lattice(q):
     return w, c.reshape(q, 3)
 
 
-def gradient_energy(q, delta, q_floor=1e-12):
-    """(A(q), dA/dq) of the pairwise gradient-energy density."""
+def gradient_energy(q, delta, q_floor=1e-12, theta=0.0):
+    """(A(q), dA/dq) of the pairwise gradient-energy density, crystal axes
+    turned by theta about z."""
     q = np.ascontiguousarray(q, dtype=np.float64)
     A = ctypes.c_double()
     dA = np.zeros(len(q))
-    assert lib().oracle_gradient_energy(_dp(q), len(q), float(delta), float(q_floor),
+    assert lib().oracle_gradient_energy(_dp(q), len(q), float(delta), float(theta), float(q_floor),
                                         ctypes.byref(A), _dp(dA)) == 0
     return A.value, dA
 

@@ -74,6 +74,7 @@ def _blank_params():
         "T_E": 1.0, "undercool": 0.0, "G": 0.0, "V": 0.0, "v0": 0.0,
         "q_floor": 1e-12,
         "eta_rho": [0.0] * 4,  # shrinkage (rho_a - rho_l) / rho_l per phase; off unless set
+        "tilt": [row[:] for row in z4],  # crystal axes of a pair turned about z (radians)
     }
 
 

@@ -201,6 +201,96 @@ def test_gradient_energy_derivative_matches_finite_difference(dim):
     np.testing.assert_array_equal(dA, 2 * q)
 
 
+# ------------------------------------------------------------ tilted crystal axes
+def test_tilted_anisotropy_is_one_plus_delta_cos4_of_the_angle_to_the_axis():
+    """Crystal axes turned by theta about z: the 2D density is
+    (1 + delta cos 4(vartheta - theta))^2 |q|^2, vartheta the polar angle of q
+    (a wrong sense of rotation gives cos 4(vartheta + theta) and fails)."""
+    for theta in (0.3, -0.55, 1.0):
+        for th in np.linspace(0, 2 * math.pi, 29):
+            r = 0.41
+            q = [r * math.cos(th), r * math.sin(th)]
+            A, _ = oracle.gradient_energy(q, 0.05, theta=theta)
+            assert A == pytest.approx((1 + 0.05 * math.cos(4 * (th - theta))) ** 2 * r * r, rel=1e-13)
+    # in 3D the <100> axis in the x-y plane lies at angle theta
+    d, theta = 0.03, 0.4
+    q = 0.5 * np.array([math.cos(theta), math.sin(theta), 0.0])
+    assert oracle.gradient_energy(q, d, theta=theta)[0] == pytest.approx((1 + d) ** 2 * 0.25, rel=1e-13)
+    q = 0.5 * np.array([math.cos(theta + math.pi / 4), math.sin(theta + math.pi / 4), 0.0])
+    assert oracle.gradient_energy(q, d, theta=theta)[0] == pytest.approx((1 - d) ** 2 * 0.25, rel=1e-13)
+    # the z axis is untouched by a turn about z
+    q = np.array([0.0, 0.0, 0.7])
+    assert oracle.gradient_energy(q, d, theta=theta)[0] == pytest.approx((1 + d) ** 2 * 0.49, rel=1e-13)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_tilted_gradient_energy_derivative_matches_finite_difference(dim):
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        q = rng.normal(size=dim)
+        theta = rng.uniform(-math.pi, math.pi)
+        _, dA = oracle.gradient_energy(q, 0.04, theta=theta)
+        h = 1e-6
+        fd = np.zeros(dim)
+        for j in range(dim):
+            e = np.zeros(dim)
+            e[j] = h
+            fd[j] = (oracle.gradient_energy(q + e, 0.04, theta=theta)[0]
+                     - oracle.gradient_energy(q - e, 0.04, theta=theta)[0]) / (2 * h)
+        np.testing.assert_allclose(dA, fd, rtol=1e-7, atol=1e-9)
+
+
+def _tilted_seed(dim, theta, delta_sign=1.0, steps=30):
+    if dim == 2:
+        sc = inputs.scenario("dendrite2d", nx=36, ny=36)
+    else:
+        sc = inputs.scenario("dendrite3d", nx=20, ny=20, nz=12)
+    sc["init"]["noise"] = 0.0
+    pr = sc["params"]
+    pr["delta"] = [[delta_sign * v for v in row] for row in pr["delta"]]
+    pr["tilt"] = [[theta if (a == 0) != (b == 0) else 0.0 for b in range(4)] for a in range(4)]
+    phi, mu = inputs.initial_state(sc)
+    nx, ny, nz = inputs.dims(sc)
+    phi1, mu1, f1 = oracle.run(sc, phi, mu, oracle.rest_populations(sc), steps)
+    shape = (nz, ny, nx)
+    return (phi1.reshape((-1,) + shape), mu1.reshape((-1,) + shape),
+            oracle.derived(sc, phi1, mu1, f1)[2].reshape((-1,) + shape))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_quarter_turn_of_cubic_axes_changes_nothing(dim):
+    """Cubic symmetry: axes turned by pi/2 give the untilted step."""
+    a = _tilted_seed(dim, 0.0)
+    b = _tilted_seed(dim, math.pi / 2)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(y, x, rtol=0, atol=1e-12 * max(1.0, np.abs(x).max()))
+
+
+def test_eighth_turn_in_2d_flips_the_sign_of_delta():
+    """cos 4(vartheta - pi/4) = -cos 4 vartheta: tilt pi/4 with delta is the
+    untilted step with -delta."""
+    a = _tilted_seed(2, 0.0, delta_sign=-1.0)
+    b = _tilted_seed(2, math.pi / 4)
+    for x, y in zip(a, b):
+        np.testing.assert_allclose(y, x, rtol=0, atol=1e-12 * max(1.0, np.abs(x).max()))
+    c = _tilted_seed(2, 0.0)
+    assert np.abs(c[0] - b[0]).max() > 1e-6  # the anisotropy does act
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_mirror_in_x_turns_theta_into_minus_theta(dim):
+    """A seed centred in a box symmetric under x -> -x: the run with tilt
+    -theta is the mirror image of the run with +theta (u_x changes sign)."""
+    phi_p, mu_p, u_p = _tilted_seed(dim, 0.35)
+    phi_m, mu_m, u_m = _tilted_seed(dim, -0.35)
+    flip = lambda a: a[..., ::-1]
+    np.testing.assert_allclose(flip(phi_m), phi_p, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(flip(mu_m), mu_p, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(-flip(u_m[0]), u_p[0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(flip(u_m[1:]), u_p[1:], rtol=0, atol=1e-14)
+    assert np.abs(phi_p - flip(phi_p)).max() > 1e-6  # the tilted seed is not symmetric itself
+
+
 # ----------------------------------------------------------------- phase field
 def _lap(a, dim):
     out = -2 * dim * a
