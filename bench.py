@@ -69,6 +69,8 @@ def parse():
                     help="3D velocity set (default D3Q19)")
     ap.add_argument("--eta", type=float, default=0.0,
                     help="shrinkage density ratio (rho_solid - rho_liquid) / rho_liquid of every solid phase")
+    ap.add_argument("--tilt", type=float, default=0.0,
+                    help="turn of every solid-liquid pair's crystal axes about z, radians")
     return ap.parse_args()
 
 
@@ -77,13 +79,18 @@ def workload(args):
                          nz=args.nz)
     if args.eta:
         sc["params"]["eta_rho"] = [0.0] + [args.eta if a < sc["n_phases"] else 0.0 for a in range(1, 4)]
+    if args.tilt:
+        NP = sc["n_phases"]
+        sc["params"]["tilt"] = [[args.tilt if a < NP and b < NP and (a == 0) != (b == 0) else 0.0
+                                 for b in range(4)] for a in range(4)]
     nx, ny, nz = inputs.dims(sc)
     if args.lattice and nz > 1:
         sc["grid"]["lattice"] = args.lattice
-    desc = "%s %s D%dQ%d N=%d K-1=%d %s%s" % (
+    desc = "%s %s D%dQ%d N=%d K-1=%d %s%s%s" % (
         args.workload, "x".join(str(n) for n in (nx, ny, nz) if n > 1),
         3 if nz > 1 else 2, lattice_q(sc), sc["n_phases"], sc["n_solutes"], sc["precision"],
-        " shrinkage eta=%g" % args.eta if args.eta else "")
+        " shrinkage eta=%g" % args.eta if args.eta else "",
+        " tilt=%g" % args.tilt if args.tilt else "")
     return sc, desc
 
 

@@ -115,6 +115,13 @@ typedef struct {
   double eta_rho[4];               /* shrinkage (rho_a - rho_0) / rho_0 per phase (Eq. shrinkage):
                                       G_S = sum_a eta_a (phi_a^{n+1} - phi_a^n) grad phi_a / |grad phi_a|
                                       joins the buoyancy in U and F; all 0 = no shrinkage */
+  double tilt[4][4];               /* crystal axes of pair (a, b) turned by this angle (radians,
+                                      counter-clockwise about z; symmetric, finite): the
+                                      anisotropy of Eq. PhfGrand is evaluated on
+                                      q' = (c q_x + s q_y, -s q_x + c q_y, q_z), c = cos, s = sin,
+                                      so the fastest growth of a delta > 0 crystal points at the
+                                      angle; the seed misorientation theta of the paper's
+                                      dendrite cases.  All 0 = axis-aligned crystals */
 } gpflbm_params;
 
 /* Device bytes the library needs for a problem (state ping-pong buffers,
@@ -230,7 +237,8 @@ gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_e
  * recomputed from its checkpoint on a second stream (the library's own).
  * Cost: H + (ceil(H/K) - 1)(K - 1) forward steps plus H adjoint steps.
  * Supported: 2D, D2Q9, two phases, one solute, GPFLBM_FP64 or GPFLBM_FP32,
- * no shrinkage (eta_rho all 0); anything else: GPFLBM_ERR_UNSUPPORTED.
+ * no shrinkage (eta_rho all 0), axis-aligned crystals (tilt all 0); anything else:
+ * GPFLBM_ERR_UNSUPPORTED.
  * Outputs (each may be NULL): *J; dparams[0] = dJ/d(1/tau_phi),
  * dparams[1] = dJ/d delta_01, dparams[2] = dJ/d gbeta_c[0] (FP64,
  * accumulated per cell in FP64 and summed in a fixed order); dmu0 =

@@ -36,8 +36,20 @@ def _headers_mtime():
     return max(os.path.getmtime(h) for h in hs)
 
 
-def _compile(src, extra):
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+def _units():
+    """(source, object name, defines): every csrc/*.cu once, and each kernel
+    instance file a second time with the turned-crystal-axes kernels."""
+    units = []
+    for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
+        name = os.path.basename(src)[:-3]
+        units.append((src, name, []))
+        if name.startswith("inst_"):
+            units.append((src, name + "_tilt", ["-DGPFLBM_TILT=1"]))
+    return units
+
+
+def _compile(src, name, extra):
+    obj = os.path.join(BUILD, name + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj, None
     cmd = [nvcc()] + ARCH + FLAGS + extra + ["-c", src, "-o", obj + ".tmp"]
@@ -51,10 +63,12 @@ def _compile(src, extra):
 def build(verbose=False, jobs=None, extra=()):
     """Compile every csrc/*.cu and link _build/libgpflbm.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
+    units = _units()
+    # the long 3D instance files first, so that they do not finish last
+    units.sort(key=lambda u: (not u[1].startswith("inst_d3"), u[1]))
+    jobs = jobs or min(len(units), max(2, os.cpu_count() or 2))
     with concurrent.futures.ThreadPoolExecutor(jobs) as pool:
-        results = list(pool.map(lambda s: _compile(s, list(extra)), srcs))
+        results = list(pool.map(lambda u: _compile(u[0], u[1], u[2] + list(extra)), units))
     errors = [e for _, e in results if e]
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))

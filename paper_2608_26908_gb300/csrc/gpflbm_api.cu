@@ -42,6 +42,7 @@ struct gpflbm_s {
   long long cells, plane;
   int px;  // padded row pitch (elements)
   const Ops* ops;
+  const Ops* ops_tilt;  // the same configuration with turned crystal axes
   Layout lay;
   unsigned char* ws;
   bool owns_ws;
@@ -73,30 +74,36 @@ gpflbm_status cuda_fail(gpflbm_t h, cudaError_t e, const char* where) {
   return fail(h, GPFLBM_ERR_CUDA, m);
 }
 
-const Ops* find_ops(int D, int lattice, int precision, int NP, int NC) {
+// The kernel table the time steps use: the turned-axes kernels when a pair
+// of the problem's phases has a nonzero tilt.
+const Ops* stepper(gpflbm_t h) { return h->pf.tilted ? h->ops_tilt : h->ops; }
+
+const Ops* find_ops(int D, int lattice, int precision, int NP, int NC, bool tilt) {
   using namespace gpflbm;
+#define GPFLBM_PICK(NAME) return tilt ? NAME##_tilt(NP, NC) : NAME(NP, NC)
   if (lattice == GPFLBM_D3Q27) {
     switch (precision) {
-      case GPFLBM_FP64: return ops_d3q27_fp64(NP, NC);
-      case GPFLBM_FP32: return ops_d3q27_fp32(NP, NC);
+      case GPFLBM_FP64: GPFLBM_PICK(ops_d3q27_fp64);
+      case GPFLBM_FP32: GPFLBM_PICK(ops_d3q27_fp32);
     }
     return nullptr;
   }
   if (D == 2) {
     switch (precision) {
-      case GPFLBM_FP64: return ops_d2_fp64(NP, NC);
-      case GPFLBM_FP32: return ops_d2_fp32(NP, NC);
-      case GPFLBM_FP32_F16STORE: return ops_d2_f16(NP, NC);
-      case GPFLBM_FP32_BF16STORE: return ops_d2_bf16(NP, NC);
+      case GPFLBM_FP64: GPFLBM_PICK(ops_d2_fp64);
+      case GPFLBM_FP32: GPFLBM_PICK(ops_d2_fp32);
+      case GPFLBM_FP32_F16STORE: GPFLBM_PICK(ops_d2_f16);
+      case GPFLBM_FP32_BF16STORE: GPFLBM_PICK(ops_d2_bf16);
     }
   } else {
     switch (precision) {
-      case GPFLBM_FP64: return ops_d3_fp64(NP, NC);
-      case GPFLBM_FP32: return ops_d3_fp32(NP, NC);
-      case GPFLBM_FP32_F16STORE: return ops_d3_f16(NP, NC);
-      case GPFLBM_FP32_BF16STORE: return ops_d3_bf16(NP, NC);
+      case GPFLBM_FP64: GPFLBM_PICK(ops_d3_fp64);
+      case GPFLBM_FP32: GPFLBM_PICK(ops_d3_fp32);
+      case GPFLBM_FP32_F16STORE: GPFLBM_PICK(ops_d3_f16);
+      case GPFLBM_FP32_BF16STORE: GPFLBM_PICK(ops_d3_bf16);
     }
   }
+#undef GPFLBM_PICK
   return nullptr;
 }
 
@@ -150,7 +157,7 @@ gpflbm_status check_grid(const gpflbm_grid* g, int NP, int NC, int* D, const Ops
     *why = "n_phases must be 2..4 and n_components 1..2";
     return GPFLBM_ERR_UNSUPPORTED;
   }
-  *ops = find_ops(*D, g->lattice, g->precision, NP, NC);
+  *ops = find_ops(*D, g->lattice, g->precision, NP, NC, false);
   if (!*ops) {
     *why = "configuration not built";
     return GPFLBM_ERR_UNSUPPORTED;
@@ -205,6 +212,12 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
     P.chi_pure[a] = Real(1) / P.inv2A[a];  // IEEE division in Real, as on the device
     P.eta[a] = a < h->NP ? (Real)p.eta_rho[a] : Real(0);
     if (P.eta[a] != Real(0)) P.shrink = 1;
+    for (int b = 0; b < 4; ++b) {
+      const double th = a < h->NP && b < h->NP && a != b ? p.tilt[a][b] : 0.0;
+      P.tilt_c[a][b] = (Real)std::cos(th);
+      P.tilt_s[a][b] = (Real)std::sin(th);
+      if (th != 0.0) P.tilted = 1;
+    }
     for (int i = 0; i < 2; ++i) P.ceq[a][i] = (Real)p.ceq[a][i];
     P.S[a] = (Real)p.S[a];
   }
@@ -243,6 +256,12 @@ gpflbm_status check_params(const gpflbm_params* p, int NP, std::string* why) {
       *why = "eta_rho must be finite";
       return GPFLBM_ERR_ARG;
     }
+  for (int a = 0; a < NP; ++a)
+    for (int b = 0; b < NP; ++b)
+      if (a != b && (!std::isfinite(p->tilt[a][b]) || p->tilt[a][b] != p->tilt[b][a])) {
+        *why = "tilt must be finite and symmetric";
+        return GPFLBM_ERR_ARG;
+      }
   if (!(p->D_liq >= 0.0) || !(p->q_floor >= 0.0)) {
     *why = "need D_liq >= 0 and q_floor >= 0";
     return GPFLBM_ERR_ARG;
@@ -298,7 +317,7 @@ gpflbm_status capture(gpflbm_t h, int from, int steps, cudaGraphExec_t* out) {
   int b = from;
   cudaError_t le = cudaSuccess;
   for (int s = 0; s < steps; ++s) {
-    le = h->ops->step(dev_params(h), step_io(h, b), h->capture);
+    le = stepper(h)->step(dev_params(h), step_io(h, b), h->capture);
     if (le != cudaSuccess) break;
     b = 1 - b;
   }
@@ -360,6 +379,7 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
   h->D = D;
   h->Q = ops->Q;
   h->ops = ops;
+  h->ops_tilt = find_ops(D, grid->lattice, grid->precision, n_phases, n_components, true);
   h->cells = (long long)grid->nx * grid->ny * grid->nz;
   h->px = (int)round_up(grid->nx, 8);
   h->plane = (long long)round_up((size_t)h->px * grid->ny * grid->nz, 64);
@@ -386,6 +406,7 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
     h->owns_ws = true;
   }
   cudaError_t e = h->ops->configure();
+  if (e == cudaSuccess) e = h->ops_tilt->configure();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "gpflbm_create: %s\n", cudaGetErrorString(e));
@@ -486,7 +507,7 @@ gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream) {
       e = cudaGraphLaunch(h->pair_graph[h->cur], s);
       left -= 2;
     } else {
-      e = h->ops->step(dev_params(h), step_io(h, h->cur), s);
+      e = stepper(h)->step(dev_params(h), step_io(h, h->cur), s);
       h->cur = 1 - h->cur;
       left -= 1;
     }
@@ -503,9 +524,9 @@ gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const gpflbm::StepIO io = step_io(h, h->cur);
   cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(events[0]), s);
-  if (e == cudaSuccess) e = h->ops->step_pf(dev_params(h), io, s);
+  if (e == cudaSuccess) e = stepper(h)->step_pf(dev_params(h), io, s);
   if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(events[1]), s);
-  if (e == cudaSuccess) e = h->ops->step_transport(dev_params(h), io, s);
+  if (e == cudaSuccess) e = stepper(h)->step_transport(dev_params(h), io, s);
   if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(events[2]), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step_timed");
   h->cur = 1 - h->cur;
@@ -768,9 +789,10 @@ AdjLayout adj_layout(gpflbm_t h, int H, int K) {
 gpflbm_status adj_check(gpflbm_t h, int H, int K) {
   const int prec = h->grid.precision;
   if (h->D != 2 || h->NP != 2 || h->NC != 1 || (prec != GPFLBM_FP64 && prec != GPFLBM_FP32) ||
-      h->pf.shrink || h->pd.shrink)
+      h->pf.shrink || h->pd.shrink || h->pf.tilted)
     return fail(h, GPFLBM_ERR_UNSUPPORTED,
-                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage");
+                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage "
+                "or tilted crystal axes");
   if (H < 1 || K < 1) return fail(h, GPFLBM_ERR_ARG, "adjoint: need horizon >= 1 and ckpt_every >= 1");
   return GPFLBM_OK;
 }

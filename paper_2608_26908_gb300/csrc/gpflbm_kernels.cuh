@@ -145,6 +145,9 @@ struct DevParams {
   // appended last: earlier fields keep their parameter-bank offsets
   Real eta[4];         // shrinkage (rho_a - rho_0) / rho_0 per phase
   int shrink;          // 1 if any eta of the problem's phases is nonzero
+  Real tilt_c[4][4];   // cos and sin of the turn of a pair's crystal axes about z
+  Real tilt_s[4][4];
+  int tilted;          // 1 if any pair of the problem's phases has a nonzero turn
 };
 
 template <class Real>
@@ -287,6 +290,46 @@ __device__ __forceinline__ void dAdq_vec(const Real* q, Real delta, Real q_floor
     const Real qt = q[t];
     const Real dac = Real(16) * delta * (qt * qt * qt - qt * s4 * inv2) * inv2 * inv2;
     out[t] = Real(2) * ac * (ac * qt + s2 * dac);
+  }
+}
+
+// dA/dq_j of pair (a, b).  With TILT its crystal axes are turned by theta
+// about z: the cubic anisotropy is a function of the crystal-frame
+// components r = (c q_x + s q_y, -s q_x + c q_y, q_z) and, by the chain rule,
+// dA/dq = (c r'_x - s r'_y, s r'_x + c r'_y, r'_z) with r' = dA/dr.
+template <int D, bool TILT, class Real>
+__device__ __forceinline__ Real dAdq_pair(const DevParams<Real>& P, int a, int b, const Real* q, int j) {
+  if constexpr (!TILT) {
+    return dAdq<D>(q, P.delta[a][b], P.q_floor, j);
+  } else {
+    const Real c = P.tilt_c[a][b], s = P.tilt_s[a][b];
+    Real r[D];
+    r[0] = c * q[0] + s * q[1];
+    r[1] = c * q[1] - s * q[0];
+    if constexpr (D == 3) r[2] = q[2];
+    if (j == 2) return dAdq<D>(r, P.delta[a][b], P.q_floor, 2);
+    const Real d0 = dAdq<D>(r, P.delta[a][b], P.q_floor, 0);
+    const Real d1 = dAdq<D>(r, P.delta[a][b], P.q_floor, 1);
+    return j == 0 ? c * d0 - s * d1 : s * d0 + c * d1;
+  }
+}
+
+// Full vector dA/dq of pair (a, b), turned as dAdq_pair.
+template <int D, bool TILT, class Real>
+__device__ __forceinline__ void dAdq_vec_pair(const DevParams<Real>& P, int a, int b, const Real* q,
+                                              Real* out) {
+  if constexpr (!TILT) {
+    dAdq_vec<D>(q, P.delta[a][b], P.q_floor, out);
+  } else {
+    const Real c = P.tilt_c[a][b], s = P.tilt_s[a][b];
+    Real r[D], d[D];
+    r[0] = c * q[0] + s * q[1];
+    r[1] = c * q[1] - s * q[0];
+    if constexpr (D == 3) r[2] = q[2];
+    dAdq_vec<D>(r, P.delta[a][b], P.q_floor, d);
+    out[0] = c * d[0] - s * d[1];
+    out[1] = s * d[0] + c * d[1];
+    if constexpr (D == 3) out[2] = d[2];
   }
 }
 

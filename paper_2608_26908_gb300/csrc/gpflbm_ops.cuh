@@ -57,8 +57,10 @@ struct Ops {
                             double* partial, int blocks, double* out, cudaStream_t s);
 };
 
-// QQ: lattice size (0 = D2Q9 in 2D, D3Q19 in 3D; 27 = D3Q27)
-template <int D, int NP, int NC, class Real, class Store, int QQ = 0>
+// QQ: lattice size (0 = D2Q9 in 2D, D3Q19 in 3D; 27 = D3Q27).
+// TILT: the step kernels turn the pairs' crystal axes (a separate table, so
+// that the axis-aligned kernels are not touched).
+template <int D, int NP, int NC, class Real, class Store, int QQ = 0, bool TILT = false>
 struct Impl {
   static constexpr int Q = QQ ? QQ : (D == 2 ? 9 : 19);
 
@@ -68,16 +70,16 @@ struct Impl {
   static cudaError_t configure() {
     cudaError_t e;
     if constexpr (D == 2) {
-      e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, false>,
+      e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, false, TILT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, true>,
+        e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, true, TILT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
     } else {
-      e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false, Q>,
+      e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false, Q, TILT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q>,
+        e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q, TILT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
     }
     return e;
@@ -90,18 +92,18 @@ struct Impl {
       const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
       if (P.shrink)
-        step2d_kernel<NP, NC, Real, Store, true><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+        step2d_kernel<NP, NC, Real, Store, true, TILT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
       else
-        step2d_kernel<NP, NC, Real, Store, false><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+        step2d_kernel<NP, NC, Real, Store, false, TILT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
     } else {
       const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
                       (P.n[2] + S3::ZS - 1) / S3::ZS);
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
       if (P.shrink)
-        step3d_kernel<NP, NC, Real, Store, true, Q><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, true, Q, TILT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
       else
-        step3d_kernel<NP, NC, Real, Store, false, Q><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, false, Q, TILT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
     }
     return cudaGetLastError();
   }
@@ -175,27 +177,42 @@ struct Impl {
   }
 };
 
-// One function per (dimension, precision) translation unit.
-const Ops* ops_d2_fp64(int NP, int NC);
-const Ops* ops_d2_fp32(int NP, int NC);
-const Ops* ops_d2_f16(int NP, int NC);
-const Ops* ops_d2_bf16(int NP, int NC);
-const Ops* ops_d3_fp64(int NP, int NC);
-const Ops* ops_d3_fp32(int NP, int NC);
-const Ops* ops_d3_f16(int NP, int NC);
-const Ops* ops_d3_bf16(int NP, int NC);
-const Ops* ops_d3q27_fp64(int NP, int NC);  // D3Q27 (FP64 and FP32 arithmetic and storage)
-const Ops* ops_d3q27_fp32(int NP, int NC);
+// One function per (dimension, precision) translation unit.  Each instance
+// file compiles twice: with GPFLBM_TILT = 0 the axis-aligned kernels, with
+// GPFLBM_TILT = 1 the turned-axes ones, whose table function is NAME_tilt.
+#define GPFLBM_DECLARE_OPS(NAME)  \
+  const Ops* NAME(int NP, int NC); \
+  const Ops* NAME##_tilt(int NP, int NC);
+GPFLBM_DECLARE_OPS(ops_d2_fp64)
+GPFLBM_DECLARE_OPS(ops_d2_fp32)
+GPFLBM_DECLARE_OPS(ops_d2_f16)
+GPFLBM_DECLARE_OPS(ops_d2_bf16)
+GPFLBM_DECLARE_OPS(ops_d3_fp64)
+GPFLBM_DECLARE_OPS(ops_d3_fp32)
+GPFLBM_DECLARE_OPS(ops_d3_f16)
+GPFLBM_DECLARE_OPS(ops_d3_bf16)
+GPFLBM_DECLARE_OPS(ops_d3q27_fp64)  // D3Q27 (FP64 and FP32 arithmetic and storage)
+GPFLBM_DECLARE_OPS(ops_d3q27_fp32)
 
-#define GPFLBM_DEFINE_OPS_Q(NAME, DIM, QQ, REAL, STORE)                        \
-  const Ops* NAME(int NP, int NC) {                                            \
-    if (NP == 2 && NC == 1) return Impl<DIM, 2, 1, REAL, STORE, QQ>::table();  \
-    if (NP == 2 && NC == 2) return Impl<DIM, 2, 2, REAL, STORE, QQ>::table();  \
-    if (NP == 3 && NC == 1) return Impl<DIM, 3, 1, REAL, STORE, QQ>::table();  \
-    if (NP == 3 && NC == 2) return Impl<DIM, 3, 2, REAL, STORE, QQ>::table();  \
-    if (NP == 4 && NC == 1) return Impl<DIM, 4, 1, REAL, STORE, QQ>::table();  \
-    if (NP == 4 && NC == 2) return Impl<DIM, 4, 2, REAL, STORE, QQ>::table();  \
-    return nullptr;                                                            \
+#ifndef GPFLBM_TILT
+#define GPFLBM_TILT 0
+#endif
+#if GPFLBM_TILT
+#define GPFLBM_OPS_NAME(NAME) NAME##_tilt
+#else
+#define GPFLBM_OPS_NAME(NAME) NAME
+#endif
+
+#define GPFLBM_IMPL(DIM, NP_, NC_, QQ, REAL, STORE) Impl<DIM, NP_, NC_, REAL, STORE, QQ, (GPFLBM_TILT != 0)>
+#define GPFLBM_DEFINE_OPS_Q(NAME, DIM, QQ, REAL, STORE)                               \
+  const Ops* GPFLBM_OPS_NAME(NAME)(int NP, int NC) {                                  \
+    if (NP == 2 && NC == 1) return GPFLBM_IMPL(DIM, 2, 1, QQ, REAL, STORE)::table();  \
+    if (NP == 2 && NC == 2) return GPFLBM_IMPL(DIM, 2, 2, QQ, REAL, STORE)::table();  \
+    if (NP == 3 && NC == 1) return GPFLBM_IMPL(DIM, 3, 1, QQ, REAL, STORE)::table();  \
+    if (NP == 3 && NC == 2) return GPFLBM_IMPL(DIM, 3, 2, QQ, REAL, STORE)::table();  \
+    if (NP == 4 && NC == 1) return GPFLBM_IMPL(DIM, 4, 1, QQ, REAL, STORE)::table();  \
+    if (NP == 4 && NC == 2) return GPFLBM_IMPL(DIM, 4, 2, QQ, REAL, STORE)::table();  \
+    return nullptr;                                                                   \
   }
 #define GPFLBM_DEFINE_OPS(NAME, DIM, REAL, STORE) GPFLBM_DEFINE_OPS_Q(NAME, DIM, 0, REAL, STORE)
 

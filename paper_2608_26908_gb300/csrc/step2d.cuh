@@ -73,9 +73,10 @@ struct Step2DIO {
   double* clock_out;
 };
 
+// TILT: the pairs' crystal axes are turned about z (dAdq_pair).
 // SHRINK: the shrinkage force needs phi^{n+1}, so the collision moves after
 // the phase-field update (the raw populations wait in the collision buffer).
-template <int NP, int NC, class Real, class Store, bool SHRINK = false>
+template <int NP, int NC, class Real, class Store, bool SHRINK = false, bool TILT = false>
 __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>::MIN_CTAS)
     step2d_kernel(const DevParams<Real> P, const Step2DIO io) {
   using S = Step2D<NP, NC, Real, Store>;
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
             Real q[2];
             q[d] = pf[a] * gn[b] - pf[b] * gn[a];
             q[1 - d] = pf[a] * gt[b] - pf[b] * gt[a];
-            const Real v = dAdq<2>(q, P.delta[a][b], P.q_floor, d);
+            const Real v = dAdq_pair<2, TILT>(P, a, b, q, d);
             fl[a] -= gab * pf[b] * v;  // dA/dq(q_ba) = -dA/dq(q_ab)
             fl[b] += gab * pf[a] * v;
           }
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
           Real q[2], v[2];
           q[0] = ph[a] * gc[b][0] - ph[b] * gc[a][0];
           q[1] = ph[a] * gc[b][1] - ph[b] * gc[a][1];
-          dAdq_vec<2>(q, P.delta[a][b], P.q_floor, v);
+          dAdq_vec_pair<2, TILT>(P, a, b, q, v);
           dadphi[a] += gab * (v[0] * gc[b][0] + v[1] * gc[b][1]);
           dadphi[b] -= gab * (v[0] * gc[a][0] + v[1] * gc[a][1]);
         }

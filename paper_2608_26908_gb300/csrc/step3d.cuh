@@ -73,9 +73,10 @@ struct Step3DIO {
   double* clock_out;
 };
 
+// TILT: the pairs' crystal axes are turned about z (dAdq_pair).
 // SHRINK: the shrinkage force needs phi^{n+1}, so the collision of a plane
 // moves after its phase-field update (its populations are read again then).
-template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19>
+template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19, bool TILT = false>
 __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
   using S = Step3D<NP, NC, Real, Store, QQ>;
@@ -210,7 +211,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         Real q[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) q[t] = pf[a] * g3[b][t] - pf[b] * g3[a][t];
-        const Real v = dAdq<3>(q, P.delta[a][b], P.q_floor, d);
+        const Real v = dAdq_pair<3, TILT>(P, a, b, q, d);
         fl[a] -= gab * pf[b] * v;
         fl[b] += gab * pf[a] * v;
       }
@@ -409,7 +410,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
             Real q[3], v[3];
 #pragma unroll
             for (int t = 0; t < 3; ++t) q[t] = ph[a] * gc[b][t] - ph[b] * gc[a][t];
-            dAdq_vec<3>(q, P.delta[a][b], P.q_floor, v);
+            dAdq_vec_pair<3, TILT>(P, a, b, q, v);
             dadphi[a] += gab * (v[0] * gc[b][0] + v[1] * gc[b][1] + v[2] * gc[b][2]);
             dadphi[b] -= gab * (v[0] * gc[a][0] + v[1] * gc[a][1] + v[2] * gc[a][2]);
           }

@@ -40,6 +40,7 @@ class Params(ctypes.Structure):
         ("G", ctypes.c_double), ("V", ctypes.c_double), ("v0", ctypes.c_double),
         ("q_floor", ctypes.c_double),
         ("eta_rho", ctypes.c_double * 4),
+        ("tilt", (ctypes.c_double * 4) * 4),
     ]
 
 
@@ -133,6 +134,8 @@ def params_struct(sc):
         p.c_ref[i] = pr["c_ref"][i]
     for a in range(4):
         p.eta_rho[a] = pr.get("eta_rho", [0.0] * 4)[a]
+        for b in range(4):
+            p.tilt[a][b] = pr.get("tilt", [[0.0] * 4] * 4)[a][b]
     return p
 
 

@@ -102,6 +102,13 @@ def test_create_rejects_bad_arguments_without_a_device(L):
     p.A[1] = 0.0
     assert L.gpflbm_create(ctypes.byref(g), 2, 1, ctypes.byref(p), None, 0,
                            ctypes.byref(h)) == gpflbm.ERR_ARG
+    p = gpflbm.params_struct(sc)
+    p.tilt[0][1] = 0.3  # tilt must be symmetric
+    assert L.gpflbm_create(ctypes.byref(g), 2, 1, ctypes.byref(p), None, 0,
+                           ctypes.byref(h)) == gpflbm.ERR_ARG
+    p.tilt[1][0] = float("nan")
+    assert L.gpflbm_create(ctypes.byref(g), 2, 1, ctypes.byref(p), None, 0,
+                           ctypes.byref(h)) == gpflbm.ERR_ARG
     assert L.gpflbm_create(ctypes.byref(g), 2, 1, ctypes.byref(gpflbm.params_struct(sc)), None, 0,
                            None) == gpflbm.ERR_ARG
     # calls on a null handle fail cleanly
