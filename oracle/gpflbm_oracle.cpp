@@ -781,6 +781,9 @@ int check(const OracleProblem* p) {
   if ((p->dim == 2 && p->q != 9) || (p->dim == 3 && p->q != 19 && p->q != 27)) return -1;
   if (p->n_phases < 2 || p->n_phases > 4 || p->n_solutes < 1 || p->n_solutes > 2) return -1;
   if (p->nx < 3 || p->ny < 3 || (p->dim == 3 && p->nz < 3)) return -1;
+  for (int a = 0; a < p->n_phases; ++a)
+    for (int b = 0; b < p->n_phases; ++b)
+      if (p->tilt[a][b] != p->tilt[b][a]) return -1;
   return 0;
 }
 
@@ -844,6 +847,37 @@ int oracle_run(const OracleProblem* p, long n0, int n_steps, double* phi, double
   std::memcpy(phi, s.phi.data(), sizeof(double) * s.phi.size());
   std::memcpy(mu, s.mu.data(), sizeof(double) * s.mu.size());
   std::memcpy(f, s.f.data(), sizeof(double) * s.f.size());
+  return 0;
+}
+
+// Moving frame of the directional-solidification case (the window follows
+// the growth front).  Moves the state `rows` cells down the vertical axis
+// (y in 2D, z in 3D): layer v takes the values of layer v + rows and the top
+// `rows` layers repeat the old top layer (a zero-gradient far field).  The
+// caller lowers v0 by `rows`, so that the frozen temperature stays with the
+// material.  Needs 0 <= rows < n_vertical and no obstacle rows on that axis.
+int oracle_shift_frame(const OracleProblem* p, int rows, double* phi, double* mu, double* f) {
+  if (check(p)) return -1;
+  Grid g(p);
+  const int ax = p->dim == 3 ? 2 : 1;
+  const int nv = g.n[ax];
+  if (rows < 0 || rows >= nv || p->wall_rows[ax] > 0) return -1;
+  auto shift = [&](double* a, int planes) {
+    for (int pl = 0; pl < planes; ++pl) {
+      double* b = a + (long)pl * g.cells;
+      const std::vector<double> old(b, b + g.cells);
+      for (long i = 0; i < g.cells; ++i) {
+        int c[3];
+        g.coords(i, c);
+        int from[3] = {c[0], c[1], c[2]};
+        from[ax] = std::min(c[ax] + rows, nv - 1);
+        b[i] = old[g.idx(from[0], from[1], from[2])];
+      }
+    }
+  };
+  shift(phi, p->n_phases);
+  shift(mu, p->n_solutes);
+  shift(f, p->q);
   return 0;
 }
 

@@ -75,6 +75,7 @@ def lib():
         P = ctypes.POINTER(OracleProblem)
         O = ctypes.POINTER(OracleObjective)
         L.oracle_run.argtypes = [P, ctypes.c_long, ctypes.c_int, dp, dp, dp]
+        L.oracle_shift_frame.argtypes = [P, ctypes.c_int, dp, dp, dp]
         L.oracle_derived.argtypes = [P, ctypes.c_long, dp, dp, dp, dp, dp, dp]
         L.oracle_invariants.argtypes = [P, dp, dp, dp, dp]
         L.oracle_objective.argtypes = [P, O, ctypes.c_long, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
@@ -170,6 +171,19 @@ def run(sc, phi, mu, f, n_steps, n0=0):
     rc = lib().oracle_run(ctypes.byref(p), int(n0), int(n_steps), _dp(phi), _dp(mu), _dp(f))
     if rc != 0:
         raise ValueError("oracle_run rejected the problem")
+    return phi, mu, f
+
+
+def shift_frame(sc, phi, mu, f, rows):
+    """Moving frame: the state moved `rows` cells down the vertical axis, the
+    top layers repeating the old top layer (copies; the caller lowers v0 by
+    `rows`)."""
+    p = problem(sc)
+    phi = np.array(phi, dtype=np.float64)
+    mu = np.array(mu, dtype=np.float64)
+    f = np.array(f, dtype=np.float64)
+    if lib().oracle_shift_frame(ctypes.byref(p), int(rows), _dp(phi), _dp(mu), _dp(f)) != 0:
+        raise ValueError("oracle_shift_frame rejected the problem or the shift")
     return phi, mu, f
 
 

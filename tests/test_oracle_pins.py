@@ -733,6 +733,78 @@ def test_frozen_temperature_gradient_sets_the_front():
     assert b > a + 0.04
 
 
+# ----------------------------------------------------------------- moving frame
+def _frame_pair(dim, s, n1, n2, lower_v0=True):
+    """Window A (nv layers) steps n1 times, moves its frame s layers up the
+    material and steps n2 times more; B covers A's first and last windows at
+    once (nv + s layers) and steps n1 + n2 times.  A starts from B's seeded
+    initial state cut to its first window.  Returns A's final fields and B's,
+    the latter cut to A's final window (B layers s .. s + nv)."""
+    nv = 84
+    if dim == 2:
+        big = inputs.scenario("eutectic2d", nx=40, ny=nv + s)
+    else:
+        big = inputs.scenario("eutectic3d", nx=12, ny=10, nz=nv + s)
+        big["init"]["height"] = 32
+        big["init"]["noise"] = 1e-3  # seeded, so that the window ends see different values
+    big["params"]["G"] = 4e-3  # a strong gradient: a frame without its T shift is visibly off
+    phi_b, mu_b = inputs.initial_state(big)
+    nx, ny, _ = inputs.dims(big)
+    layer = nx * (ny if dim == 3 else 1)
+    NP, NC = big["n_phases"], big["n_solutes"]
+    small = copy.deepcopy(big)
+    small["grid"]["nz" if dim == 3 else "ny"] = nv
+    cut = lambda a, k: a.reshape(k, -1)[:, :nv * layer].reshape(-1)
+    phi_a, mu_a = cut(phi_b, NP), cut(mu_b, NC)
+    f_a, f_b = oracle.rest_populations(small), oracle.rest_populations(big)
+    phi_a, mu_a, f_a = oracle.run(small, phi_a, mu_a, f_a, n1)
+    phi_a, mu_a, f_a = oracle.shift_frame(small, phi_a, mu_a, f_a, s)
+    if lower_v0:
+        small["params"]["v0"] -= s
+    phi_a, mu_a, f_a = oracle.run(small, phi_a, mu_a, f_a, n2, n0=n1)
+    phi_b, mu_b, f_b = oracle.run(big, phi_b, mu_b, f_b, n1 + n2)
+    win = lambda a, k: a.reshape(k, -1)[:, s * layer:(s + nv) * layer]
+    Q = 19 if dim == 3 else 9
+    A = [x.reshape(k, -1) for x, k in ((phi_a, NP), (mu_a, NC), (f_a, Q))]
+    B = [win(phi_b, NP), win(mu_b, NC), win(f_b, Q)]
+    return A, B, layer
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_moving_frame_matches_the_taller_domain_away_from_its_ends(dim):
+    """Moving the window and lowering v0 by the same s changes nothing where
+    neither window's ends can be felt: a step reaches at most 2 cells (phi^{n+1}
+    of the neighbours enters mu^{n+1}), so layers more than 2 (n1 + n2) + 1
+    below A's first top and 2 n2 + 1 above its last bottom agree with the
+    taller run to rounding (T = T_E - u + G (v - (v0 - s) - V t) is the same
+    number up to the order of its sums)."""
+    s, n1, n2 = 10, 6, 6
+    A, B, layer = _frame_pair(dim, s, n1, n2)
+    lo = 2 * n2 + 1
+    hi = 84 - s - 2 * (n1 + n2) - 1
+    assert hi - lo >= 20
+    band = slice(lo * layer, hi * layer)
+    for a, b in zip(A, B):
+        np.testing.assert_allclose(a[:, band], b[:, band], rtol=0, atol=1e-12)
+    # the ends of the window do differ (the band is not trivially everything)
+    assert max(np.abs(a - b).max() for a, b in zip(A, B)) > 1e-9
+    # without lowering v0 the frozen temperature slides with the window
+    A2, B2, _ = _frame_pair(dim, s, n1, n2, lower_v0=False)
+    assert np.abs(A2[0][:, band] - B2[0][:, band]).max() > 1e-7
+
+
+def test_moving_frame_rejects_bad_shifts():
+    sc = inputs.scenario("eutectic2d", nx=8, ny=12)
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    for rows in (-1, 12):
+        with pytest.raises(ValueError):
+            oracle.shift_frame(sc, phi, mu, f, rows)
+    sc["grid"]["wall_rows"] = [0, 2, 0]
+    with pytest.raises(ValueError):
+        oracle.shift_frame(sc, phi, mu, f, 1)
+
+
 # ----------------------------------------------------------------- shrinkage
 @pytest.mark.parametrize("dim", [2, 3])
 def test_shrinkage_momentum_balances_the_solidified_volume(dim):
