@@ -156,6 +156,20 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
  * replayed from a CUDA graph captured on first use. */
 gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream);
 
+/* Moving frame of the directional-solidification case (Sec. "Case 2:
+ * Directional Solidification": the window follows the growth front).  Moves
+ * the state `rows` cells down the vertical axis (y in 2D, z in 3D, the axis
+ * of the temperature gradient G): layer v takes the values of layer
+ * v + rows (phi, mu and the stored populations, copied exactly), the top
+ * `rows` layers repeat the old top layer (a zero-gradient far field), and
+ * params.v0 is lowered by `rows`, so that the frozen temperature
+ * T = T_E - undercool + G (v - v0 - V t) stays with the material.  The step
+ * counter is unchanged.  Asynchronous on `stream`, ordered after earlier
+ * steps on it.  GPFLBM_ERR_ARG unless 0 <= rows < the vertical size;
+ * GPFLBM_ERR_UNSUPPORTED with obstacle rows on the vertical axis
+ * (wall_rows != 0 there); GPFLBM_ERR_STATE before set_state. */
+gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream);
+
 /* One step launched directly (not from a graph) that records three caller
  * CUDA events (cudaEvent_t) on `stream`: events[0] before the step kernel
  * (one fused launch for all three updates), events[1] after it, and

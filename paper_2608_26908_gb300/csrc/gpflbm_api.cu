@@ -517,6 +517,57 @@ gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream) {
   return GPFLBM_OK;
 }
 
+gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  const int ax = h->D == 3 ? 2 : 1;
+  const int nv = ax == 2 ? h->grid.nz : h->grid.ny;
+  if (rows < 0 || rows >= nv) return fail(h, GPFLBM_ERR_ARG, "shift_frame: need 0 <= rows < n_vertical");
+  if (h->grid.wall_rows[ax] != 0)
+    return fail(h, GPFLBM_ERR_UNSUPPORTED, "shift_frame: obstacle rows on the vertical axis");
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "shift_frame: no state loaded");
+  if (rows == 0) return GPFLBM_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long layer = ax == 2 ? (long long)h->px * h->grid.ny : h->px;
+  const long long n = layer * nv;
+  const int threads = 256;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  const int from = h->cur, to = 1 - h->cur;
+  auto move = [&](size_t src_off, size_t dst_off, int planes, size_t word) {
+    const void* a = at(h, src_off);
+    void* b = at(h, dst_off);
+    switch (word) {
+      case 2:
+        gpflbm::shift_frame_kernel<unsigned short><<<blocks, threads, 0, s>>>(
+            static_cast<const unsigned short*>(a), static_cast<unsigned short*>(b), planes, h->plane, n,
+            layer, nv, rows);
+        break;
+      case 4:
+        gpflbm::shift_frame_kernel<unsigned int><<<blocks, threads, 0, s>>>(
+            static_cast<const unsigned int*>(a), static_cast<unsigned int*>(b), planes, h->plane, n, layer,
+            nv, rows);
+        break;
+      default:
+        gpflbm::shift_frame_kernel<unsigned long long><<<blocks, threads, 0, s>>>(
+            static_cast<const unsigned long long*>(a), static_cast<unsigned long long*>(b), planes,
+            h->plane, n, layer, nv, rows);
+    }
+    return cudaGetLastError();
+  };
+  cudaError_t e = move(h->lay.phi[from], h->lay.phi[to], h->ops->stored_phi_planes, h->ops->real_size);
+  if (e == cudaSuccess) e = move(h->lay.mu[from], h->lay.mu[to], h->NC, h->ops->real_size);
+  if (e == cudaSuccess) e = move(h->lay.f[from], h->lay.f[to], h->Q, h->ops->store_size);
+  if (e == cudaSuccess) {
+    double* clk = reinterpret_cast<double*>(at(h, h->lay.clock));
+    e = cudaMemcpyAsync(clk + to, clk + from, sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "shift_frame");
+  h->cur = to;
+  h->params.v0 -= rows;
+  set_device_params(h);
+  drop_graphs(h);  // v0 is baked into captured launches
+  return GPFLBM_OK;
+}
+
 gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream) {
   if (!h || !events || !events[0] || !events[1] || !events[2])
     return fail(h, GPFLBM_ERR_ARG, "step_timed: three events are required");

@@ -406,6 +406,20 @@ __device__ __forceinline__ long long cell_index(const DevParams<Real>& P, int x,
 }
 
 // ------------------------------------------------------------------ state I/O
+// Moving frame: layer v of every plane of dst takes layer
+// min(v + rows, nv - 1) of src.  W is a word of the stored type's size; the
+// layout is the padded one (`layer` words per vertical layer, `n` words per
+// plane in use, planes `plane` words apart).  dst and src do not overlap.
+template <class W>
+__global__ void shift_frame_kernel(const W* __restrict__ src, W* __restrict__ dst, int planes,
+                                   long long plane, long long n, long long layer, int nv, int rows) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int v = (int)(i / layer);
+  const long long j = i + (long long)(min(v + rows, nv - 1) - v) * layer;
+  for (int p = 0; p < planes; ++p) dst[p * plane + i] = src[p * plane + j];
+}
+
 // phi from N exchange planes (liquid first) to the stored planes.
 // Offset of logical cell x (x fastest, no padding) in the padded layout.
 __device__ __forceinline__ long long padded(long long x, int nx, int px) {

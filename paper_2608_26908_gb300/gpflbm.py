@@ -4,6 +4,7 @@ Argument marshalling only: every step of the method runs in the CUDA
 library.  PyTorch provides the device workspace and the current stream.  If
 the library has not been built, loading it raises -- there is no CPU path.
 """
+import copy
 import ctypes
 import os
 
@@ -83,6 +84,7 @@ def lib():
         L.gpflbm_set_params.argtypes = [vp, ctypes.POINTER(Params)]
         L.gpflbm_set_state.argtypes = [vp, vp, vp, vp, i, ll, vp]
         L.gpflbm_step.argtypes = [vp, i, vp]
+        L.gpflbm_shift_frame.argtypes = [vp, i, vp]
         L.gpflbm_step_timed.argtypes = [vp, ctypes.POINTER(vp), vp]
         L.gpflbm_get_fields.argtypes = [vp, u, ctypes.POINTER(vp), i, vp]
         L.gpflbm_get_deviations.argtypes = [vp, vp, i, vp]
@@ -208,6 +210,14 @@ class Sim:
             return ctypes.c_void_p(a.data_ptr()), a.is_cuda, a
         a = np.ascontiguousarray(a, dtype=self.dtype)
         return ctypes.c_void_p(a.ctypes.data), False, a
+
+    def shift_frame(self, rows):
+        """Moving frame: the state moves `rows` cells down the vertical axis
+        and v0 drops by `rows` (this object's scenario follows)."""
+        self._check(lib().gpflbm_shift_frame(self.h, int(rows), _stream(self.torch)), "shift_frame")
+        self.sc = copy.deepcopy(self.sc)
+        self.sc["params"]["v0"] = self.sc["params"]["v0"] - rows
+        self._params = params_struct(self.sc)
 
     def set_params(self, sc):
         self.sc = sc
