@@ -71,6 +71,7 @@ typedef struct {
   double q_floor;      // |q|^2 at or below which the anisotropy is dropped
   double eta[4];       // shrinkage (rho_a - rho_liq) / rho_liq per phase, Eq. shrinkage
   double tilt[4][4];   // crystal axes of a pair turned by this angle about z (radians)
+  double dceq_dT[4][2];  // slope of the equilibrium composition with temperature
 } OracleProblem;
 
 // Objective for the gradient checks: J = w_frac * mean_x sum_{a>0} h_a(phi)
@@ -249,20 +250,27 @@ R dh_fn(const R* phi, int N, int b, int a) {
   return 2.0 * phi[b] * s;
 }
 
-// Phase composition for the parabolic free energy f_a(c) = A_a |c - ceq_a|^2:
-// c_a(mu) = ceq_a + mu / (2 A_a)  (Eq. conc uses dc_a/dmu = 1/(2 A_a)).
-template <class R>
-R c_phase(const OracleProblem* p, int a, int i, const R* mu) {
-  return p->ceq[a][i] + mu[i] / (2.0 * p->A[a]);
+// Equilibrium composition of phase a at temperature T, linear in T:
+// ceq_a(T) = ceq_a + (dceq_a/dT) (T - T_E).
+double ceq_T(const OracleProblem* p, int a, int i, double T) {
+  return p->ceq[a][i] + p->dceq_dT[a][i] * (T - p->T_E);
 }
 
-// Grand potential of phase a [R2]: psi_a = -|mu|^2/(4 A_a) - mu.ceq_a
+// Phase composition for the parabolic free energy
+// f_a(c, T) = A_a |c - ceq_a(T)|^2:  c_a(mu, T) = ceq_a(T) + mu / (2 A_a)
+// (Eq. conc uses dc_a/dmu = 1/(2 A_a) and (dc_a/dT)_mu = dceq_a/dT).
+template <class R>
+R c_phase(const OracleProblem* p, int a, int i, const R* mu, double T) {
+  return ceq_T(p, a, i, T) + mu[i] / (2.0 * p->A[a]);
+}
+
+// Grand potential of phase a [R2]: psi_a = -|mu|^2/(4 A_a) - mu.ceq_a(T)
 //   + S_a (T - T_E).
 template <class R>
 R psi_fn(const OracleProblem* p, int a, const R* mu, double T) {
   R s = 0.0;
   for (int i = 0; i < p->n_solutes; ++i)
-    s += -mu[i] * mu[i] / (4.0 * p->A[a]) - mu[i] * p->ceq[a][i];
+    s += -mu[i] * mu[i] / (4.0 * p->A[a]) - mu[i] * ceq_T(p, a, i, T);
   return s + p->S[a] * (T - p->T_E);
 }
 
@@ -427,8 +435,9 @@ void macroscopic(const Grid& g, const Lattice& L, const Coeffs<R>& k, const Stat
     R kappa = 2.0 * nu * p->h_drag * (1.0 - phil) * (1.0 - phil) / (p->W0 * p->W0);
     R mu[2];
     for (int i = 0; i < NC; ++i) mu[i] = s.mu[i * cells + x];
-    R drive = p->gbeta_T * (temperature(p, g.vertical(c), t) - p->T_ref);
-    for (int i = 0; i < NC; ++i) drive += k.gbeta_c[i] * (c_phase(p, 0, i, mu) - p->c_ref[i]);
+    const double T = temperature(p, g.vertical(c), t);
+    R drive = p->gbeta_T * (T - p->T_ref);
+    for (int i = 0; i < NC; ++i) drive += k.gbeta_c[i] * (c_phase(p, 0, i, mu, T) - p->c_ref[i]);
     R FB = rho * phil * drive;
     R FS[3] = {R(0.0), R(0.0), R(0.0)};
     if (phi_new) {
@@ -580,10 +589,13 @@ void phase_field_update(const Grid& g, const Coeffs<R>& k, const State<R>& s, do
 // antitrapping [R13] -a_at eps sum_{a>0} [phi_l]_f [c_l - c_a]_f [dphi_a]_f
 // n_a.e_d (weighted by the liquid on the face: it corrects solute trapping
 // at solid-liquid interfaces only), advection of h_l c_l U with U^n [R14], the source
-// -sum_a c_a (h_a^{n+1} - h_a^n), all divided by chi(phi^{n+1}).
+// -sum_a c_a (h_a^{n+1} - h_a^n), and the temperature term of Eq. conc
+// -(T^{n+1} - T^n) sum_a (dc_a/dT)_mu h_a^{n+1}, all divided by
+// chi(phi^{n+1}).  With h at n+1 the discrete solute
+// sum_a h_a c_a(mu, T) changes by exactly minus the flux divergence.
 template <class R>
 void chemical_potential_update(const Grid& g, const State<R>& s, const std::vector<R>& phi_new,
-                               const Macro<R>& m, std::vector<R>& mu_new) {
+                               const Macro<R>& m, double t, std::vector<R>& mu_new) {
   const OracleProblem* p = g.p;
   const int D = p->dim, N = p->n_phases, NC = p->n_solutes;
   const long cells = g.cells;
@@ -616,9 +628,10 @@ void chemical_potential_update(const Grid& g, const State<R>& s, const std::vect
       }
       R hla = h_fn(pa, N, 0), hlb = h_fn(pb, N, 0);
       R ua = m.u[d * cells + x], ub = m.u[d * cells + y];
+      const double Ta = temperature(p, g.vertical(c), t), Tb = temperature(p, g.vertical(cy), t);
       for (int i = 0; i < NC; ++i) {
         R J = -0.5 * (Ma + Mb) * (mub[i] - mua[i]);
-        J += 0.5 * (ua * hla * c_phase(p, 0, i, mua) + ub * hlb * c_phase(p, 0, i, mub));
+        J += 0.5 * (ua * hla * c_phase(p, 0, i, mua, Ta) + ub * hlb * c_phase(p, 0, i, mub, Tb));
         if (p->a_at != 0.0) {
           R at = 0.0;
           for (int a = 1; a < N; ++a) {
@@ -627,8 +640,8 @@ void chemical_potential_update(const Grid& g, const State<R>& s, const std::vect
             R g2 = 0.0;
             for (int j = 0; j < D; ++j) g2 += gr[j] * gr[j];
             if (val(g2) <= 1e-12) continue;
-            R dc = 0.5 * ((c_phase(p, 0, i, mua) - c_phase(p, a, i, mua)) +
-                          (c_phase(p, 0, i, mub) - c_phase(p, a, i, mub)));
+            R dc = 0.5 * ((c_phase(p, 0, i, mua, Ta) - c_phase(p, a, i, mua, Ta)) +
+                          (c_phase(p, 0, i, mub, Tb) - c_phase(p, a, i, mub, Tb)));
             R dphi = 0.5 * ((phi_new[a * cells + x] - s.phi[a * cells + x]) +
                             (phi_new[a * cells + y] - s.phi[a * cells + y]));
             R liq = 0.5 * (s.phi[0 * cells + x] + s.phi[0 * cells + y]);
@@ -666,8 +679,10 @@ void chemical_potential_update(const Grid& g, const State<R>& s, const std::vect
         if (!(p->bc[d] == 1 && c[d] == 0)) lower = flux[((long)d * NC + i) * cells + g.nb(c, dn)];
         div += flux[((long)d * NC + i) * cells + x] - lower;
       }
+      const double T0 = temperature(p, g.vertical(c), t), T1 = temperature(p, g.vertical(c), t + 1.0);
       R src = 0.0;
-      for (int a = 0; a < N; ++a) src += c_phase(p, a, i, mu) * (h_fn(pn, N, a) - h_fn(po, N, a));
+      for (int a = 0; a < N; ++a) src += c_phase(p, a, i, mu, T0) * (h_fn(pn, N, a) - h_fn(po, N, a));
+      for (int a = 0; a < N; ++a) src += (T1 - T0) * p->dceq_dT[a][i] * h_fn(pn, N, a);
       mu_new[i * cells + x] = mu[i] + (-div - src) / chi;
     }
   }
@@ -739,7 +754,7 @@ void step(const Grid& g, const Lattice& L, const Coeffs<R>& k, State<R>& s, long
   Macro<R> m;
   phase_field_update(g, k, s, t, phi_new);
   macroscopic(g, L, k, s, &phi_new, t, m);
-  chemical_potential_update(g, s, phi_new, m, mu_new);
+  chemical_potential_update(g, s, phi_new, m, t, mu_new);
   lattice_boltzmann_update(g, L, s, m, f_new);
   s.phi.swap(phi_new);
   s.mu.swap(mu_new);
@@ -898,9 +913,12 @@ int oracle_derived(const OracleProblem* p, long n, const double* phi, const doub
     double ph[4], mm[2];
     for (int a = 0; a < p->n_phases; ++a) ph[a] = phi[a * g.cells + x];
     for (int i = 0; i < p->n_solutes; ++i) mm[i] = mu[i * g.cells + x];
+    int cx[3];
+    g.coords(x, cx);
+    const double T = temperature(p, g.vertical(cx), (double)n);
     for (int i = 0; i < p->n_solutes; ++i) {
       double cc = 0.0;
-      for (int a = 0; a < p->n_phases; ++a) cc += h_fn(ph, p->n_phases, a) * c_phase(p, a, i, mm);
+      for (int a = 0; a < p->n_phases; ++a) cc += h_fn(ph, p->n_phases, a) * c_phase(p, a, i, mm, T);
       if (c_out) c_out[i * g.cells + x] = cc;
     }
     if (rho_out) rho_out[x] = m.rho[x];
@@ -913,7 +931,7 @@ int oracle_derived(const OracleProblem* p, long n, const double* phi, const doub
 // Global totals in FP64: out[0] = sum_x sum_k f_k, out[1..K-1] = sum_x c_i,
 // out[K] = mean_x sum_{a>0} h_a.  Each cell's value is formed first, then
 // the cells are added sequentially in index order.
-int oracle_invariants(const OracleProblem* p, const double* phi, const double* mu,
+int oracle_invariants(const OracleProblem* p, long n, const double* phi, const double* mu,
                       const double* f, double* out) {
   if (check(p)) return -1;
   Grid g(p);
@@ -926,9 +944,12 @@ int oracle_invariants(const OracleProblem* p, const double* phi, const double* m
     double rho = 0.0;
     for (int q = 0; q < Q; ++q) rho += f[q * g.cells + x];
     mass += rho;
+    int cx[3];
+    g.coords(x, cx);
+    const double T = temperature(p, g.vertical(cx), (double)n);
     for (int i = 0; i < NC; ++i) {
       double cc = 0.0;
-      for (int a = 0; a < N; ++a) cc += h_fn(ph, N, a) * c_phase(p, a, i, mm);
+      for (int a = 0; a < N; ++a) cc += h_fn(ph, N, a) * c_phase(p, a, i, mm, T);
       sol[i] += cc;
     }
     double hs = 0.0;

@@ -53,6 +53,7 @@ class OracleProblem(ctypes.Structure):
         ("q_floor", ctypes.c_double),
         ("eta", ctypes.c_double * 4),
         ("tilt", (ctypes.c_double * 4) * 4),
+        ("dceq_dT", (ctypes.c_double * 2) * 4),
     ]
 
 
@@ -77,7 +78,7 @@ def lib():
         L.oracle_run.argtypes = [P, ctypes.c_long, ctypes.c_int, dp, dp, dp]
         L.oracle_shift_frame.argtypes = [P, ctypes.c_int, dp, dp, dp]
         L.oracle_derived.argtypes = [P, ctypes.c_long, dp, dp, dp, dp, dp, dp]
-        L.oracle_invariants.argtypes = [P, dp, dp, dp, dp]
+        L.oracle_invariants.argtypes = [P, ctypes.c_long, dp, dp, dp, dp]
         L.oracle_objective.argtypes = [P, O, ctypes.c_long, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
         L.oracle_objective_value.argtypes = [P, O, dp, dp]
         L.oracle_lattice.argtypes = [ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]
@@ -133,6 +134,8 @@ def problem(sc):
         p.eta[a] = pr.get("eta_rho", [0.0] * 4)[a]
         for b in range(4):
             p.tilt[a][b] = pr.get("tilt", [[0.0] * 4] * 4)[a][b]
+        for i in range(2):
+            p.dceq_dT[a][i] = pr.get("dceq_dT", [[0.0] * 2] * 4)[a][i]
     return p
 
 
@@ -204,14 +207,15 @@ def derived(sc, phi, mu, f, n=0):
     return c, rho, u
 
 
-def invariants(sc, phi, mu, f):
-    """(mass, [solute_i], solid fraction) as plain sequential FP64 sums."""
+def invariants(sc, phi, mu, f, n=0):
+    """(mass, [solute_i], solid fraction) of the state at time n as plain
+    sequential FP64 sums."""
     p = problem(sc)
     out = np.zeros(2 + p.n_solutes)
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     mu = np.ascontiguousarray(mu, dtype=np.float64)
     f = np.ascontiguousarray(f, dtype=np.float64)
-    assert lib().oracle_invariants(ctypes.byref(p), _dp(phi), _dp(mu), _dp(f), _dp(out)) == 0
+    assert lib().oracle_invariants(ctypes.byref(p), int(n), _dp(phi), _dp(mu), _dp(f), _dp(out)) == 0
     return out[0], out[1:1 + p.n_solutes].copy(), out[1 + p.n_solutes]
 
 

@@ -75,6 +75,7 @@ def _blank_params():
         "q_floor": 1e-12,
         "eta_rho": [0.0] * 4,  # shrinkage (rho_a - rho_l) / rho_l per phase; off unless set
         "tilt": [row[:] for row in z4],  # crystal axes of a pair turned about z (radians)
+        "dceq_dT": [[0.0, 0.0] for _ in range(4)],  # ceq_a(T) = ceq_a + dceq_dT_a (T - T_E)
     }
 
 

@@ -327,10 +327,12 @@ def test_isotropic_two_phase_step_is_textbook_allen_cahn(dim):
     assert A == 1.0
 
 
-def _flat_interface(eps, mu_shift=0.0, steps=2000, delta=0.0):
+def _flat_interface(eps, mu_shift=0.0, steps=2000, delta=0.0, dceq=None):
     n = int(16 * eps)
     sc, _, _ = _liquid_box(n, 3, bc=(1, 0, 0), eps=eps, W0=eps)
     p = sc["params"]
+    if dceq is not None:  # (liquid, solid) slopes of ceq(T)
+        p["dceq_dT"][0][0], p["dceq_dT"][1][0] = dceq
     for a in range(4):
         for b in range(4):
             p["delta"][a][b] = delta if (a != b and (a == 0 or b == 0)) else 0.0
@@ -343,7 +345,12 @@ def _flat_interface(eps, mu_shift=0.0, steps=2000, delta=0.0):
     phi = np.stack([1 - s, s]).reshape(-1)
     dc = p["ceq"][0][0] - p["ceq"][1][0]
     mu_star = 2 * p["A"][0] * dc * p["undercool"]
-    mu = np.full(3 * n, mu_star + mu_shift)
+    if dceq is not None and mu_shift is not None:
+        # psi_l = psi_s with ceq(T): mu* = (S_l - S_s) theta / (ceq_l(T) - ceq_s(T))
+        theta = -p["undercool"]
+        dcT = dc + (dceq[0] - dceq[1]) * theta
+        mu_star = (p["S"][0] - p["S"][1]) * theta / dcT
+    mu = np.full(3 * n, mu_star + (mu_shift or 0.0))
     f = oracle.rest_populations(sc)
     phi1, mu1, f1 = oracle.run(sc, phi, mu, f, steps)
     return sc, x, prof, phi1.reshape(2, 3, n)[1, 1], mu1.reshape(3, n)[1], mu_star, f1
@@ -379,6 +386,47 @@ def test_flat_interface_equilibrium_compositions():
     dc = p["ceq"][0][0] - p["ceq"][1][0]
     assert c[-1] == pytest.approx(p["ceq"][0][0] + dc * u, abs=1e-6)  # 0.555
     assert c[0] == pytest.approx(p["ceq"][1][0] + dc * u, abs=1e-6)   # 0.205
+
+
+def test_flat_interface_with_temperature_dependent_ceq():
+    """ceq_a(T) = ceq_a + k_a (T - T_E), k = (0.5, 0.1), T - T_E = -0.3: the
+    interface is at rest at mu* = (S_l - S_s) theta / (ceq_l(T) - ceq_s(T))
+    (0.320, not the 0.210 of k = 0), with c_l = ceq_l(T) + mu*/(2A) and
+    c_s = ceq_s(T) + mu*/(2A) on either side; started at the k = 0 value of
+    mu* the solid grows."""
+    k = (0.5, 0.1)
+    sc, x, prof, s, mu, mu_star, f = _flat_interface(4.0, steps=400, dceq=k)
+    assert mu_star == pytest.approx(2 * 0.35 ** 2 * 0.3 / 0.23, rel=1e-12)
+    assert abs(_crossing(x, s) - _crossing(x, prof)) < 0.03
+    p = sc["params"]
+    c, _, _ = oracle.derived(sc, np.stack([1 - np.tile(s, 3), np.tile(s, 3)]).reshape(-1),
+                             np.tile(mu, 3), f)
+    c = c.reshape(3, -1)[1]
+    theta = -p["undercool"]
+    assert c[-1] == pytest.approx(0.45 + k[0] * theta + mu_star / 2, abs=1e-6)  # 0.4598
+    assert c[0] == pytest.approx(0.10 + k[1] * theta + mu_star / 2, abs=1e-6)   # 0.2298
+    _, x, prof, s0, _, _, _ = _flat_interface(4.0, mu_shift=None, steps=200, dceq=k)
+    assert _crossing(x, s0) > _crossing(x, prof) + 0.05
+
+
+def test_uniform_melt_keeps_its_composition_as_the_temperature_falls():
+    """The temperature term of Eq. conc: a uniform melt at rest under
+    T = T_E + G (v - v0 - V t) with dceq_l/dT = k keeps c = ceq_l(T) + mu/(2A)
+    fixed in every cell, so mu rises by 2 A k G V per step (exactly linear);
+    the fields at time 0 and at time 50 give the same c."""
+    for dim in (2, 3):
+        sc, phi, mu = _liquid_box(5, 7, 4 if dim == 3 else 1, bc=(0, 1, 1), G=4e-3, V=1e-2, v0=3.0)
+        p = sc["params"]
+        p["dceq_dT"][0][0] = 0.5
+        mu = mu + 0.02
+        f = oracle.rest_populations(sc)
+        phi1, mu1, f1 = oracle.run(sc, phi, mu, f, 50)
+        rate = 2 * p["A"][0] * 0.5 * 4e-3 * 1e-2
+        np.testing.assert_allclose(mu1, 0.02 + 50 * rate, rtol=0, atol=1e-13)
+        c0, _, _ = oracle.derived(sc, phi, mu, f, 0)
+        c1, _, _ = oracle.derived(sc, phi1, mu1, f1, 50)
+        np.testing.assert_allclose(c1, c0, rtol=0, atol=1e-13)
+        assert np.ptp(c0) > 0.005  # c varies with height, mu does not
 
 
 def test_interface_moves_with_the_sign_of_the_driving_force():
@@ -566,11 +614,35 @@ def test_mass_and_solute_are_conserved(case):
     f = oracle.rest_populations(sc)
     m0, s0, _ = oracle.invariants(sc, phi, mu, f)
     phi1, mu1, f1 = oracle.run(sc, phi, mu, f, 40)
-    m1, s1, _ = oracle.invariants(sc, phi1, mu1, f1)
+    m1, s1, _ = oracle.invariants(sc, phi1, mu1, f1, 40)
     _, _, u = oracle.derived(sc, phi1, mu1, f1, 40)
     assert np.abs(u).max() > 1e-6  # there is flow
     assert abs(m1 - m0) / m0 < 1e-12
     np.testing.assert_allclose(s1, s0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("case", ["eutectic2d", "eutectic3d"])
+def test_solute_is_conserved_with_temperature_dependent_ceq(case):
+    """Different slopes dceq_a/dT per phase and solute under a fast-falling
+    temperature: the solute sum_a h_a c_a(mu, T) at T^n is conserved by the
+    flux form with the temperature term at h^{n+1}."""
+    sizes = {"eutectic2d": dict(nx=48, ny=40), "eutectic3d": dict(nx=16, ny=14, nz=20)}
+    sc = inputs.scenario(case, **sizes[case])
+    sc["init"]["height"] = 12 if case == "eutectic2d" else 8
+    pr = sc["params"]
+    pr["gbeta_c"] = [3e-3, 2e-3]
+    pr["G"], pr["V"] = 4e-3, 2e-2
+    pr["dceq_dT"] = [[0.4, -0.2], [0.1, 0.3], [-0.3, 0.05], [0.2, 0.2]]
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    _, s0, _ = oracle.invariants(sc, phi, mu, f, 0)
+    phi1, mu1, f1 = oracle.run(sc, phi, mu, f, 40)
+    _, s1, _ = oracle.invariants(sc, phi1, mu1, f1, 40)
+    np.testing.assert_allclose(s1, s0, rtol=1e-12)
+    # the solute at time 40 counted with the temperature of time 0 is not
+    # the same number: the temperature term did work
+    _, s1_stale, _ = oracle.invariants(sc, phi1, mu1, f1, 0)
+    assert np.abs(s1_stale - s0).max() > 1e-6 * np.abs(s0).max()
 
 
 # ----------------------------------------------------------------- derivatives
