@@ -71,6 +71,8 @@ def parse():
                     help="shrinkage density ratio (rho_solid - rho_liquid) / rho_liquid of every solid phase")
     ap.add_argument("--tilt", type=float, default=0.0,
                     help="turn of every solid-liquid pair's crystal axes about z, radians")
+    ap.add_argument("--dceq-dT", type=float, default=0.0,
+                    help="slope of every phase's equilibrium compositions with temperature")
     return ap.parse_args()
 
 
@@ -83,14 +85,17 @@ def workload(args):
         NP = sc["n_phases"]
         sc["params"]["tilt"] = [[args.tilt if a < NP and b < NP and (a == 0) != (b == 0) else 0.0
                                  for b in range(4)] for a in range(4)]
+    if args.dceq_dT:
+        sc["params"]["dceq_dT"] = [[args.dceq_dT] * 2 for _ in range(4)]
     nx, ny, nz = inputs.dims(sc)
     if args.lattice and nz > 1:
         sc["grid"]["lattice"] = args.lattice
-    desc = "%s %s D%dQ%d N=%d K-1=%d %s%s%s" % (
+    desc = "%s %s D%dQ%d N=%d K-1=%d %s%s%s%s" % (
         args.workload, "x".join(str(n) for n in (nx, ny, nz) if n > 1),
         3 if nz > 1 else 2, lattice_q(sc), sc["n_phases"], sc["n_solutes"], sc["precision"],
         " shrinkage eta=%g" % args.eta if args.eta else "",
-        " tilt=%g" % args.tilt if args.tilt else "")
+        " tilt=%g" % args.tilt if args.tilt else "",
+        " dceq/dT=%g" % args.dceq_dT if args.dceq_dT else "")
     return sc, desc
 
 

@@ -122,6 +122,11 @@ typedef struct {
                                       so the fastest growth of a delta > 0 crystal points at the
                                       angle; the seed misorientation theta of the paper's
                                       dendrite cases.  All 0 = axis-aligned crystals */
+  double dceq_dT[4][2];            /* temperature dependence of the equilibrium compositions:
+                                      ceq_a,i(T) = ceq[a][i] + dceq_dT[a][i] (T - T_E), in c_a(mu, T),
+                                      psi_a and every composition; Eq. conc gains
+                                      -(dT/dt) sum_a dceq_dT[a][i] h_a (dT/dt = -G V, h at n+1).
+                                      All 0 = ceq independent of T */
 } gpflbm_params;
 
 /* Device bytes the library needs for a problem (state ping-pong buffers,
@@ -191,7 +196,9 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
 
 /* Global totals in FP64, by a fixed-order reduction (identical from run to
  * run): mass = sum_x sum_k (f_k - w_k) + cells, solute[i] = sum_x c_i,
- * solid_frac = (1/cells) sum_x sum_{a>0} h_a.  Per cell, values are widened
+ * solid_frac = (1/cells) sum_x sum_{a>0} h_a, with c_i at the state's time
+ * (ceq_a,i(T) = ceq + dceq_dT (theta_t + G v), theta_t = -undercool - G v0
+ * - G V t, when dceq_dT is not all 0).  Per cell, values are widened
  * to FP64 first and combined without fused multiply-add.  Order: 256-thread
  * blocks, grid G = min(ceil(cells/256), 608); thread t of block b adds the
  * cells b*256 + t + j*G*256 (j = 0, 1, ...) in turn; a warp combines by
@@ -251,8 +258,8 @@ gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_e
  * recomputed from its checkpoint on a second stream (the library's own).
  * Cost: H + (ceil(H/K) - 1)(K - 1) forward steps plus H adjoint steps.
  * Supported: 2D, D2Q9, two phases, one solute, GPFLBM_FP64 or GPFLBM_FP32,
- * no shrinkage (eta_rho all 0), axis-aligned crystals (tilt all 0); anything else:
- * GPFLBM_ERR_UNSUPPORTED.
+ * no shrinkage (eta_rho all 0), axis-aligned crystals (tilt all 0), ceq independent of
+ * T (dceq_dT all 0); anything else: GPFLBM_ERR_UNSUPPORTED.
  * Outputs (each may be NULL): *J; dparams[0] = dJ/d(1/tau_phi),
  * dparams[1] = dJ/d delta_01, dparams[2] = dJ/d gbeta_c[0] (FP64,
  * accumulated per cell in FP64 and summed in a fixed order); dmu0 =

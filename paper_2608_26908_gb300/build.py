@@ -38,13 +38,13 @@ def _headers_mtime():
 
 def _units():
     """(source, object name, defines): every csrc/*.cu once, and each kernel
-    instance file a second time with the turned-crystal-axes kernels."""
+    instance file a second time with the extended-model kernels."""
     units = []
     for src in sorted(glob.glob(os.path.join(CSRC, "*.cu"))):
         name = os.path.basename(src)[:-3]
         units.append((src, name, []))
         if name.startswith("inst_"):
-            units.append((src, name + "_tilt", ["-DGPFLBM_TILT=1"]))
+            units.append((src, name + "_ext", ["-DGPFLBM_EXT=1"]))
     return units
 
 

@@ -42,7 +42,7 @@ struct gpflbm_s {
   long long cells, plane;
   int px;  // padded row pitch (elements)
   const Ops* ops;
-  const Ops* ops_tilt;  // the same configuration with turned crystal axes
+  const Ops* ops_ext;  // the same configuration, extended model (tilt, ceq(T))
   Layout lay;
   unsigned char* ws;
   bool owns_ws;
@@ -74,13 +74,14 @@ gpflbm_status cuda_fail(gpflbm_t h, cudaError_t e, const char* where) {
   return fail(h, GPFLBM_ERR_CUDA, m);
 }
 
-// The kernel table the time steps use: the turned-axes kernels when a pair
-// of the problem's phases has a nonzero tilt.
-const Ops* stepper(gpflbm_t h) { return h->pf.tilted ? h->ops_tilt : h->ops; }
+// The kernel table the time steps use: the extended model's when a pair of
+// the problem's phases has a nonzero tilt or an equilibrium composition
+// depends on temperature.
+const Ops* stepper(gpflbm_t h) { return h->pf.tilted || h->pf.tdep ? h->ops_ext : h->ops; }
 
-const Ops* find_ops(int D, int lattice, int precision, int NP, int NC, bool tilt) {
+const Ops* find_ops(int D, int lattice, int precision, int NP, int NC, bool ext) {
   using namespace gpflbm;
-#define GPFLBM_PICK(NAME) return tilt ? NAME##_tilt(NP, NC) : NAME(NP, NC)
+#define GPFLBM_PICK(NAME) return ext ? NAME##_ext(NP, NC) : NAME(NP, NC)
   if (lattice == GPFLBM_D3Q27) {
     switch (precision) {
       case GPFLBM_FP64: GPFLBM_PICK(ops_d3q27_fp64);
@@ -218,6 +219,11 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
       P.tilt_s[a][b] = (Real)std::sin(th);
       if (th != 0.0) P.tilted = 1;
     }
+    for (int i = 0; i < 2; ++i) {
+      const double k = a < h->NP && i < h->NC ? p.dceq_dT[a][i] : 0.0;
+      P.dceq_dT[a][i] = (Real)k;
+      if (k != 0.0) P.tdep = 1;
+    }
     for (int i = 0; i < 2; ++i) P.ceq[a][i] = (Real)p.ceq[a][i];
     P.S[a] = (Real)p.S[a];
   }
@@ -262,6 +268,12 @@ gpflbm_status check_params(const gpflbm_params* p, int NP, std::string* why) {
         *why = "tilt must be finite and symmetric";
         return GPFLBM_ERR_ARG;
       }
+  for (int a = 0; a < NP; ++a)
+    for (int i = 0; i < 2; ++i)
+      if (!std::isfinite(p->dceq_dT[a][i])) {
+        *why = "dceq_dT must be finite";
+        return GPFLBM_ERR_ARG;
+      }
   if (!(p->D_liq >= 0.0) || !(p->q_floor >= 0.0)) {
     *why = "need D_liq >= 0 and q_floor >= 0";
     return GPFLBM_ERR_ARG;
@@ -276,8 +288,15 @@ void set_device_params(gpflbm_t h) {
   h->inv.plane = h->plane;
   h->inv.nx = h->grid.nx;
   h->inv.px = h->px;
+  h->inv.vlayer = h->D == 3 ? (long long)h->grid.nx * h->grid.ny : h->grid.nx;
+  h->inv.G = h->params.G;
+  h->inv.tdep = 0;
   for (int a = 0; a < 4; ++a) {
-    for (int i = 0; i < 2; ++i) h->inv.ceq[a][i] = h->params.ceq[a][i];
+    for (int i = 0; i < 2; ++i) {
+      h->inv.ceq[a][i] = h->params.ceq[a][i];
+      h->inv.dceq_dT[a][i] = a < h->NP && i < h->NC ? h->params.dceq_dT[a][i] : 0.0;
+      if (h->inv.dceq_dT[a][i] != 0.0) h->inv.tdep = 1;
+    }
     h->inv.inv2A[a] = 1.0 / (2.0 * h->params.A[a]);
   }
 }
@@ -379,7 +398,7 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
   h->D = D;
   h->Q = ops->Q;
   h->ops = ops;
-  h->ops_tilt = find_ops(D, grid->lattice, grid->precision, n_phases, n_components, true);
+  h->ops_ext = find_ops(D, grid->lattice, grid->precision, n_phases, n_components, true);
   h->cells = (long long)grid->nx * grid->ny * grid->nz;
   h->px = (int)round_up(grid->nx, 8);
   h->plane = (long long)round_up((size_t)h->px * grid->ny * grid->nz, 64);
@@ -406,7 +425,7 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
     h->owns_ws = true;
   }
   cudaError_t e = h->ops->configure();
-  if (e == cudaSuccess) e = h->ops_tilt->configure();
+  if (e == cudaSuccess) e = h->ops_ext->configure();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     std::fprintf(stderr, "gpflbm_create: %s\n", cudaGetErrorString(e));
@@ -653,7 +672,7 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
   const int blocks = (int)(want < gpflbm::kRedMaxBlocks ? want : gpflbm::kRedMaxBlocks);
   double* partial = reinterpret_cast<double*>(at(h, h->lay.partial));
   double* red = reinterpret_cast<double*>(at(h, h->lay.red));
-  cudaError_t e = h->ops->invariants(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
+  cudaError_t e = (h->inv.theta_t = h->pd.theta0 - h->pd.GV * (double)h->t, h->ops->invariants)(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
                                      at(h, h->lay.f[h->cur]), partial, blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: kernel");
   double out[GPFLBM_MAX_SOLUTES + 3];
@@ -772,7 +791,7 @@ extern "C" gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, dou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* partial = scratch;
   double* red = scratch + (size_t)kNoAllocMaxBlocks * kNoAllocValues;
-  e = h->ops->invariants(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
+  e = (h->inv.theta_t = h->pd.theta0 - h->pd.GV * (double)h->t, h->ops->invariants)(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
                          at(h, h->lay.f[h->cur]), partial, (int)blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: kernel");
   double out[kNoAllocValues];
@@ -840,10 +859,10 @@ AdjLayout adj_layout(gpflbm_t h, int H, int K) {
 gpflbm_status adj_check(gpflbm_t h, int H, int K) {
   const int prec = h->grid.precision;
   if (h->D != 2 || h->NP != 2 || h->NC != 1 || (prec != GPFLBM_FP64 && prec != GPFLBM_FP32) ||
-      h->pf.shrink || h->pd.shrink || h->pf.tilted)
+      h->pf.shrink || h->pd.shrink || h->pf.tilted || h->pf.tdep)
     return fail(h, GPFLBM_ERR_UNSUPPORTED,
-                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage "
-                "or tilted crystal axes");
+                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage, "
+                "tilted crystal axes or temperature-dependent ceq");
   if (H < 1 || K < 1) return fail(h, GPFLBM_ERR_ARG, "adjoint: need horizon >= 1 and ckpt_every >= 1");
   return GPFLBM_OK;
 }

@@ -148,6 +148,8 @@ struct DevParams {
   Real tilt_c[4][4];   // cos and sin of the turn of a pair's crystal axes about z
   Real tilt_s[4][4];
   int tilted;          // 1 if any pair of the problem's phases has a nonzero turn
+  Real dceq_dT[4][2];  // ceq_a,i(T) = ceq[a][i] + dceq_dT[a][i] (T - T_E)
+  int tdep;            // 1 if any of them is nonzero
 };
 
 template <class Real>
@@ -467,7 +469,7 @@ __global__ void load_f_kernel(long long cells, int nx, int px, long long plane,
 }
 
 // Exchange-format fields of the current state; any output may be null.
-// phi: N planes (liquid first); c_i = sum_a h_a (ceq_a,i + mu_i / (2 A_a));
+// phi: N planes (liquid first); c_i = sum_a h_a (ceq_a,i(T) + mu_i / (2 A_a));
 // f = w + d; rho = 1 + sum d; U as in the step (force-corrected); dev = d.
 template <int D, int Q, int NP, int NC, class Real, class Store, class Out>
 __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ phi,
@@ -494,6 +496,8 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
   if (o_mu)
 #pragma unroll
     for (int i = 0; i < NC; ++i) o_mu[i * cells + x] = Out(mu[i]);
+  const int v_coord = D == 3 ? gz : gy;
+  const Real theta = Real(P.theta0 - P.GV * clock[0]) + P.G * Real(v_coord);  // T - T_E
   if (o_c) {
     Real h[NP];
 #pragma unroll
@@ -502,7 +506,7 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
     for (int i = 0; i < NC; ++i) {
       Real c = Real(0);
 #pragma unroll
-      for (int a = 0; a < NP; ++a) c += h[a] * (P.ceq[a][i] + mu[i] * P.inv2A[a]);
+      for (int a = 0; a < NP; ++a) c += h[a] * (P.ceq[a][i] + P.dceq_dT[a][i] * theta + mu[i] * P.inv2A[a]);
       o_c[i * cells + x] = Out(c);
     }
   }
@@ -525,11 +529,10 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
     const Real phil = obstacle(P, gx, gy, gz) ? Real(0) : p[0];
     const Real sl = Real(1) - phil;
     const Real kappa = P.kappa0 * sl * sl;
-    const int v_coord = D == 3 ? gz : gy;
-    const Real theta = Real(P.theta0 - P.GV * clock[0]) + P.G * Real(v_coord);
     Real drive = P.gbeta_T * (theta + P.dT_ref);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
+    for (int i = 0; i < NC; ++i)
+      drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * theta + mu[i] * P.inv2A[0]);
     const Real FB = rho * phil * drive;
     const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
 #pragma unroll
@@ -545,6 +548,11 @@ struct InvParams {
   int nx, px;
   double ceq[4][2];
   double inv2A[4];
+  // temperature-dependent ceq: T - T_E = theta_t + G v, v = x / vlayer
+  double dceq_dT[4][2];
+  double theta_t, G;
+  long long vlayer;
+  int tdep;
 };
 
 constexpr int kRedThreads = 256;
@@ -600,12 +608,15 @@ __global__ void __launch_bounds__(kRedThreads)
     for (int a = 0; a < NP; ++a) h[a] = h_exact<NP>(p, a);
     double v[NV];
     v[0] = dm;
+    const double th = P.tdep ? __dadd_rn(P.theta_t, __dmul_rn(P.G, (double)(x / P.vlayer))) : 0.0;
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
       double c = 0.0;
 #pragma unroll
-      for (int a = 0; a < NP; ++a)
-        c = __dadd_rn(c, __dmul_rn(h[a], __dadd_rn(P.ceq[a][i], __dmul_rn(m[i], P.inv2A[a]))));
+      for (int a = 0; a < NP; ++a) {
+        const double ce = P.tdep ? __dadd_rn(P.ceq[a][i], __dmul_rn(P.dceq_dT[a][i], th)) : P.ceq[a][i];
+        c = __dadd_rn(c, __dmul_rn(h[a], __dadd_rn(ce, __dmul_rn(m[i], P.inv2A[a]))));
+      }
       v[1 + i] = c;
     }
     double sol = 0.0;

@@ -58,9 +58,10 @@ struct Ops {
 };
 
 // QQ: lattice size (0 = D2Q9 in 2D, D3Q19 in 3D; 27 = D3Q27).
-// TILT: the step kernels turn the pairs' crystal axes (a separate table, so
-// that the axis-aligned kernels are not touched).
-template <int D, int NP, int NC, class Real, class Store, int QQ = 0, bool TILT = false>
+// EXT: the step kernels of the extended model -- turned crystal axes and
+// temperature-dependent equilibrium compositions (a separate table, so that
+// the plain kernels are not touched).
+template <int D, int NP, int NC, class Real, class Store, int QQ = 0, bool EXT = false>
 struct Impl {
   static constexpr int Q = QQ ? QQ : (D == 2 ? 9 : 19);
 
@@ -70,16 +71,16 @@ struct Impl {
   static cudaError_t configure() {
     cudaError_t e;
     if constexpr (D == 2) {
-      e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, false, TILT>,
+      e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, false, EXT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, true, TILT>,
+        e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, true, EXT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
     } else {
-      e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false, Q, TILT>,
+      e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false, Q, EXT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q, TILT>,
+        e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q, EXT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
     }
     return e;
@@ -92,18 +93,18 @@ struct Impl {
       const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
       if (P.shrink)
-        step2d_kernel<NP, NC, Real, Store, true, TILT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+        step2d_kernel<NP, NC, Real, Store, true, EXT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
       else
-        step2d_kernel<NP, NC, Real, Store, false, TILT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
+        step2d_kernel<NP, NC, Real, Store, false, EXT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
     } else {
       const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
                       (P.n[2] + S3::ZS - 1) / S3::ZS);
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
       if (P.shrink)
-        step3d_kernel<NP, NC, Real, Store, true, Q, TILT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, true, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
       else
-        step3d_kernel<NP, NC, Real, Store, false, Q, TILT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, false, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
     }
     return cudaGetLastError();
   }
@@ -178,11 +179,11 @@ struct Impl {
 };
 
 // One function per (dimension, precision) translation unit.  Each instance
-// file compiles twice: with GPFLBM_TILT = 0 the axis-aligned kernels, with
-// GPFLBM_TILT = 1 the turned-axes ones, whose table function is NAME_tilt.
+// file compiles twice: with GPFLBM_EXT = 0 the plain kernels, with
+// GPFLBM_EXT = 1 those of the extended model, whose table function is NAME_ext.
 #define GPFLBM_DECLARE_OPS(NAME)  \
   const Ops* NAME(int NP, int NC); \
-  const Ops* NAME##_tilt(int NP, int NC);
+  const Ops* NAME##_ext(int NP, int NC);
 GPFLBM_DECLARE_OPS(ops_d2_fp64)
 GPFLBM_DECLARE_OPS(ops_d2_fp32)
 GPFLBM_DECLARE_OPS(ops_d2_f16)
@@ -194,16 +195,16 @@ GPFLBM_DECLARE_OPS(ops_d3_bf16)
 GPFLBM_DECLARE_OPS(ops_d3q27_fp64)  // D3Q27 (FP64 and FP32 arithmetic and storage)
 GPFLBM_DECLARE_OPS(ops_d3q27_fp32)
 
-#ifndef GPFLBM_TILT
-#define GPFLBM_TILT 0
+#ifndef GPFLBM_EXT
+#define GPFLBM_EXT 0
 #endif
-#if GPFLBM_TILT
-#define GPFLBM_OPS_NAME(NAME) NAME##_tilt
+#if GPFLBM_EXT
+#define GPFLBM_OPS_NAME(NAME) NAME##_ext
 #else
 #define GPFLBM_OPS_NAME(NAME) NAME
 #endif
 
-#define GPFLBM_IMPL(DIM, NP_, NC_, QQ, REAL, STORE) Impl<DIM, NP_, NC_, REAL, STORE, QQ, (GPFLBM_TILT != 0)>
+#define GPFLBM_IMPL(DIM, NP_, NC_, QQ, REAL, STORE) Impl<DIM, NP_, NC_, REAL, STORE, QQ, (GPFLBM_EXT != 0)>
 #define GPFLBM_DEFINE_OPS_Q(NAME, DIM, QQ, REAL, STORE)                               \
   const Ops* GPFLBM_OPS_NAME(NAME)(int NP, int NC) {                                  \
     if (NP == 2 && NC == 1) return GPFLBM_IMPL(DIM, 2, 1, QQ, REAL, STORE)::table();  \

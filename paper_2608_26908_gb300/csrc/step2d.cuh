@@ -73,10 +73,11 @@ struct Step2DIO {
   double* clock_out;
 };
 
-// TILT: the pairs' crystal axes are turned about z (dAdq_pair).
+// EXT: the extended model -- pairs' crystal axes turned about z (dAdq_pair)
+// and equilibrium compositions ceq_a(T) with the temperature term of Eq. conc.
 // SHRINK: the shrinkage force needs phi^{n+1}, so the collision moves after
 // the phase-field update (the raw populations wait in the collision buffer).
-template <int NP, int NC, class Real, class Store, bool SHRINK = false, bool TILT = false>
+template <int NP, int NC, class Real, class Store, bool SHRINK = false, bool EXT = false>
 __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>::MIN_CTAS)
     step2d_kernel(const DevParams<Real> P, const Step2DIO io) {
   using S = Step2D<NP, NC, Real, Store>;
@@ -112,6 +113,13 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
   const bool obs = (P.wall[0] | P.wall[1]) != 0 && obstacle(P, fx, fy, 0);
+  // EXT: ceq_a,i(T) of this cell, T - T_E = theta_base + G v
+  auto ceq_of = [&](int a, int i, int v) -> Real {
+    if constexpr (EXT)
+      return P.ceq[a][i] + P.dceq_dT[a][i] * (theta_base + P.G * Real(v));
+    else
+      return P.ceq[a][i];
+  };
 
   // 0. own cell: phases present, mu; ring cells (phi only); collision
   Real ph[NP];
@@ -170,7 +178,13 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     const Real kappa = P.kappa0 * sl * sl;
     Real drive = P.gbeta_T * (theta_base + P.G * Real(fy) + P.dT_ref);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
+    for (int i = 0; i < NC; ++i) {
+      if constexpr (EXT)
+        drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * (theta_base + P.G * Real(fy)) +
+                                 mu[i] * P.inv2A[0]);
+      else
+        drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
+    }
     const Real FB = rho * phil * drive;
     const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
     Real ux, uy, Fx, Fy;
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
             Real q[2];
             q[d] = pf[a] * gn[b] - pf[b] * gn[a];
             q[1 - d] = pf[a] * gt[b] - pf[b] * gt[a];
-            const Real v = dAdq_pair<2, TILT>(P, a, b, q, d);
+            const Real v = dAdq_pair<2, EXT>(P, a, b, q, d);
             fl[a] -= gab * pf[b] * v;  // dA/dq(q_ba) = -dA/dq(q_ab)
             fl[b] += gab * pf[a] * v;
           }
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
           Real q[2], v[2];
           q[0] = ph[a] * gc[b][0] - ph[b] * gc[a][0];
           q[1] = ph[a] * gc[b][1] - ph[b] * gc[a][1];
-          dAdq_vec_pair<2, TILT>(P, a, b, q, v);
+          dAdq_vec_pair<2, EXT>(P, a, b, q, v);
           dadphi[a] += gab * (v[0] * gc[b][0] + v[1] * gc[b][1]);
           dadphi[b] -= gab * (v[0] * gc[a][0] + v[1] * gc[a][1]);
         }
@@ -293,7 +307,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
       for (int b = 0; b < NP; ++b) {
         Real sv = P.S[b] * theta;
 #pragma unroll
-        for (int i = 0; i < NC; ++i) sv -= mu[i] * mu[i] * P.inv4A[b] + mu[i] * P.ceq[b][i];
+        for (int i = 0; i < NC; ++i) sv -= mu[i] * mu[i] * P.inv4A[b] + mu[i] * ceq_of(b, i, fy);
         psi[b] = sv;
       }
       Real rate[NP];
@@ -399,11 +413,13 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     if (!closed) {
       const Real Mf = Real(0.5) * P.M0 * (s_pn[tid] + s_pn[nb]);  // plane 0 = liquid
       const Real ua = s_u[d * NT + tid] * s_hl[tid], ub = s_u[d * NT + nb] * s_hl[nb];
+      // vertical index of the neighbour (for ceq(T))
+      const int vb = d == 0 ? fy : (inner_tile ? fy + 1 : fold_axis(P, gy + 1, 1));
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
         const Real ma = s_mu[i * NT + tid], mb = s_mu[i * NT + nb];
-        J[i] = -Mf * (mb - ma) +
-               Real(0.5) * (ua * (P.ceq[0][i] + ma * P.inv2A[0]) + ub * (P.ceq[0][i] + mb * P.inv2A[0]));
+        J[i] = -Mf * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fy) + ma * P.inv2A[0]) +
+                                              ub * (ceq_of(0, i, vb) + mb * P.inv2A[0]));
       }
       if (any_changed && P.at_eps != Real(0) && (s_chg[tid] | s_chg[nb])) {
         const int st = d == 0 ? W2 : 1;  // transverse stride
@@ -423,8 +439,13 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
           const Real dinv = P.inv2A[0] - P.inv2A[a];
 #pragma unroll
           for (int i = 0; i < NC; ++i) {
-            const Real dc = (P.ceq[0][i] - P.ceq[a][i]) +
-                            Real(0.5) * (s_mu[i * NT + tid] + s_mu[i * NT + nb]) * dinv;
+            Real dc = (P.ceq[0][i] - P.ceq[a][i]) +
+                      Real(0.5) * (s_mu[i * NT + tid] + s_mu[i * NT + nb]) * dinv;
+            if constexpr (EXT) {
+              const int vb = d == 0 ? fy : (inner_tile ? fy + 1 : fold_axis(P, gy + 1, 1));
+              dc += (P.dceq_dT[0][i] - P.dceq_dT[a][i]) *
+                    (theta_base + Real(0.5) * P.G * Real(fy + vb));
+            }
             at[i] += dc * dphi * nd;
           }
         }
@@ -449,7 +470,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   if (obs) {
 #pragma unroll
     for (int i = 0; i < NC; ++i) (mu_out + i * P.plane)[g] = mu[i];
-  } else if (!changed && pure >= 0) {
+  } else if (!EXT && !changed && pure >= 0) {
     // unchanged pure cell: source term exactly 0, chi = 1 / (2 A_pure)
     Real ichi = P.chi_pure[0];
 #pragma unroll
@@ -477,7 +498,12 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
       Real src = Real(0);
       if (changed) {
 #pragma unroll
-        for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu[i] * P.inv2A[a]) * (hn[a] - ho[a]);
+        for (int a = 0; a < NP; ++a) src += (ceq_of(a, i, fy) + mu[i] * P.inv2A[a]) * (hn[a] - ho[a]);
+      }
+      if constexpr (EXT) {
+        // -(dT/dt) sum_a (dc_a/dT)_mu h_a^{n+1}, dT/dt = -G V
+#pragma unroll
+        for (int a = 0; a < NP; ++a) src -= Real(P.GV) * P.dceq_dT[a][i] * hn[a];
       }
       (mu_out + i * P.plane)[g] = mu[i] + (-div - src) * ichi;
     }

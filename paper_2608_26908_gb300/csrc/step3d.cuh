@@ -73,10 +73,11 @@ struct Step3DIO {
   double* clock_out;
 };
 
-// TILT: the pairs' crystal axes are turned about z (dAdq_pair).
+// EXT: the extended model -- pairs' crystal axes turned about z (dAdq_pair)
+// and equilibrium compositions ceq_a(T) with the temperature term of Eq. conc.
 // SHRINK: the shrinkage force needs phi^{n+1}, so the collision of a plane
 // moves after its phase-field update (its populations are read again then).
-template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19, bool TILT = false>
+template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19, bool EXT = false>
 __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
   using S = Step3D<NP, NC, Real, Store, QQ>;
@@ -116,6 +117,13 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   const double t_now = io.clock_in[0];
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
+  // EXT: ceq_a,i(T) at vertical index v, T - T_E = theta_base + G v
+  auto ceq_of = [&](int a, int i, int v) -> Real {
+    if constexpr (EXT)
+      return P.ceq[a][i] + P.dceq_dT[a][i] * (theta_base + P.G * Real(v));
+    else
+      return P.ceq[a][i];
+  };
   const bool has_walls = (P.wall[0] | P.wall[1] | P.wall[2]) != 0;  // obstacle rows
 
   int rx = 0, ry = 0;  // ring column held by threads tid < RING
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         Real q[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) q[t] = pf[a] * g3[b][t] - pf[b] * g3[a][t];
-        const Real v = dAdq_pair<3, TILT>(P, a, b, q, d);
+        const Real v = dAdq_pair<3, EXT>(P, a, b, q, d);
         fl[a] -= gab * pf[b] * v;
         fl[b] += gab * pf[a] * v;
       }
@@ -275,7 +283,13 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       const Real kappa = P.kappa0 * sl * sl;
       Real drive = P.gbeta_T * (theta_base + P.G * Real(fzc) + P.dT_ref);
 #pragma unroll
-      for (int i = 0; i < NC; ++i) drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
+      for (int i = 0; i < NC; ++i) {
+        if constexpr (EXT)
+          drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * (theta_base + P.G * Real(fzc)) +
+                                   mu[i] * P.inv2A[0]);
+        else
+          drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
+      }
       const Real FB = rho * phl * drive;
       const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
       Real u[3], F[3];
@@ -410,11 +424,12 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
             Real q[3], v[3];
 #pragma unroll
             for (int t = 0; t < 3; ++t) q[t] = ph[a] * gc[b][t] - ph[b] * gc[a][t];
-            dAdq_vec_pair<3, TILT>(P, a, b, q, v);
+            dAdq_vec_pair<3, EXT>(P, a, b, q, v);
             dadphi[a] += gab * (v[0] * gc[b][0] + v[1] * gc[b][1] + v[2] * gc[b][2]);
             dadphi[b] -= gab * (v[0] * gc[a][0] + v[1] * gc[a][1] + v[2] * gc[a][2]);
           }
-        const Real theta = theta_base + P.G * Real(fold_axis(P, C, 2));
+        const int fzC = fold_axis(P, C, 2);
+        const Real theta = theta_base + P.G * Real(fzC);
         Real mu[NC];
 #pragma unroll
         for (int i = 0; i < NC; ++i) mu[i] = s_mu[(slot2(C) * NC + i) * NT + tid];
@@ -423,7 +438,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         for (int b = 0; b < NP; ++b) {
           Real sv = P.S[b] * theta;
 #pragma unroll
-          for (int i = 0; i < NC; ++i) sv -= mu[i] * mu[i] * P.inv4A[b] + mu[i] * P.ceq[b][i];
+          for (int i = 0; i < NC; ++i) sv -= mu[i] * mu[i] * P.inv4A[b] + mu[i] * ceq_of(b, i, fzC);
           psi[b] = sv;
         }
         Real rate[NP];
@@ -511,8 +526,14 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         const Real kappa = P.kappa0 * sl * sl;
         Real drive = P.gbeta_T * (theta_base + P.G * Real(fzc) + P.dT_ref);
 #pragma unroll
-        for (int i = 0; i < NC; ++i)
-          drive += P.gbeta_c[i] * (P.dcl_ref[i] + s_mu[(slot2(C) * NC + i) * NT + tid] * P.inv2A[0]);
+        for (int i = 0; i < NC; ++i) {
+          const Real mc = s_mu[(slot2(C) * NC + i) * NT + tid];
+          if constexpr (EXT)
+            drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * (theta_base + P.G * Real(fzc)) +
+                                     mc * P.inv2A[0]);
+          else
+            drive += P.gbeta_c[i] * (P.dcl_ref[i] + mc * P.inv2A[0]);
+        }
         const Real FB = rho * phl * drive;
         const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
         Real u[3], F[3];
@@ -570,11 +591,12 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         const Real Mf = Real(0.5) * P.M0 * (pnA[A] + pnB[nbT]);  // plane 0 = liquid
         const Real ua = s_u[(slot2(pA) * 3 + d) * NT + A] * s_hl[slot2(pA) * NT + A];
         const Real ub = s_u[(slot2(pB) * 3 + d) * NT + nbT] * s_hl[slot2(pB) * NT + nbT];
+        const int fzB = d == 2 ? fold_axis(P, pB, 2) : fzm;  // vertical index of B (ceq(T))
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
           const Real ma = s_mu[(slot2(pA) * NC + i) * NT + A], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
-          J[i] = -Mf * (mb - ma) +
-                 Real(0.5) * (ua * (P.ceq[0][i] + ma * P.inv2A[0]) + ub * (P.ceq[0][i] + mb * P.inv2A[0]));
+          J[i] = -Mf * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fzm) + ma * P.inv2A[0]) +
+                                                ub * (ceq_of(0, i, fzB) + mb * P.inv2A[0]));
         }
         if (P.at_eps != Real(0) && (s_chg[slot2(pA) * NT + A] | s_chg[slot2(pB) * NT + nbT])) {
           const Real liq = Real(0.5) * (PH(pA, 0, rA) + PH(pB, 0, nbR));
@@ -601,8 +623,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
             const Real dinv = P.inv2A[0] - P.inv2A[a];
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-              const Real dc = (P.ceq[0][i] - P.ceq[a][i]) +
-                              Real(0.5) * (s_mu[(slot2(pA) * NC + i) * NT + A] + s_mu[(slot2(pB) * NC + i) * NT + nbT]) * dinv;
+              Real dc = (P.ceq[0][i] - P.ceq[a][i]) +
+                        Real(0.5) * (s_mu[(slot2(pA) * NC + i) * NT + A] + s_mu[(slot2(pB) * NC + i) * NT + nbT]) * dinv;
+              if constexpr (EXT)
+                dc += (P.dceq_dT[0][i] - P.dceq_dT[a][i]) * (theta_base + Real(0.5) * P.G * Real(fzm + fzB));
               at[i] += dc * dphi * nd;
             }
           }
@@ -650,7 +674,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       if (has_walls && obstacle(P, fx, fy, fzm)) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = s_mu[(slot2(M) * NC + i) * NT + tid];
-      } else if (s_chg[slot2(M) * NT + tid] == 0 && pure_phase<NP>(pn) >= 0) {
+      } else if (!EXT && s_chg[slot2(M) * NT + tid] == 0 && pure_phase<NP>(pn) >= 0) {
         // unchanged pure cell: source term exactly 0, chi = 1 / (2 A_pure)
         const int pa = pure_phase<NP>(pn);
         Real ichi = P.chi_pure[0];
@@ -684,7 +708,12 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
           Real src = Real(0);
           if (changed) {
 #pragma unroll
-            for (int a = 0; a < NP; ++a) src += (P.ceq[a][i] + mu * P.inv2A[a]) * (hn[a] - ho[a]);
+            for (int a = 0; a < NP; ++a) src += (ceq_of(a, i, fzm) + mu * P.inv2A[a]) * (hn[a] - ho[a]);
+          }
+          if constexpr (EXT) {
+            // -(dT/dt) sum_a (dc_a/dT)_mu h_a^{n+1}, dT/dt = -G V
+#pragma unroll
+            for (int a = 0; a < NP; ++a) src -= Real(P.GV) * P.dceq_dT[a][i] * hn[a];
           }
           mu_out[i * P.plane + g] = mu + (-div - src) * ichi;
         }

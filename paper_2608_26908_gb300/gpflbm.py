@@ -42,6 +42,7 @@ class Params(ctypes.Structure):
         ("q_floor", ctypes.c_double),
         ("eta_rho", ctypes.c_double * 4),
         ("tilt", (ctypes.c_double * 4) * 4),
+        ("dceq_dT", (ctypes.c_double * 2) * 4),
     ]
 
 
@@ -138,6 +139,8 @@ def params_struct(sc):
         p.eta_rho[a] = pr.get("eta_rho", [0.0] * 4)[a]
         for b in range(4):
             p.tilt[a][b] = pr.get("tilt", [[0.0] * 4] * 4)[a][b]
+        for i in range(2):
+            p.dceq_dT[a][i] = pr.get("dceq_dT", [[0.0] * 2] * 4)[a][i]
     return p
 
 
