@@ -122,8 +122,16 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   };
 
   // 0. own cell: phases present, mu; ring cells (phi only); collision
+  // a cell of pure liquid: phi_0 = 1 and every other phase 0, exactly
+  auto pure_liquid = [](const Real* v) {
+    bool p = v[0] == Real(1);
+#pragma unroll
+    for (int a = 1; a < NP; ++a) p = p && v[a] == Real(0);
+    return p;
+  };
   Real ph[NP];
   load_phases<NP>(phi_in, g, P.plane, ph);
+  bool liquid = pure_liquid(ph) && !obs;  // the tile's cells, for the liquid-tile path
   {
     unsigned m = 0;
 #pragma unroll
@@ -152,6 +160,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     const int qy = inner_tile ? y0 - 2 + ry : fold_axis(P, y0 - 2 + ry, 1);
     Real v[NP];
     load_phases<NP>(phi_in, qy * px + qx, P.plane, v);
+    liquid = liquid && pure_liquid(v);
     unsigned m = 0;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
@@ -216,7 +225,84 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
       lbm_cell(dk, Real(0), Real(0));
     }
   }
-  __syncthreads();
+  // the inner cells write mu^{n+1}, phi^{n+1} and pull f^{n+1}
+  const bool inner = !(tx < 1 || tx > BX - 2 || ty < 1 || ty > BY - 2 || gx >= nx || gy >= ny);
+  Real* __restrict__ phi_out = static_cast<Real*>(io.phi_out);
+  Real* __restrict__ mu_out = static_cast<Real*>(io.mu_out);
+  Store* __restrict__ f_out = static_cast<Store*>(io.f_out);
+  auto pull_f = [&]() {
+    if (inner_tile) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k)
+        (f_out + k * P.plane)[g] = s_fs[k * NT + tid - Lat::c(k, 0) - Lat::c(k, 1) * BX];
+    } else {
+      const bool wx = P.bc[0] == kWall, wy = P.bc[1] == kWall;
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        const int cx = Lat::c(k, 0), cy = Lat::c(k, 1);
+        const bool bounce =
+            (wx && (gx - cx < 0 || gx - cx >= nx)) || (wy && (gy - cy < 0 || gy - cy >= ny));
+        const Store v = bounce ? s_fs[Lat::opp(k) * NT + tid] : s_fs[k * NT + tid - cx - cy * BX];
+        (f_out + k * P.plane)[g] = v;
+      }
+    }
+  };
+
+  // Liquid tile: every cell of R1 and its ring is pure liquid and none is an
+  // obstacle.  The phase field stays exactly as it is, h_l = 1, M = M0,
+  // chi = 1 / (2 A_l) and there is no antitrapping, so the general path
+  // below reduces to these few lines (the same arithmetic, term for term).
+  if (__syncthreads_and(liquid)) {
+    if constexpr (SHRINK) {
+      // F_S = 0 where nothing solidifies: the deferred collision of the
+      // general path with a zero shrinkage force
+      Real dk[Q];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(s_fs[k * NT + tid]);
+      lbm_cell(dk, Real(0), Real(0));
+      __syncthreads();
+    }
+    auto face = [&](int d) {
+      const int nb = d == 0 ? tid + 1 : tid + BX;
+      const int gbd = (d == 0 ? gx : gy) + 1;
+      const bool closed = (P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d];
+      Real J[NC];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) J[i] = Real(0);
+      if (!closed) {
+        const Real Mf = P.M0;                                   // 0.5 M0 (1 + 1)
+        const Real ua = s_u[d * NT + tid], ub = s_u[d * NT + nb];  // h_l = 1
+        const int vb = d == 0 ? fy : (inner_tile ? fy + 1 : fold_axis(P, gy + 1, 1));
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          const Real ma = s_mu[i * NT + tid], mb = s_mu[i * NT + nb];
+          J[i] = -Mf * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fy) + ma * P.inv2A[0]) +
+                                                ub * (ceq_of(0, i, vb) + mb * P.inv2A[0]));
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NC; ++i) s_flux[i * 2 * NT + d * NT + tid] = J[i];
+    };
+    if (tx < BX - 1) face(0);
+    if (ty < BY - 1) face(1);
+    __syncthreads();
+    if (!inner) return;
+#pragma unroll
+    for (int sidx = 0; sidx < NS; ++sidx) (phi_out + sidx * P.plane)[g] = ph[NP == 2 ? 1 : sidx];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const Real* Ji = s_flux + i * 2 * NT;
+      const Real div = (Ji[tid] - Ji[tid - 1]) + (Ji[NT + tid] - Ji[NT + tid - BX]);
+      Real src = Real(0);
+      if constexpr (EXT) {
+#pragma unroll
+        for (int a = 0; a < NP; ++a) src -= Real(P.GV) * P.dceq_dT[a][i] * (a == 0 ? Real(1) : Real(0));
+      }
+      (mu_out + i * P.plane)[g] = mu[i] + (-div - src) * P.chi_pure[0];
+    }
+    pull_f();
+    return;
+  }
 
   // 1. phase field where phases mix
   unsigned act = 0;
@@ -461,10 +547,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   __syncthreads();
 
   // 3. inner cells: mu^{n+1}, phi^{n+1}, pulled f^{n+1}
-  if (tx < 1 || tx > BX - 2 || ty < 1 || ty > BY - 2 || gx >= nx || gy >= ny) return;
-  Real* __restrict__ phi_out = static_cast<Real*>(io.phi_out);
-  Real* __restrict__ mu_out = static_cast<Real*>(io.mu_out);
-  Store* __restrict__ f_out = static_cast<Store*>(io.f_out);
+  if (!inner) return;
 #pragma unroll
   for (int sidx = 0; sidx < NS; ++sidx) (phi_out + sidx * P.plane)[g] = out[NP == 2 ? 1 : sidx];
   if (obs) {
@@ -508,21 +591,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
       (mu_out + i * P.plane)[g] = mu[i] + (-div - src) * ichi;
     }
   }
-  if (inner_tile) {
-#pragma unroll
-    for (int k = 0; k < Q; ++k)
-      (f_out + k * P.plane)[g] = s_fs[k * NT + tid - Lat::c(k, 0) - Lat::c(k, 1) * BX];
-  } else {
-    const bool wx = P.bc[0] == kWall, wy = P.bc[1] == kWall;
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      const int cx = Lat::c(k, 0), cy = Lat::c(k, 1);
-      const bool bounce =
-          (wx && (gx - cx < 0 || gx - cx >= nx)) || (wy && (gy - cy < 0 || gy - cy >= ny));
-      const Store v = bounce ? s_fs[Lat::opp(k) * NT + tid] : s_fs[k * NT + tid - cx - cy * BX];
-      (f_out + k * P.plane)[g] = v;
-    }
-  }
+  pull_f();
 }
 
 }  // namespace gpflbm
