@@ -897,18 +897,31 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     if (j == seg_len(c) && c + 1 < n_ck) return clk + c + 1;
     return clk + n_ck + (c & 1) * K + (j - 1);
   };
-  auto step = [&](int c, int j, cudaStream_t st) {
+  // The forward pass keeps only the checkpoints and the last segment: the
+  // inner states of the other segments alternate between two slots of the
+  // segment buffer the last segment does not use (they stay in L2; the
+  // backward pass recomputes them).
+  const int last = n_ck - 1;
+  auto fw_at = [&](int c, int j) {
+    if (c == last || j == 0 || j == seg_len(c)) return st_at(c, j);
+    return ws + L.seg[(last + 1) & 1] + (size_t)((j - 1) & 1) * L.state;
+  };
+  auto fw_clk = [&](int c, int j) {
+    if (c == last || j == 0 || j == seg_len(c)) return clk_at(c, j);
+    return clk + n_ck + ((last + 1) & 1) * K + ((j - 1) & 1);
+  };
+  auto step = [&](int c, int j, cudaStream_t st, bool forward_pass) {
     gpflbm::StepIO io;
-    unsigned char* in = st_at(c, j);
-    unsigned char* out = st_at(c, j + 1);
+    unsigned char* in = forward_pass ? fw_at(c, j) : st_at(c, j);
+    unsigned char* out = forward_pass ? fw_at(c, j + 1) : st_at(c, j + 1);
     io.phi_in = in;
     io.mu_in = in + pl;
     io.f_in = in + 2 * pl;
     io.phi_out = out;
     io.mu_out = out + pl;
     io.f_out = out + 2 * pl;
-    io.clock_in = clk_at(c, j);
-    io.clock_out = clk_at(c, j + 1);
+    io.clock_in = forward_pass ? fw_clk(c, j) : clk_at(c, j);
+    io.clock_out = forward_pass ? fw_clk(c, j + 1) : clk_at(c, j + 1);
     io.err = err;
     return h->ops->step(P, io, st);
   };
@@ -929,10 +942,9 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: checkpoint copy");
   for (int c = 0; c < n_ck; ++c)
     for (int j = 0; j < seg_len(c); ++j) {
-      e = step(c, j, s);
+      e = step(c, j, s, true);
       if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: forward step");
     }
-  const int last = n_ck - 1;
   e = copy_state(st_at(last, seg_len(last)), clk_at(last, seg_len(last)), false);
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: final state");
   h->t += H;
@@ -960,7 +972,7 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     if (c >= 1) {
       // segment c-1 reuses the slots segment c+1 was read from
       if (c + 1 <= last) e = cudaStreamWaitEvent(h->aux, h->ev_adj[(c + 1) & 1], 0);
-      for (int j = 0; j + 1 < seg_len(c - 1) && e == cudaSuccess; ++j) e = step(c - 1, j, h->aux);
+      for (int j = 0; j + 1 < seg_len(c - 1) && e == cudaSuccess; ++j) e = step(c - 1, j, h->aux, false);
       if (e == cudaSuccess) e = cudaEventRecord(h->ev_rec[(c - 1) & 1], h->aux);
       if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: recompute");
     }
