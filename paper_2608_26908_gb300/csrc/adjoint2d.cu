@@ -60,9 +60,20 @@ struct AdjImpl {
     io.ld0 = static_cast<Real*>(v.ld0);
     io.gacc = v.gacc;
     io.clock = v.clock;
-    const dim3 grid((P.n[0] + S::OX - 1) / S::OX, (P.n[1] + S::OY - 1) / S::OY);
-    adj2d_kernel<Real><<<grid, S::NT, S::bytes, st>>>(P, io);
-    return cudaGetLastError();
+    // programmatic dependent launch: this step's prologue (stored states
+    // only) overlaps the previous step's last CTAs; the kernel waits for
+    // the previous step before it touches lambda or gacc
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((P.n[0] + S::OX - 1) / S::OX, (P.n[1] + S::OY - 1) / S::OY);
+    cfg.blockDim = dim3(S::NT);
+    cfg.dynamicSmemBytes = S::bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, adj2d_kernel<Real>, P, io);
   }
 
   static cudaError_t sum(const void* p, const double* v, double* partial, int blocks, cudaStream_t st) {

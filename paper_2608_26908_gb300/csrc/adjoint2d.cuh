@@ -182,6 +182,14 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
   const Real e = P.inv2A[1] - P.inv2A[0];
   const Real mob = P.mob_eps * P.eps;  // 1 / tau_phi
 
+  // Programmatic dependent launch: the next adjoint step may start as this
+  // one's CTAs retire.  Until the wait below a step reads only the stored
+  // forward states (written before the segment's adjoint began), never the
+  // lambda of the previous step; everything it writes to global memory comes
+  // after the wait, which returns once the previous step has finished and
+  // its writes are visible.
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+
   // 0. per-cell values: own cell, then the outer ring
   const Real s0 = __ldg(io.s0 + o), s1 = __ldg(io.s1 + o), mu0 = __ldg(io.mu0 + o);
   const bool obs = walls && obstacle(P, fx, fy, 0);
@@ -192,15 +200,17 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
 #pragma unroll
     for (int k = 0; k < 9; ++k) dk[k] = __ldg(io.d0 + k * plane + o);
     m = macro2(P, dk, s0, mu0, obs, theta_base + P.G * Real(fy));
-    Aown = obs ? Real(0) : __ldg(io.lmu1 + o) / (P.inv2A[0] + Hs(s1) * e);
     sc[S::S0 * C2 + h2] = s0;
     sc[S::S1 * C2 + h2] = s1;
     sc[S::MU0 * C2 + h2] = mu0;
-    sc[S::AA * C2 + h2] = Aown;
     sc[S::UX * C2 + h2] = m.ux;
     sc[S::UY * C2 + h2] = m.uy;
     sm[h2] = (unsigned char)((s0 > Real(0) ? 2u : 0u) | (Real(1) - s0 > Real(0) ? 1u : 0u) | (obs ? 4u : 0u));
   }
+  long long q = 0;  // ring cell of threads tid < RING
+  Real rden = Real(0);
+  bool robs = false;
+  int rc = 0;
   if (tid < S::RING) {
     int ri, rj;
     if (tid < W2) {
@@ -218,22 +228,28 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
     }
     const int qx = inner_tile ? x0 - 2 + ri : fold_axis(P, x0 - 2 + ri, 0);
     const int qy = inner_tile ? y0 - 2 + rj : fold_axis(P, y0 - 2 + rj, 1);
-    const long long q = (long long)qy * P.px + qx;
+    q = (long long)qy * P.px + qx;
     const Real rs0 = __ldg(io.s0 + q), rs1 = __ldg(io.s1 + q), rmu = __ldg(io.mu0 + q);
-    const bool robs = walls && obstacle(P, qx, qy, 0);
+    robs = walls && obstacle(P, qx, qy, 0);
     Real dk[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) dk[k] = __ldg(io.d0 + k * plane + q);
     const Macro2<Real> rm = macro2(P, dk, rs0, rmu, robs, theta_base + P.G * Real(qy));
     const int c = rj * W2 + ri;
+    rc = c;
+    rden = P.inv2A[0] + Hs(rs1) * e;
     sc[S::S0 * C2 + c] = rs0;
     sc[S::S1 * C2 + c] = rs1;
     sc[S::MU0 * C2 + c] = rmu;
-    sc[S::AA * C2 + c] = robs ? Real(0) : __ldg(io.lmu1 + q) / (P.inv2A[0] + Hs(rs1) * e);
     sc[S::UX * C2 + c] = rm.ux;
     sc[S::UY * C2 + c] = rm.uy;
     sm[c] = (unsigned char)((rs0 > Real(0) ? 2u : 0u) | (Real(1) - rs0 > Real(0) ? 1u : 0u) | (robs ? 4u : 0u));
   }
+  // lambda^{n+1} is the previous step's output
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  Aown = obs ? Real(0) : io.lmu1[o] / (P.inv2A[0] + Hs(s1) * e);
+  sc[S::AA * C2 + h2] = Aown;
+  if (tid < S::RING) sc[S::AA * C2 + rc] = robs ? Real(0) : io.lmu1[q] / rden;
   __syncthreads();
 
   // 1. solute faces, by their lower cell a (tile + two-cell halo coordinates)
@@ -312,9 +328,9 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
 
   // 2. lambda through the mu stage, the faces and the collision
   auto F = [&](int d, int v, int c) { return sf[(d * NF + v) * C2 + c]; };
-  Real lsp = __ldg(io.ls1 + o) + F(0, S::F_SPA, h2) + F(1, S::F_SPA, h2) + F(0, S::F_SPB, h2 - 1) +
+  Real lsp = io.ls1[o] + F(0, S::F_SPA, h2) + F(1, S::F_SPA, h2) + F(0, S::F_SPB, h2 - 1) +
              F(1, S::F_SPB, h2 - W2);
-  Real lmu = __ldg(io.lmu1 + o);
+  Real lmu = io.lmu1[o];
   Real ls = Real(0);
   const Real mu1 = __ldg(io.mu1 + o);
   if (!obs) {
@@ -357,18 +373,18 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
     Real a[9];
     if (fx >= 1 && fx <= nx - 2 && fy >= 1 && fy <= ny - 2) {  // no wall or wrap in reach
 #pragma unroll
-      for (int k = 0; k < 9; ++k) a[k] = __ldg(io.ld1 + k * plane + o + Lat::c(k, 0) + Lat::c(k, 1) * P.px);
+      for (int k = 0; k < 9; ++k) a[k] = io.ld1[k * plane + o + Lat::c(k, 0) + Lat::c(k, 1) * P.px];
     } else {
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
         int qx = fx + Lat::c(k, 0), qy = fy + Lat::c(k, 1);
         const bool bounce = (P.bc[0] == kWall && (qx < 0 || qx >= nx)) || (P.bc[1] == kWall && (qy < 0 || qy >= ny));
         if (bounce) {
-          a[k] = __ldg(io.ld1 + Lat::opp(k) * plane + o);
+          a[k] = io.ld1[Lat::opp(k) * plane + o];
         } else {
           qx = qx < 0 ? qx + nx : (qx >= nx ? qx - nx : qx);
           qy = qy < 0 ? qy + ny : (qy >= ny ? qy - ny : qy);
-          a[k] = __ldg(io.ld1 + k * plane + (long long)qy * P.px + qx);
+          a[k] = io.ld1[k * plane + (long long)qy * P.px + qx];
         }
       }
     }
