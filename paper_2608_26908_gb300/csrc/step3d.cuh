@@ -162,6 +162,17 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     return b[a * C2 + i];
   };
   auto MK = [&](int p, int i) -> unsigned { return s_mask[slot3(p) * C2 + i]; };
+  // a cell of pure liquid: phi_0 = 1 and every other phase 0, exactly
+  auto pure_liquid = [](const Real* v) {
+    bool p = v[0] == Real(1);
+#pragma unroll
+    for (int a = 1; a < NP; ++a) p = p && v[a] == Real(0);
+    return p;
+  };
+  // Liquid planes: bit 0 = plane L, bit 1 = C, bit 2 = M, bit 3 = M - 1 is
+  // set when every cell of that plane in R1 and its ring is pure liquid and
+  // no cell of R1 is an obstacle (the whole CTA agrees: __syncthreads_and).
+  unsigned liq_hist = 0;
 
   // OR of the phase masks over the 3x3 in-plane neighbourhood of this
   // column, for planes C-1 and C (carried) and L (new)
@@ -228,6 +239,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   const int L0 = z0 - 2, L1 = z0 + ZS + 1;
   for (int L = L0; L <= L1; ++L) {
     const int C = L - 1, M = L - 2;
+    bool liq_l;  // this thread's cells of plane L are pure liquid
     // A. phi^n of plane L
     {
       const int zo = fold_axis(P, L, 2) * zst;
@@ -241,8 +253,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         if (v[a] > Real(0)) m |= 1u << a;
       }
       s_mask[slot3(L) * C2 + r2] = (unsigned char)m;
+      liq_l = pure_liquid(v) && !(has_walls && obstacle(P, fx, fy, fold_axis(P, L, 2)));
       if (tid < S::RING) {
         load_phases<NP>(phi_in, zo + gring, P.plane, v);
+        liq_l = liq_l && pure_liquid(v);
         m = 0;
 #pragma unroll
         for (int a = 0; a < NP; ++a) {
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       }
       }  // !SHRINK
     }
-    __syncthreads();
+    liq_hist = ((liq_hist << 1) | (__syncthreads_and(liq_l) ? 1u : 0u)) & 15u;
 
     // C. phase field of plane C where phases mix
     const bool pfC = C >= z0 - 1 && C <= z0 + ZS;
@@ -345,10 +359,14 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     bool mixed = false, multi = false;
     unsigned act = 0;
     unsigned xy_l = 0;
+    if (liq_hist & 1u) {
+      xy_l = 1u;  // plane L is liquid: every mask of the 3x3 is the liquid bit
+    } else {
 #pragma unroll
-    for (int dy = -1; dy <= 1; ++dy)
+      for (int dy = -1; dy <= 1; ++dy)
 #pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) xy_l |= MK(L, r2 + dy * W2 + dx);
+        for (int dx = -1; dx <= 1; ++dx) xy_l |= MK(L, r2 + dy * W2 + dx);
+    }
     act = xy_m1 | xy_0 | xy_l;  // the 3x3x3 neighbourhood of plane C
     xy_m1 = xy_0;
     xy_0 = xy_l;
@@ -362,7 +380,9 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     // A face flux reads cells inside the 3x3x3 neighbourhood of its cell in
     // plane C, so with no mixed neighbourhood in the plane every face of the
     // plane (and the z-face above it) is exactly zero.
-    if (!__syncthreads_or(pfC && mixed)) {
+    // (planes C-1, C and L all liquid: nothing mixes, and the CTA knows it
+    // without another barrier)
+    if ((liq_hist & 7u) == 7u || !__syncthreads_or(pfC && mixed)) {
 #pragma unroll
       for (int a = 0; a < NP; ++a) pfz_hi[a] = Real(0);
     } else {
@@ -575,17 +595,31 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     // D. solute fluxes of plane M and the update of the owned planes
     const bool doM = M >= z0 - 1 && M <= z0 + ZS - 1;
     const bool outM = doM && M >= z0 && M < nz;
+    // planes M-1 .. M+2 liquid: phi^{n+1} = phi^n = liquid on planes M and
+    // M+1, so h_l = 1, M = M0, no antitrapping, chi = 1 / (2 A_l), no obstacles
+    const bool lean_d = (liq_hist & 15u) == 15u;
     if (doM) {
       const int fzm = fold_axis(P, M, 2);
       const bool walls = has_walls;
       // flux between this cell (plane M) and neighbour nb: d normal axis
       auto mu_face = [&](int d, int pB, int nbT, int nbR, int gbd, bool obsB, Real* J) {
         bool closed = (P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d];
-        if (!closed && walls) closed = obstacle(P, fx, fy, fzm) || obsB;
+        if (!closed && walls && !lean_d) closed = obstacle(P, fx, fy, fzm) || obsB;
 #pragma unroll
         for (int i = 0; i < NC; ++i) J[i] = Real(0);
         if (closed) return;
         const int pA = M, A = tid, rA = r2;
+        if (lean_d) {
+          const Real ua = s_u[(slot2(pA) * 3 + d) * NT + A], ub = s_u[(slot2(pB) * 3 + d) * NT + nbT];
+          const int fzB = d == 2 ? fold_axis(P, pB, 2) : fzm;
+#pragma unroll
+          for (int i = 0; i < NC; ++i) {
+            const Real ma = s_mu[(slot2(pA) * NC + i) * NT + A], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
+            J[i] = -P.M0 * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fzm) + ma * P.inv2A[0]) +
+                                                    ub * (ceq_of(0, i, fzB) + mb * P.inv2A[0]));
+          }
+          return;
+        }
         const Real* pnA = s_pn + slot3(pA) * NP * NT;
         const Real* pnB = s_pn + slot3(pB) * NP * NT;
         const Real Mf = Real(0.5) * P.M0 * (pnA[A] + pnB[nbT]);  // plane 0 = liquid
@@ -637,7 +671,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       // z-face (M, M+1) of this column, for the carry
       {
         const int fzb = fold_axis(P, M + 1, 2);
-        mu_face(2, M + 1, tid, r2, M + 1, walls && obstacle(P, fx, fy, fzb), mz_hi);
+        mu_face(2, M + 1, tid, r2, M + 1, walls && !lean_d && obstacle(P, fx, fy, fzb), mz_hi);
       }
       if (M == z0 - 1) {
 #pragma unroll
@@ -646,13 +680,13 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         // in-plane faces of plane M
         Real J[NC];
         if (tx < BX - 1) {
-          const bool ob = walls && obstacle(P, fold_axis(P, gx + 1, 0), fy, fzm);
+          const bool ob = walls && !lean_d && obstacle(P, fold_axis(P, gx + 1, 0), fy, fzm);
           mu_face(0, M, tid + 1, r2 + 1, gx + 1, ob, J);
 #pragma unroll
           for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 0) * NT + tid] = J[i];
         }
         if (ty < BY - 1) {
-          const bool ob = walls && obstacle(P, fx, fold_axis(P, gy + 1, 1), fzm);
+          const bool ob = walls && !lean_d && obstacle(P, fx, fold_axis(P, gy + 1, 1), fzm);
           mu_face(1, M, tid + BX, r2 + W2, gy + 1, ob, J);
 #pragma unroll
           for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 1) * NT + tid] = J[i];
@@ -671,7 +705,23 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       }
 #pragma unroll
       for (int sidx = 0; sidx < NS; ++sidx) phi_out[sidx * P.plane + g] = pn[NP == 2 ? 1 : sidx];
-      if (has_walls && obstacle(P, fx, fy, fzm)) {
+      if (lean_d) {
+        // unchanged liquid cell: chi = 1 / (2 A_l); the source is the
+        // temperature term alone (extended model)
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          const Real* Jx = s_flux + (i * 2 + 0) * NT;
+          const Real* Jy = s_flux + (i * 2 + 1) * NT;
+          const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
+          const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
+          Real src = Real(0);
+          if constexpr (EXT) {
+#pragma unroll
+            for (int a = 0; a < NP; ++a) src -= Real(P.GV) * P.dceq_dT[a][i] * (a == 0 ? Real(1) : Real(0));
+          }
+          mu_out[i * P.plane + g] = mu + (-div - src) * P.chi_pure[0];
+        }
+      } else if (has_walls && obstacle(P, fx, fy, fzm)) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = s_mu[(slot2(M) * NC + i) * NT + tid];
       } else if (!EXT && s_chg[slot2(M) * NT + tid] == 0 && pure_phase<NP>(pn) >= 0) {
