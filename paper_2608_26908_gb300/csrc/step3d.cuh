@@ -172,6 +172,9 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   // Liquid planes: bit 0 = plane L, bit 1 = C, bit 2 = M, bit 3 = M - 1 is
   // set when every cell of that plane in R1 and its ring is pure liquid and
   // no cell of R1 is an obstacle (the whole CTA agrees: __syncthreads_and).
+  // The shrinkage variant keeps the general path everywhere (its registers
+  // are already spent on the deferred collision).
+  constexpr bool LIQ = !SHRINK;
   unsigned liq_hist = 0;
 
   // OR of the phase masks over the 3x3 in-plane neighbourhood of this
@@ -351,7 +354,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       }
       }  // !SHRINK
     }
-    liq_hist = ((liq_hist << 1) | (__syncthreads_and(liq_l) ? 1u : 0u)) & 15u;
+    if constexpr (LIQ)
+      liq_hist = ((liq_hist << 1) | (__syncthreads_and(liq_l) ? 1u : 0u)) & 15u;
+    else
+      __syncthreads();
 
     // C. phase field of plane C where phases mix
     const bool pfC = C >= z0 - 1 && C <= z0 + ZS;
