@@ -152,6 +152,11 @@ struct DevParams {
   int tdep;            // 1 if any of them is nonzero
 };
 
+// 1/x rounded to nearest: the same value as the IEEE division 1/x, by the
+// correctly rounded reciprocal instead of the division routine.
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+
 template <class Real>
 __device__ __forceinline__ int fold_axis(const DevParams<Real>& P, int i, int a) {
   const int n = P.n[a];
@@ -534,7 +539,7 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
     for (int i = 0; i < NC; ++i)
       drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * theta + mu[i] * P.inv2A[0]);
     const Real FB = rho * phil * drive;
-    const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
+    const Real inv = rcp_rn(rho * (Real(1) + Real(0.5) * kappa));
 #pragma unroll
     for (int a = 0; a < D; ++a) o_u[a * cells + x] = Out((m[a] + (a == D - 1 ? Real(0.5) * FB : Real(0))) * inv);
   }

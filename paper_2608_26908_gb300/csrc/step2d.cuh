@@ -132,15 +132,8 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   Real ph[NP];
   load_phases<NP>(phi_in, g, P.plane, ph);
   bool liquid = pure_liquid(ph) && !obs;  // the tile's cells, for the liquid-tile path
-  {
-    unsigned m = 0;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      s_phi[a * C2 + r2] = ph[a];
-      if (ph[a] > Real(0)) m |= 1u << a;
-    }
-    s_mask[r2] = (unsigned char)m;
-  }
+  int rr = 0;  // the ring cell of threads tid < RING (R1-plus-ring index) and its phases
+  Real rv[NP];
   if (tid < S::RING) {
     int rx, ry;
     if (tid < W2) {
@@ -158,17 +151,30 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     }
     const int qx = inner_tile ? x0 - 2 + rx : fold_axis(P, x0 - 2 + rx, 0);
     const int qy = inner_tile ? y0 - 2 + ry : fold_axis(P, y0 - 2 + ry, 1);
-    Real v[NP];
-    load_phases<NP>(phi_in, qy * px + qx, P.plane, v);
-    liquid = liquid && pure_liquid(v);
+    rr = ry * W2 + rx;
+    load_phases<NP>(phi_in, qy * px + qx, P.plane, rv);
+    liquid = liquid && pure_liquid(rv);
+  }
+  // phi^n and the phases present, in shared memory for the phase-field
+  // stencil (the general path only)
+  auto stage_phi = [&]() {
     unsigned m = 0;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
-      s_phi[a * C2 + ry * W2 + rx] = v[a];
-      if (v[a] > Real(0)) m |= 1u << a;
+      s_phi[a * C2 + r2] = ph[a];
+      if (ph[a] > Real(0)) m |= 1u << a;
     }
-    s_mask[ry * W2 + rx] = (unsigned char)m;
-  }
+    s_mask[r2] = (unsigned char)m;
+    if (tid < S::RING) {
+      m = 0;
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        s_phi[a * C2 + rr] = rv[a];
+        if (rv[a] > Real(0)) m |= 1u << a;
+      }
+      s_mask[rr] = (unsigned char)m;
+    }
+  };
   Real mu[NC];
 #pragma unroll
   for (int i = 0; i < NC; ++i) {
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
         drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
     }
     const Real FB = rho * phil * drive;
-    const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
+    const Real inv = rcp_rn(rho * (Real(1) + Real(0.5) * kappa));
     Real ux, uy, Fx, Fy;
     if constexpr (SHRINK) {
       ux = (mx + Real(0.5) * fsx) * inv;
@@ -303,6 +309,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     pull_f();
     return;
   }
+
+  stage_phi();
+  __syncthreads();
 
   // 1. phase field where phases mix
   unsigned act = 0;
@@ -573,7 +582,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
       ho[a] = changed ? interp_h<NP>(ph, a) : hn[a];
       chi += hn[a] * P.inv2A[a];
     }
-    const Real ichi = Real(1) / chi;
+    const Real ichi = rcp_rn(chi);
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
       const Real* Ji = s_flux + i * 2 * NT;

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
           drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
       }
       const Real FB = rho * phl * drive;
-      const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
+      const Real inv = rcp_rn(rho * (Real(1) + Real(0.5) * kappa));
       Real u[3], F[3];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
             drive += P.gbeta_c[i] * (P.dcl_ref[i] + mc * P.inv2A[0]);
         }
         const Real FB = rho * phl * drive;
-        const Real inv = Real(1) / (rho * (Real(1) + Real(0.5) * kappa));
+        const Real inv = rcp_rn(rho * (Real(1) + Real(0.5) * kappa));
         Real u[3], F[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
           ho[a] = changed ? interp_h<NP>(po, a) : hn[a];
           chi += hn[a] * P.inv2A[a];
         }
-        const Real ichi = Real(1) / chi;
+        const Real ichi = rcp_rn(chi);
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
           const Real* Jx = s_flux + (i * 2 + 0) * NT;
