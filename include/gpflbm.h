@@ -153,7 +153,10 @@ gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params);
  * full populations, or NULL for the fluid at rest (f_k = w_k).
  * src_is_device: 1 if the pointers are device memory, 0 for host memory
  * (pageable or pinned).  The library copies; the caller keeps ownership.
- * Sets the step counter to t0.  Host sources are read before return. */
+ * Pinned or registered host buffers (all three of them) are read in place by
+ * the load kernels over the host link; pageable ones are staged through the
+ * workspace plane by plane.  Sets the step counter to t0.  Host sources are
+ * read before return. */
 gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, const void* f,
                                int src_is_device, long long t0, void* stream);
 
@@ -186,7 +189,9 @@ gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream);
 /* Copy fields of the current state out.  field_mask is an OR of
  * GPFLBM_FIELD_*; dst holds one pointer per set bit, in increasing bit
  * order, each large enough for that field's planes.  dst_is_device as in
- * set_state.  For host destinations the call synchronises `stream`. */
+ * set_state.  Device and pinned host destinations are written by one
+ * kernel launch; pageable host destinations are staged field by field.  For
+ * host destinations the call synchronises `stream`. */
 gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* dst,
                                 int dst_is_device, void* stream);
 

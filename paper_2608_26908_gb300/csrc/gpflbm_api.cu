@@ -321,6 +321,24 @@ gpflbm::StepIO step_io(gpflbm_t h, int from) {
   return io;
 }
 
+// The device address of a host buffer the GPU can read and write directly:
+// pinned or registered host memory, mapped into the device's address space
+// (over NVLink-C2C on a Grace-Blackwell node the kernels stream it at link
+// speed).  nullptr for pageable memory, which has to be staged.
+void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer is not an error here
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+__global__ void set_clock_kernel(double* clock, double t) {
+  clock[0] = t;
+  clock[1] = t;
+}
+
 void drop_graphs(gpflbm_t h) {
   for (int i = 0; i < 2; ++i) {
     if (h->chunk_graph[i]) cudaGraphExecDestroy(h->chunk_graph[i]);
@@ -469,7 +487,21 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   void* mu_d = at(h, h->lay.mu[h->cur]);
   void* f_d = at(h, h->lay.f[h->cur]);
   cudaError_t e;
+  bool staged = false;
   if (!src_is_device) {
+    // pinned host sources are read by the load kernels in place
+    void* mp = mapped_host(phi);
+    void* mm = mapped_host(mu);
+    void* mf = f ? mapped_host(f) : nullptr;
+    if (mp && mm && (!f || mf)) {
+      sp = mp;
+      sm = mm;
+      sf = mf;
+    } else {
+      staged = true;
+    }
+  }
+  if (staged) {
     // stage through the idle buffers: phi in the stage area, mu in the idle
     // mu buffer, f in the stage area after phi has been converted
     unsigned char* stage = static_cast<unsigned char*>(at(h, h->lay.stage));
@@ -491,12 +523,12 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   // (the load launcher always rewrites f: from sf, or the fluid at rest)
   e = h->ops->load(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
-  double tt[2] = {(double)t0, (double)t0};
-  e = cudaMemcpyAsync(at(h, h->lay.clock), tt, sizeof(tt), cudaMemcpyHostToDevice, s);
+  set_clock_kernel<<<1, 1, 0, s>>>(reinterpret_cast<double*>(at(h, h->lay.clock)), (double)t0);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state: clock");
   e = cudaMemsetAsync(at(h, h->lay.err), 0, sizeof(int), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state: error word");
-  e = cudaStreamSynchronize(s);  // host sources (and tt) must outlive the copies
+  e = cudaStreamSynchronize(s);  // host sources must outlive the copies and loads
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state: synchronize");
   h->t = t0;
   h->has_state = true;
@@ -614,28 +646,52 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
   const size_t rs = h->ops->real_size;
   const size_t n = (size_t)h->cells;
   const int planes[6] = {h->NP, h->NC, h->NC, h->Q, 1, h->D};
+  gpflbm::FieldsIO base;
+  std::memset(&base, 0, sizeof(base));
+  base.phi = at(h, h->lay.phi[h->cur]);
+  base.mu = at(h, h->lay.mu[h->cur]);
+  base.f = at(h, h->lay.f[h->cur]);
+  base.clock = reinterpret_cast<const double*>(at(h, h->lay.clock)) + h->cur;
+  // device and pinned host destinations are written by one launch; pageable
+  // host destinations go through the stage area one field at a time
+  gpflbm::FieldsIO direct = base;
+  void** outs_direct[6] = {&direct.o_phi, &direct.o_mu, &direct.o_c, &direct.o_f, &direct.o_rho, &direct.o_u};
+  void* staged_dst[6] = {};
+  bool any_direct = false;
   int slot = 0;
   for (int bit = 0; bit < 6; ++bit) {
     if (!(field_mask & (1u << bit))) continue;
     void* d = dst[slot++];
     if (!d) return fail(h, GPFLBM_ERR_ARG, "get_fields: a destination is NULL");
-    void* target = dst_is_device ? d : at(h, h->lay.stage);
-    gpflbm::FieldsIO io;
-    std::memset(&io, 0, sizeof(io));
-    io.phi = at(h, h->lay.phi[h->cur]);
-    io.mu = at(h, h->lay.mu[h->cur]);
-    io.f = at(h, h->lay.f[h->cur]);
-    io.clock = reinterpret_cast<const double*>(at(h, h->lay.clock)) + h->cur;
+    void* m = dst_is_device ? d : mapped_host(d);
+    if (m) {
+      *outs_direct[bit] = m;
+      any_direct = true;
+    } else {
+      staged_dst[bit] = d;
+    }
+  }
+  cudaError_t e;
+  if (any_direct) {
+    e = h->ops->fields(dev_params(h), direct, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: kernel");
+  }
+  for (int bit = 0; bit < 6; ++bit) {
+    if (!staged_dst[bit]) continue;
+    void* target = at(h, h->lay.stage);
+    gpflbm::FieldsIO io = base;
     void** outs[6] = {&io.o_phi, &io.o_mu, &io.o_c, &io.o_f, &io.o_rho, &io.o_u};
     *outs[bit] = target;
-    cudaError_t e = h->ops->fields(dev_params(h), io, s);
+    e = h->ops->fields(dev_params(h), io, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: kernel");
-    if (!dst_is_device) {
-      e = cudaMemcpyAsync(d, target, planes[bit] * n * rs, cudaMemcpyDeviceToHost, s);
-      if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: copy");
-      e = cudaStreamSynchronize(s);  // the stage area is reused by the next field
-      if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: synchronize");
-    }
+    e = cudaMemcpyAsync(staged_dst[bit], target, planes[bit] * n * rs, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: copy");
+    e = cudaStreamSynchronize(s);  // the stage area is reused by the next field
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: synchronize");
+  }
+  if (!dst_is_device) {
+    e = cudaStreamSynchronize(s);  // host destinations are complete on return
+    if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: synchronize");
   }
   return GPFLBM_OK;
 }
