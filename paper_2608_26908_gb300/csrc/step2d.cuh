@@ -29,14 +29,17 @@ namespace gpflbm {
 template <class Real>
 struct Block2D;
 // MIN_CTAS: resident CTAs per SM the register budget is cut for (FP32: three,
-// 40 registers a thread, 48 warps; FP64 needs twice the shared memory).
+// 40 registers a thread, 48 warps; FP64: four CTAs of 256 threads, 64
+// registers).
 template <>
 struct Block2D<float> {
   static constexpr int BX = 32, BY = 16, MIN_CTAS = 3;
 };
 template <>
 struct Block2D<double> {
-  static constexpr int BX = 32, BY = 16, MIN_CTAS = 2;
+  // half-height tiles: FP64 arithmetic is slow on this part, and the small
+  // FP64 grids need the CTAs spread over every SM
+  static constexpr int BX = 32, BY = 8, MIN_CTAS = 4;
 };
 
 template <int NP, int NC, class Real, class Store>
