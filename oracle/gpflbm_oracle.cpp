@@ -111,8 +111,28 @@ inline Dual exp(Dual a) {
   double e = std::exp(a.v);
   return Dual(e, e * a.d);
 }
+// Counting number: a double whose +, -, *, /, sqrt and exp each add one to
+// a global tally (the floating-point operations of the method, counted by
+// running the same templated steps on it; single-threaded).
+long long g_flops = 0;
+struct Cnt {
+  double v;
+  Cnt(double a = 0.0) : v(a) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v / b.v); }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+inline Cnt& operator*=(Cnt& a, Cnt b) { a = a * b; return a; }
+inline Cnt sqrt(Cnt a) { ++g_flops; return Cnt(std::sqrt(a.v)); }
+inline Cnt exp(Cnt a) { ++g_flops; return Cnt(std::exp(a.v)); }
+
 inline double val(double x) { return x; }
 inline double val(const Dual& x) { return x.v; }
+inline double val(const Cnt& x) { return x.v; }
 using std::exp;
 using std::sqrt;
 
@@ -1003,6 +1023,53 @@ int oracle_objective_value(const OracleProblem* p, const OracleObjective* o, con
   State<double> s;
   s.phi.assign(phi, phi + (long)p->n_phases * g.cells);
   *J = objective(g, o, s);
+  return 0;
+}
+
+// Floating-point operations of n_steps steps from the given state, by stage
+// (out[0] phase field, out[1] moments and forces, out[2] chemical potential,
+// out[3] lattice Boltzmann): the same steps as oracle_run on the counting
+// number type, with one thread so that the tally is exact.
+int oracle_count_flops(const OracleProblem* p, long n0, int n_steps, const double* phi,
+                       const double* mu, const double* f, double* out) {
+  if (check(p)) return -1;
+  Grid g(p);
+  Lattice L = make_lattice(p->q);
+  Coeffs<Cnt> k = plain_coeffs<Cnt>(p);
+  State<Cnt> s;
+  s.phi.assign(phi, phi + (long)p->n_phases * g.cells);
+  s.mu.assign(mu, mu + (long)p->n_solutes * g.cells);
+  s.f.assign(f, f + (long)L.q * g.cells);
+#ifdef _OPENMP
+  const int threads = omp_get_max_threads();
+  omp_set_num_threads(1);
+#endif
+  for (int j = 0; j < 4; ++j) out[j] = 0.0;
+  for (int n = 0; n < n_steps; ++n) {
+    const double t = (double)(n0 + n);
+    std::vector<Cnt> phi_new((long)p->n_phases * g.cells), mu_new((long)p->n_solutes * g.cells),
+        f_new((long)L.q * g.cells);
+    Macro<Cnt> m;
+    long long c0 = g_flops;
+    phase_field_update(g, k, s, t, phi_new);
+    long long c1 = g_flops;
+    macroscopic(g, L, k, s, &phi_new, t, m);
+    long long c2 = g_flops;
+    chemical_potential_update(g, s, phi_new, m, t, mu_new);
+    long long c3 = g_flops;
+    lattice_boltzmann_update(g, L, s, m, f_new);
+    long long c4 = g_flops;
+    out[0] += (double)(c1 - c0);
+    out[1] += (double)(c2 - c1);
+    out[2] += (double)(c3 - c2);
+    out[3] += (double)(c4 - c3);
+    s.phi.swap(phi_new);
+    s.mu.swap(mu_new);
+    s.f.swap(f_new);
+  }
+#ifdef _OPENMP
+  omp_set_num_threads(threads);
+#endif
   return 0;
 }
 

@@ -77,6 +77,7 @@ def lib():
         O = ctypes.POINTER(OracleObjective)
         L.oracle_run.argtypes = [P, ctypes.c_long, ctypes.c_int, dp, dp, dp]
         L.oracle_shift_frame.argtypes = [P, ctypes.c_int, dp, dp, dp]
+        L.oracle_count_flops.argtypes = [P, ctypes.c_long, ctypes.c_int, dp, dp, dp, dp]
         L.oracle_derived.argtypes = [P, ctypes.c_long, dp, dp, dp, dp, dp, dp]
         L.oracle_invariants.argtypes = [P, ctypes.c_long, dp, dp, dp, dp]
         L.oracle_objective.argtypes = [P, O, ctypes.c_long, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
@@ -175,6 +176,26 @@ def run(sc, phi, mu, f, n_steps, n0=0):
     if rc != 0:
         raise ValueError("oracle_run rejected the problem")
     return phi, mu, f
+
+
+def count_flops(sc, phi, mu, f, n_steps=1, n0=0):
+    """Floating-point operations per cell-update of the method (the oracle's
+    own steps on a counting number type), by stage: dict of phase_field,
+    macroscopic, chemical_potential, lattice_boltzmann and total."""
+    p = problem(sc)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(4)
+    if lib().oracle_count_flops(ctypes.byref(p), int(n0), int(n_steps), _dp(phi), _dp(mu), _dp(f),
+                                _dp(out)) != 0:
+        raise ValueError("oracle_count_flops rejected the problem")
+    cells = p.nx * p.ny * (p.nz if p.dim == 3 else 1)
+    per = out / float(cells * n_steps)
+    names = ("phase_field", "macroscopic", "chemical_potential", "lattice_boltzmann")
+    d = dict(zip(names, per))
+    d["total"] = float(per.sum())
+    return d
 
 
 def shift_frame(sc, phi, mu, f, rows):

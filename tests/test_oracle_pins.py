@@ -945,3 +945,23 @@ def test_3d_shear_wave_decays_at_the_bgk_viscosity(q):
     r16, r32 = rate(16), rate(32)
     assert abs(r32 - 1) < 3e-3
     assert abs(r16 - 1) / abs(r32 - 1) > 3.0  # second order in k
+
+
+# ----------------------------------------------------------------- flop counter
+def test_flop_counter_is_per_cell_and_per_step():
+    """The instrumented oracle (the same steps on a counting number type):
+    on a uniform liquid box every cell does the same work, so the count per
+    cell-update does not depend on the grid size or the number of steps, and
+    the stages add up to the total."""
+    counts = []
+    for n, steps in ((8, 1), (16, 1), (16, 3)):
+        sc, phi, mu = _liquid_box(n, n, bc=(0, 0, 0))
+        f = oracle.rest_populations(sc)
+        d = oracle.count_flops(sc, phi, mu, f, steps)
+        parts = d["phase_field"] + d["macroscopic"] + d["chemical_potential"] + d["lattice_boltzmann"]
+        assert d["total"] == pytest.approx(parts, rel=1e-15)
+        counts.append(d)
+    for d in counts[1:]:
+        for k in d:
+            assert d[k] == pytest.approx(counts[0][k], rel=1e-15), k
+    assert counts[0]["lattice_boltzmann"] > 100 and counts[0]["phase_field"] > 0
