@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   Real ph[NP];
   load_phases<NP>(phi_in, g, P.plane, ph);
   bool liquid = pure_liquid(ph) && !obs;  // the tile's cells, for the liquid-tile path
-  int rr = 0;  // the ring cell of threads tid < RING (R1-plus-ring index) and its phases
-  Real rv[NP];
-  if (tid < S::RING) {
+  // the ring cell of a thread tid < RING: its R1-plus-ring index rr and its
+  // offset in a plane
+  auto ring_cell = [&](int& rr) {
     int rx, ry;
     if (tid < W2) {
       rx = tid;
@@ -155,11 +155,17 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     const int qx = inner_tile ? x0 - 2 + rx : fold_axis(P, x0 - 2 + rx, 0);
     const int qy = inner_tile ? y0 - 2 + ry : fold_axis(P, y0 - 2 + ry, 1);
     rr = ry * W2 + rx;
-    load_phases<NP>(phi_in, qy * px + qx, P.plane, rv);
+    return qy * px + qx;
+  };
+  if (tid < S::RING) {
+    int rr;
+    Real rv[NP];
+    load_phases<NP>(phi_in, ring_cell(rr), P.plane, rv);
     liquid = liquid && pure_liquid(rv);
   }
   // phi^n and the phases present, in shared memory for the phase-field
-  // stencil (the general path only)
+  // stencil (the general path only; the ring is read again here rather than
+  // held in registers through the collision)
   auto stage_phi = [&]() {
     unsigned m = 0;
 #pragma unroll
@@ -169,6 +175,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     }
     s_mask[r2] = (unsigned char)m;
     if (tid < S::RING) {
+      int rr;
+      Real rv[NP];
+      load_phases<NP>(phi_in, ring_cell(rr), P.plane, rv);
       m = 0;
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
