@@ -147,6 +147,24 @@ def test_3d_workloads_full_size_fp32(name, steps):
         assert e <= TOL["fp32"], (k, e)
 
 
+@pytest.mark.parametrize("name,size,prec", [
+    ("dendrite3d", dict(nx=64, ny=64, nz=64), "fp32"),
+    ("dendrite3d", dict(nx=64, ny=64, nz=64), "fp32_f16"),
+    ("dendrite3d", dict(nx=64, ny=64, nz=64), "fp32_bf16"),
+    ("eutectic3d", dict(nx=64, ny=64, nz=128), "fp32"),
+])
+def test_parity_on_the_stated_3d_crops(name, size, prec):
+    """The 3D dendrite on a 64^3 crop (FP32 and both 16-bit storages) and the
+    ternary eutectic on a 64 x 64 x 128 crop, 100 steps."""
+    sc = inputs.scenario(name, precision=prec, **size)
+    errs, sim, got, ref = errors(sc, 100)
+    _report(name + "-crop", prec, errs)
+    for k, e in errs.items():
+        if k == "dev" and prec.startswith("fp32_"):
+            continue  # stored populations are rounded to 16 bits
+        assert e <= TOL[prec], (k, e)
+
+
 def test_fp64_dendrite_full_horizon():
     """The FP64 configuration (2D dendrite, 128^2) over its whole 1000-step
     horizon, in one graph-replayed call."""
