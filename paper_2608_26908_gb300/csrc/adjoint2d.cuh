@@ -73,6 +73,20 @@ __device__ __forceinline__ Tan<Real> dAdq_tan(const Tan<Real>* q, Tan<Real> delt
   return Tan<Real>(Real(2)) * ac * (ac * qj + s2 * dac);
 }
 
+// dA/dq_j with the crystal axes turned by theta about z (c = cos, s = sin):
+// A of the crystal-frame components r = (c q_x + s q_y, -s q_x + c q_y),
+// dA/dq = (c r'_x - s r'_y, s r'_x + c r'_y), r' = dA/dr (as the forward)
+template <class Real>
+__device__ __forceinline__ Tan<Real> dAdq_tan_tilted(const Tan<Real>* q, Tan<Real> delta, Real c, Real s,
+                                                     Real q_floor, int j) {
+  const Tan<Real> C(c), S(s);
+  Tan<Real> r[2];
+  r[0] = C * q[0] + S * q[1];
+  r[1] = C * q[1] - S * q[0];
+  const Tan<Real> a0 = dAdq_tan<Real>(r, delta, q_floor, 0), a1 = dAdq_tan<Real>(r, delta, q_floor, 1);
+  return j == 0 ? C * a0 - S * a1 : S * a0 + C * a1;
+}
+
 // H(s) = s^2 (3 - 2 s) and H'(s) = 6 s (1 - s): h_1 for two phases
 template <class Real>
 __device__ __forceinline__ Real Hs(Real s) { return s * s * (Real(3) - Real(2) * s); }
@@ -478,7 +492,8 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
             q[d] = Tan<Real>(g_n, j == 0 ? Real(1) : Real(0));
             q[1 - d] = Tan<Real>(g_t, j == 1 ? Real(1) : Real(0));
             const Tan<Real> dl(P.delta[0][1], j == 2 ? Real(1) : Real(0));
-            dV[j] = dAdq_tan<Real>(q, dl, P.q_floor, d).d;
+            dV[j] = P.tilted ? dAdq_tan_tilted<Real>(q, dl, P.tilt_c[0][1], P.tilt_s[0][1], P.q_floor, d).d
+                             : dAdq_tan<Real>(q, dl, P.q_floor, d).d;
           }
           cn = lV * dV[0];
           ct = Real(0.25) * lV * dV[1];

@@ -915,10 +915,10 @@ AdjLayout adj_layout(gpflbm_t h, int H, int K) {
 gpflbm_status adj_check(gpflbm_t h, int H, int K) {
   const int prec = h->grid.precision;
   if (h->D != 2 || h->NP != 2 || h->NC != 1 || (prec != GPFLBM_FP64 && prec != GPFLBM_FP32) ||
-      h->pf.shrink || h->pd.shrink || h->pf.tilted || h->pf.tdep)
+      h->pf.shrink || h->pd.shrink || h->pf.tdep)
     return fail(h, GPFLBM_ERR_UNSUPPORTED,
-                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage, "
-                "tilted crystal axes or temperature-dependent ceq");
+                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage "
+                "or temperature-dependent ceq");
   if (H < 1 || K < 1) return fail(h, GPFLBM_ERR_ARG, "adjoint: need horizon >= 1 and ckpt_every >= 1");
   return GPFLBM_OK;
 }
@@ -979,7 +979,7 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     io.clock_in = forward_pass ? fw_clk(c, j) : clk_at(c, j);
     io.clock_out = forward_pass ? fw_clk(c, j + 1) : clk_at(c, j + 1);
     io.err = err;
-    return h->ops->step(P, io, st);
+    return stepper(h)->step(P, io, st);
   };
   // copies of one stored state: handle -> slot, or slot -> handle
   auto copy_state = [&](unsigned char* slot, double* slot_clk, bool to_slot) {

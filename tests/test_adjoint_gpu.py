@@ -18,10 +18,12 @@ from paper_2608_26908_gb300 import gpflbm, inputs
 pytestmark = pytest.mark.gpu
 
 
-def _case(nx, ny, prec):
+def _case(nx, ny, prec, tilt=0.0):
     sc = inputs.scenario("adjoint2d", nx=nx, ny=ny, precision=prec)
     sc["init"]["radius"] = 6.0
     sc["params"]["gbeta_c"] = [2e-3, 0.0]  # a flow strong enough to matter
+    if tilt:
+        sc["params"]["tilt"][0][1] = sc["params"]["tilt"][1][0] = tilt
     return sc
 
 
@@ -49,11 +51,12 @@ def _close(a, b, rtol, scale):
     return abs(a - b) <= rtol * max(abs(b), scale)
 
 
+@pytest.mark.parametrize("tilt", [0.0, 0.35])
 @pytest.mark.parametrize("prec,rtol", [("fp64", 1e-8), ("fp32", 2e-4)])
-def test_adjoint_matches_oracle_dual_derivatives(prec, rtol):
+def test_adjoint_matches_oracle_dual_derivatives(prec, rtol, tilt):
     """40 x 36 (ragged against 256-thread blocks), 23 steps, K = 5: four
-    full segments and a ragged one."""
-    sc = _case(40, 36, prec)
+    full segments and a ragged one; axis-aligned and tilted crystal axes."""
+    sc = _case(40, 36, prec, tilt)
     H, K = 23, 5
     _, J, dpar, dmu = _gpu_adjoint(sc, H, K)
     rng = np.random.default_rng(11)

@@ -76,13 +76,3 @@ def test_tilt_turns_the_growth_and_a_quarter_turn_does_not():
     quarter = _phi_after(_case("dendrite2d", {}, "fp64", theta=math.pi / 2), 60)
     assert np.abs(turned - base).max() > 1e-6
     assert np.abs(quarter - base).max() < 1e-12
-
-
-def test_adjoint_rejects_tilt():
-    sc = _case("adjoint2d", dict(nx=40, ny=36), "fp32")
-    sim = gpflbm.Sim(sc)
-    sim.set_state(*inputs.initial_state(sc))
-    obj = {"w_frac": 1.0, "w_tip": 0.0, "kappa": 1.0, "x0": 20, "y0": 18}
-    with pytest.raises(gpflbm.GpflbmError) as e:
-        sim.adjoint(obj, 4, 2)
-    assert e.value.status == gpflbm.ERR_UNSUPPORTED
