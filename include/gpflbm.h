@@ -263,8 +263,8 @@ gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_e
  * recomputed from its checkpoint on a second stream (the library's own).
  * Cost: H + (ceil(H/K) - 1)(K - 1) forward steps plus H adjoint steps.
  * Supported: 2D, D2Q9, two phases, one solute, GPFLBM_FP64 or GPFLBM_FP32,
- * no shrinkage (eta_rho all 0), ceq independent of T (dceq_dT all 0); tilted crystal
- * axes are supported.  Anything else: GPFLBM_ERR_UNSUPPORTED.
+ * no shrinkage (eta_rho all 0); tilted crystal axes and temperature-dependent ceq are
+ * supported.  Anything else: GPFLBM_ERR_UNSUPPORTED.
  * Outputs (each may be NULL): *J; dparams[0] = dJ/d(1/tau_phi),
  * dparams[1] = dJ/d delta_01, dparams[2] = dJ/d gbeta_c[0] (FP64,
  * accumulated per cell in FP64 and summed in a fixed order); dmu0 =

@@ -127,7 +127,9 @@ __device__ __forceinline__ Macro2<Real> macro2(const DevParams<Real>& P, const R
   m.phil = obs ? Real(0) : Real(1) - s;
   const Real sl = Real(1) - m.phil;
   m.kappa = P.kappa0 * sl * sl;
-  m.B = P.gbeta_T * (theta + P.dT_ref) + P.gbeta_c[0] * (P.dcl_ref[0] + mu * P.inv2A[0]);
+  // c_l - c_ref with ceq_l(T) = ceq_l + dceq_dT (T - T_E)
+  m.B = P.gbeta_T * (theta + P.dT_ref) +
+        P.gbeta_c[0] * (P.dcl_ref[0] + P.dceq_dT[0][0] * theta + mu * P.inv2A[0]);
   m.FB = m.rho * m.phil * m.B;
   m.iv = Real(1) / (m.rho * (Real(1) + Real(0.5) * m.kappa));
   m.ux = m.mx * m.iv;
@@ -293,7 +295,17 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
       cf[S::F_SPB] = dM;
       // advection 1/2 [U_d h0' c0(mu)]_a + [..]_b with h0' = 1 - H(s')
       const Real h0a = Real(1) - Hs(s1a), h0b = Real(1) - Hs(s1b);
-      const Real c0a = P.ceq[0][0] + mua * P.inv2A[0], c0b = P.ceq[0][0] + mub * P.inv2A[0];
+      // T - T_E of cells a and b (vertical index folded as the loads were),
+      // needed only when ceq depends on T
+      Real tha = Real(0), thb = Real(0);
+      if (P.tdep) {
+        const int ya = inner_tile ? y0 - 2 + ja : fold_axis(P, y0 - 2 + ja, 1);
+        const int yb = d == 1 ? (inner_tile ? ya + 1 : fold_axis(P, y0 - 1 + ja, 1)) : ya;
+        tha = theta_base + P.G * Real(ya);
+        thb = theta_base + P.G * Real(yb);
+      }
+      const Real c0a = P.ceq[0][0] + P.dceq_dT[0][0] * tha + mua * P.inv2A[0];
+      const Real c0b = P.ceq[0][0] + P.dceq_dT[0][0] * thb + mub * P.inv2A[0];
       cf[S::F_UA] = L * Real(0.5) * h0a * c0a;
       cf[S::F_UB] = L * Real(0.5) * h0b * c0b;
       cf[S::F_MUA] += L * Real(0.5) * ua * h0a * P.inv2A[0];
@@ -311,7 +323,9 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
           const Real nd = g_n * rg;
           const Real liq = Real(1) - Real(0.5) * (s0a + s0b);
           const Real dinv = P.inv2A[0] - P.inv2A[1];
-          const Real dc = (P.ceq[0][0] - P.ceq[1][0]) + Real(0.5) * (mua + mub) * dinv;
+          const Real dc = (P.ceq[0][0] - P.ceq[1][0]) +
+                          (P.dceq_dT[0][0] - P.dceq_dT[1][0]) * Real(0.5) * (tha + thb) +
+                          Real(0.5) * (mua + mub) * dinv;
           const Real dphi = Real(0.5) * ((s1a - s0a) + (s1b - s0b));
           const Real k = -P.at_eps * L;
           const Real jl = k * dc * dphi * nd;   // d / d liq
@@ -348,10 +362,13 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
   Real ls = Real(0);
   const Real mu1 = __ldg(io.mu1 + o);
   if (!obs) {
-    // mu' = mu + (-div J - src) / chi', src = (c1 - c0)(mu) (H(s') - H(s))
-    const Real c10 = (P.ceq[1][0] - P.ceq[0][0]) + mu0 * e;
+    // mu' = mu + (-div J - src) / chi', src = (c1 - c0)(mu, T) (H(s') - H(s))
+    //   - (dT/dt) (dceq_0/dT (1 - H(s')) + dceq_1/dT H(s')),  dT/dt = -G V
+    const Real th = theta_base + P.G * Real(fy);
+    const Real c10 = (P.ceq[1][0] - P.ceq[0][0]) + (P.dceq_dT[1][0] - P.dceq_dT[0][0]) * th + mu0 * e;
     lmu -= Aown * e * (Hs(s1) - Hs(s0));
     lsp += -Aown * c10 * dHs(s1) - Aown * (mu1 - mu0) * e * dHs(s1);
+    lsp += Aown * Real(P.GV) * (P.dceq_dT[1][0] - P.dceq_dT[0][0]) * dHs(s1);
     ls += Aown * c10 * dHs(s0);
   }
   bool multi = false;
@@ -447,14 +464,16 @@ __global__ void __launch_bounds__(Adj2D<Real>::NT, Adj2D<Real>::MIN_CTAS) adj2d_
       io.ld0[k * plane + o] = omega * a[k] + gr + Real(Lat::c(k, 0)) * gmx + Real(Lat::c(k, 1)) * gmy;
     if (!obs) ls -= gphil;  // phil = 1 - s
     lmu += gB * P.gbeta_c[0] * P.inv2A[0];
-    io.gacc[2 * plane + o] += (double)(gB * (P.dcl_ref[0] + mu0 * P.inv2A[0]));
+    io.gacc[2 * plane + o] +=
+        (double)(gB * (P.dcl_ref[0] + P.dceq_dT[0][0] * (theta_base + P.G * Real(fy)) + mu0 * P.inv2A[0]));
 
     // phase field: s' = clamp(u) where both phases are present, s' = s elsewhere
     if (multi) {
       if (lu != Real(0)) {
-        const Real dpsi = -mu0 * mu0 * (P.inv4A[1] - P.inv4A[0]) - mu0 * (P.ceq[1][0] - P.ceq[0][0]) +
-                          (P.S[1] - P.S[0]) * (theta_base + P.G * Real(fy));
-        const Real dpsi_dmu = -mu0 * e - (P.ceq[1][0] - P.ceq[0][0]);
+        const Real thc = theta_base + P.G * Real(fy);
+        const Real dceq = (P.ceq[1][0] - P.ceq[0][0]) + (P.dceq_dT[1][0] - P.dceq_dT[0][0]) * thc;
+        const Real dpsi = -mu0 * mu0 * (P.inv4A[1] - P.inv4A[0]) - mu0 * dceq + (P.S[1] - P.S[0]) * thc;
+        const Real dpsi_dmu = -mu0 * e - dceq;
         const Real cob = P.obst * P.gamma[0][1] / P.eps;  // 16 gamma / (pi^2 eps^2)
         ls += lu * (Real(1) + Real(0.5) * mob * (Real(2) * cob - (Real(6) / P.eps) * (Real(1) - Real(2) * s0) * dpsi));
         lmu += lu * Real(0.5) * mob * (-(Real(6) / P.eps) * s0 * (Real(1) - s0) * dpsi_dmu);

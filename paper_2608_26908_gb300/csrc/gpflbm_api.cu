@@ -915,10 +915,9 @@ AdjLayout adj_layout(gpflbm_t h, int H, int K) {
 gpflbm_status adj_check(gpflbm_t h, int H, int K) {
   const int prec = h->grid.precision;
   if (h->D != 2 || h->NP != 2 || h->NC != 1 || (prec != GPFLBM_FP64 && prec != GPFLBM_FP32) ||
-      h->pf.shrink || h->pd.shrink || h->pf.tdep)
+      h->pf.shrink || h->pd.shrink)
     return fail(h, GPFLBM_ERR_UNSUPPORTED,
-                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage "
-                "or temperature-dependent ceq");
+                "adjoint: built for 2D, two phases, one solute, in FP64 or FP32, without shrinkage");
   if (H < 1 || K < 1) return fail(h, GPFLBM_ERR_ARG, "adjoint: need horizon >= 1 and ckpt_every >= 1");
   return GPFLBM_OK;
 }

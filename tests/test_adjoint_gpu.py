@@ -18,12 +18,16 @@ from paper_2608_26908_gb300 import gpflbm, inputs
 pytestmark = pytest.mark.gpu
 
 
-def _case(nx, ny, prec, tilt=0.0):
+def _case(nx, ny, prec, ext="plain"):
     sc = inputs.scenario("adjoint2d", nx=nx, ny=ny, precision=prec)
     sc["init"]["radius"] = 6.0
-    sc["params"]["gbeta_c"] = [2e-3, 0.0]  # a flow strong enough to matter
-    if tilt:
-        sc["params"]["tilt"][0][1] = sc["params"]["tilt"][1][0] = tilt
+    pr = sc["params"]
+    pr["gbeta_c"] = [2e-3, 0.0]  # a flow strong enough to matter
+    if ext == "tilt":
+        pr["tilt"][0][1] = pr["tilt"][1][0] = 0.35
+    elif ext == "ceqT":  # ceq(T) under a falling temperature
+        pr["G"], pr["V"], pr["v0"] = 4e-3, 2e-2, 10.0
+        pr["dceq_dT"][0][0], pr["dceq_dT"][1][0] = 0.4, 0.1
     return sc
 
 
@@ -51,12 +55,13 @@ def _close(a, b, rtol, scale):
     return abs(a - b) <= rtol * max(abs(b), scale)
 
 
-@pytest.mark.parametrize("tilt", [0.0, 0.35])
+@pytest.mark.parametrize("ext", ["plain", "tilt", "ceqT"])
 @pytest.mark.parametrize("prec,rtol", [("fp64", 1e-8), ("fp32", 2e-4)])
-def test_adjoint_matches_oracle_dual_derivatives(prec, rtol, tilt):
+def test_adjoint_matches_oracle_dual_derivatives(prec, rtol, ext):
     """40 x 36 (ragged against 256-thread blocks), 23 steps, K = 5: four
-    full segments and a ragged one; axis-aligned and tilted crystal axes."""
-    sc = _case(40, 36, prec, tilt)
+    full segments and a ragged one; the plain model, tilted crystal axes
+    (0.35 rad), and temperature-dependent ceq under a falling temperature."""
+    sc = _case(40, 36, prec, ext)
     H, K = 23, 5
     _, J, dpar, dmu = _gpu_adjoint(sc, H, K)
     rng = np.random.default_rng(11)

@@ -104,13 +104,3 @@ def test_uniform_melt_follows_the_falling_temperature():
     sim.step(50)
     got = sim.fields(("mu",))["mu"]
     np.testing.assert_allclose(got, 0.02 + 50 * 2 * pr["A"][0] * 0.5 * 4e-3 * 1e-2, rtol=0, atol=1e-13)
-
-
-def test_adjoint_rejects_ceqT():
-    sc = _case("adjoint2d", dict(nx=40, ny=36), "fp32")
-    sim = gpflbm.Sim(sc)
-    sim.set_state(*inputs.initial_state(sc))
-    obj = {"w_frac": 1.0, "w_tip": 0.0, "kappa": 1.0, "x0": 20, "y0": 18}
-    with pytest.raises(gpflbm.GpflbmError) as e:
-        sim.adjoint(obj, 4, 2)
-    assert e.value.status == gpflbm.ERR_UNSUPPORTED
