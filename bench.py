@@ -218,10 +218,20 @@ def cpu_baseline(sc, seconds):
     t0 = time.perf_counter()
     oracle.run(sc, phi, mu, f, steps, n0=1)
     dt = time.perf_counter() - t0
-    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.max_threads(),
-            "kind": "oracle",
-            "sample": "%d steps of the full %s grid (%d cells) after one step" % (
-                steps, sc["name"], cells)}
+    cores = oracle.max_threads()
+    # one thread, one step of the same grid, when that fits in about the
+    # same time
+    single = None
+    if one * cores <= seconds:
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.run(sc, phi, mu, f, 1, n0=1 + steps)
+        single = cells / (time.perf_counter() - t0) / 1e6
+        oracle.set_threads(threads)
+    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": cores,
+            "kind": "oracle", "single_thread_value": single,
+            "sample": "%d steps of the full %s grid (%d cells) after one step; single thread: "
+                      "one step" % (steps, sc["name"], cells)}
 
 
 def adjoint_ratio(args):
