@@ -426,9 +426,10 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
   h->has_state = false;
   if (workspace) {
     if (workspace_bytes < h->lay.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0) {
+      const gpflbm_status bad = workspace_bytes < h->lay.total ? GPFLBM_ERR_OOM : GPFLBM_ERR_ARG;
       delete h;
       std::fprintf(stderr, "gpflbm_create: workspace too small or not 256-byte aligned\n");
-      return workspace_bytes < h->lay.total ? GPFLBM_ERR_OOM : GPFLBM_ERR_ARG;
+      return bad;
     }
     h->ws = static_cast<unsigned char*>(workspace);
     h->owns_ws = false;

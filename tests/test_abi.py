@@ -111,6 +111,17 @@ def test_create_rejects_bad_arguments_without_a_device(L):
                            ctypes.byref(h)) == gpflbm.ERR_ARG
     assert L.gpflbm_create(ctypes.byref(g), 2, 1, ctypes.byref(gpflbm.params_struct(sc)), None, 0,
                            None) == gpflbm.ERR_ARG
+    # a caller's workspace that is too small or misaligned is refused before
+    # the device is touched (the pointer is only checked, never used)
+    g = gpflbm.grid_struct(sc)
+    p = gpflbm.params_struct(sc)
+    need = gpflbm.workspace_bytes(sc)
+    assert L.gpflbm_create(ctypes.byref(g), 2, 1, ctypes.byref(p), ctypes.c_void_p(1 << 20), need - 1,
+                           ctypes.byref(h)) == gpflbm.ERR_OOM
+    assert h.value is None
+    assert L.gpflbm_create(ctypes.byref(g), 2, 1, ctypes.byref(p), ctypes.c_void_p((1 << 20) + 8), need,
+                           ctypes.byref(h)) == gpflbm.ERR_ARG
+    assert h.value is None
     # calls on a null handle fail cleanly
     assert L.gpflbm_step(None, 1, None) == gpflbm.ERR_ARG
     assert L.gpflbm_set_state(None, None, None, None, 0, 0, None) == gpflbm.ERR_ARG
