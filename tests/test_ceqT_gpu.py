@@ -41,6 +41,8 @@ def _case(name, size, prec, slopes=SLOPES):
         sc["init"]["height"] = 12
     pr = sc["params"]
     pr["G"], pr["V"] = 4e-3, 2e-2
+    if name.startswith("eutectic"):  # the isotherm near the solid's top
+        pr["v0"] = 32.0 if name == "eutectic2d" else 24.0
     pr["dceq_dT"] = [row[:] for row in slopes]
     return sc
 

@@ -32,7 +32,11 @@ def _case(name, size, prec):
     if name == "eutectic3d":
         sc["init"]["height"] = 20
         sc["init"]["noise"] = 1e-3
-    sc["params"]["G"] = 4e-3  # the shift of v0 matters
+    # a strong gradient, so that the shift of v0 matters, with the isotherm
+    # near the solid's top
+    sc["params"]["G"] = 4e-3
+    if name.startswith("eutectic"):
+        sc["params"]["v0"] = 32.0 if name == "eutectic2d" else 24.0
     return sc
 
 

@@ -632,6 +632,7 @@ def test_solute_is_conserved_with_temperature_dependent_ceq(case):
     pr = sc["params"]
     pr["gbeta_c"] = [3e-3, 2e-3]
     pr["G"], pr["V"] = 4e-3, 2e-2
+    pr["v0"] = 32.0 if case == "eutectic2d" else 24.0  # isotherm near the solid's top
     pr["dceq_dT"] = [[0.4, -0.2], [0.1, 0.3], [-0.3, 0.05], [0.2, 0.2]]
     phi, mu = inputs.initial_state(sc)
     f = oracle.rest_populations(sc)
@@ -805,6 +806,29 @@ def test_frozen_temperature_gradient_sets_the_front():
     assert b > a + 0.04
 
 
+def _lamella_pair_rows(v0, steps):
+    """Solid rows of one alpha/beta lamella pair of the eutectic2d workload
+    (32 x 72, periodic x) after `steps` steps with the isotherm at v0."""
+    sc = inputs.scenario("eutectic2d", nx=32, ny=72, precision="fp64")
+    sc["params"]["v0"] = v0
+    phi, mu = inputs.initial_state(sc)
+    oracle.set_threads(oracle.max_threads())
+    phi, _, _ = oracle.run(sc, phi, mu, oracle.rest_populations(sc), steps)
+    return (1.0 - phi.reshape(3, -1)[0]).sum() / 32.0
+
+
+def test_eutectic_lamellae_grow_below_their_isotherm():
+    """Capillarity of 16-cell lamellae at gamma = 1/5 needs an undercooling of
+    about 0.06 to hold them still, far more than G = 1e-4 gives over the grid:
+    with T_E at the lamellae's top (v0 = 32) they melt back while the isotherm
+    rises; with T_E 0.125 / G above them (the workload's v0) they grow at
+    about V = 1e-3 (about 6 rows in 6000 steps)."""
+    assert inputs.scenario("eutectic2d")["params"]["v0"] == pytest.approx(1282.0)
+    assert _lamella_pair_rows(32.0, 6000) < 32.0 - 1.0
+    grown = _lamella_pair_rows(1282.0, 6000)
+    assert 32.0 + 2.0 < grown < 32.0 + 20.0
+
+
 # ----------------------------------------------------------------- moving frame
 def _frame_pair(dim, s, n1, n2, lower_v0=True):
     """Window A (nv layers) steps n1 times, moves its frame s layers up the
@@ -820,6 +844,7 @@ def _frame_pair(dim, s, n1, n2, lower_v0=True):
         big["init"]["height"] = 32
         big["init"]["noise"] = 1e-3  # seeded, so that the window ends see different values
     big["params"]["G"] = 4e-3  # a strong gradient: a frame without its T shift is visibly off
+    big["params"]["v0"] = 32.0 if dim == 2 else 24.0  # isotherm near the solid's top
     phi_b, mu_b = inputs.initial_state(big)
     nx, ny, _ = inputs.dims(big)
     layer = nx * (ny if dim == 3 else 1)
