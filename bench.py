@@ -201,6 +201,31 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def host_link(h_phi, h_mu, h_f, o_phi, o_mu, reps=5):
+    """Host-link rates with the copy engines on the same pinned buffers as the
+    end-to-end step (H2D: its three input buffers; D2H: its two outputs)."""
+    import torch
+
+    srcs = (h_phi, h_mu, h_f)
+    dsts = (o_phi, o_mu)
+    dev_in = [torch.empty_like(t, device="cuda") for t in srcs]
+    dev_out = [torch.empty_like(t, device="cuda") for t in dsts]
+    out = {}
+    for key, pairs in (("h2d_gbs", list(zip(dev_in, srcs))), ("d2h_gbs", list(zip(dsts, dev_out)))):
+        nbytes = sum(d.numel() * d.element_size() for d, _ in pairs)
+        for d, s in pairs:
+            d.copy_(s, non_blocking=True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            for d, s in pairs:
+                d.copy_(s, non_blocking=True)
+        b.record()
+        torch.cuda.synchronize()
+        out[key] = nbytes * reps / (a.elapsed_time(b) / 1e3) / 1e9
+    return out
+
+
 def cpu_baseline(sc, seconds):
     """FP64 oracle MLUPS on the host cores on a bounded sample (the
     workload's grid, as many steps as fit in about `seconds`)."""
@@ -422,11 +447,14 @@ def our_arm(args):
     t_now = sim.time()
 
     def e2e_step():
+        # pinned buffers, asynchronous: the stream runs load, step and field
+        # write-back back to back; the loop ends with a synchronize
         st1 = L.gpflbm_set_state(sim.h, ctypes.c_void_p(h_phi.data_ptr()),
                                  ctypes.c_void_p(h_mu.data_ptr()), ctypes.c_void_p(h_f.data_ptr()),
-                                 0, t_now, stream)
+                                 gpflbm.ASYNC, t_now, stream)
         st2 = L.gpflbm_step(sim.h, 1, stream)
-        st3 = L.gpflbm_get_fields(sim.h, gpflbm.FIELD["phi"] | gpflbm.FIELD["mu"], outs, 0, stream)
+        st3 = L.gpflbm_get_fields(sim.h, gpflbm.FIELD["phi"] | gpflbm.FIELD["mu"], outs,
+                                  gpflbm.ASYNC, stream)
         if st1 or st2 or st3:
             raise RuntimeError("e2e step failed: %s" % L.gpflbm_last_error(sim.h))
 
@@ -441,11 +469,19 @@ def our_arm(args):
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
     esz = 8 if sc["precision"] == "fp64" else 4
+    h2d_b, d2h_b = (NP + NC + Q) * cells * esz, (NP + NC) * cells * esz
+    link = host_link(h_phi, h_mu, h_f, o_phi, o_mu)
+    # the step's transfers and its kernel back to back at the measured link rates
+    bound_s = h2d_b / (link["h2d_gbs"] * 1e9) + d2h_b / (link["d2h_gbs"] * 1e9) + statistics.mean(pf_ms) / 1e3
+    link["serial_bound_us"] = bound_s * 1e6
+    link["frac"] = bound_s * args.e2e_steps / e2e_s
     e2e = {"value": job_mlups(world, cells, args.e2e_steps, e2e_s), "unit": "MLUPS",
-           "h2d_bytes_per_step": (NP + NC + Q) * cells * esz,
-           "d2h_bytes_per_step": (NP + NC) * cells * esz,
+           "h2d_bytes_per_step": h2d_b,
+           "d2h_bytes_per_step": d2h_b,
            "steps": args.e2e_steps,
-           "path": "gpflbm_set_state(pinned host) + gpflbm_step(1) + gpflbm_get_fields(pinned host)"}
+           "path": "gpflbm_set_state(pinned host, GPFLBM_ASYNC) + gpflbm_step(1) + "
+                   "gpflbm_get_fields(pinned host, GPFLBM_ASYNC), one stream, synchronised at the end",
+           "host_link": link}
 
     adjoint = None if args.no_adjoint else adjoint_ratio(args)
     if rank != 0:

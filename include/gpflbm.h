@@ -149,14 +149,27 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
 /* Replace the model parameters (same grid, phase and solute counts). */
 gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params);
 
+/* Flags of the src_is_device / dst_is_device arguments of gpflbm_set_state
+ * and gpflbm_get_fields (0 = host memory, returned to the caller complete).
+ * GPFLBM_ON_DEVICE: the pointers are device memory.
+ * GPFLBM_ASYNC: with device or pinned (page-locked or registered) host
+ * buffers the call does not synchronise `stream`; as with cudaMemcpyAsync on
+ * page-locked memory, the caller keeps the sources alive and unchanged, and
+ * reads the destinations, only once the stream has reached that point.
+ * Pageable host buffers are staged and waited for whatever the flag. */
+#define GPFLBM_ON_DEVICE 1
+#define GPFLBM_ASYNC 2
+
 /* Load S^n.  phi: N planes (liquid first); mu: K-1 planes; f: Q planes of
  * full populations, or NULL for the fluid at rest (f_k = w_k).
- * src_is_device: 1 if the pointers are device memory, 0 for host memory
- * (pageable or pinned).  The library copies; the caller keeps ownership.
- * Pinned or registered host buffers (all three of them) are read in place by
- * the load kernels over the host link; pageable ones are staged through the
- * workspace plane by plane.  Sets the step counter to t0.  Host sources are
- * read before return. */
+ * src_is_device: flags as above (1 = device memory, 0 = host memory,
+ * pageable or pinned).  The library copies; the caller keeps ownership.
+ * Device and pinned or registered host sources (all three of them) are read
+ * in place by one load kernel (over the host link for host memory);
+ * pageable ones are staged through the workspace plane by plane.  Sets the
+ * step counter to t0.  Host sources are read before return unless
+ * GPFLBM_ASYNC is given with pinned sources.  GPFLBM_ERR_ARG for an unknown
+ * flag bit. */
 gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, const void* f,
                                int src_is_device, long long t0, void* stream);
 
@@ -188,10 +201,12 @@ gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream);
 
 /* Copy fields of the current state out.  field_mask is an OR of
  * GPFLBM_FIELD_*; dst holds one pointer per set bit, in increasing bit
- * order, each large enough for that field's planes.  dst_is_device as in
- * set_state.  Device and pinned host destinations are written by one
+ * order, each large enough for that field's planes.  dst_is_device: flags
+ * as in set_state.  Device and pinned host destinations are written by one
  * kernel launch; pageable host destinations are staged field by field.  For
- * host destinations the call synchronises `stream`. */
+ * host destinations the call synchronises `stream`, unless GPFLBM_ASYNC is
+ * given and every destination is pinned.  GPFLBM_ERR_ARG for an unknown flag
+ * bit. */
 gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* dst,
                                 int dst_is_device, void* stream);
 

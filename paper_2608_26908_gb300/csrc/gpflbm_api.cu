@@ -478,6 +478,10 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
                                int src_is_device, long long t0, void* stream) {
   if (!h) return GPFLBM_ERR_ARG;
   if (!phi || !mu) return fail(h, GPFLBM_ERR_ARG, "set_state: phi and mu are required");
+  if (src_is_device & ~(GPFLBM_ON_DEVICE | GPFLBM_ASYNC))
+    return fail(h, GPFLBM_ERR_ARG, "set_state: unknown flag");
+  const bool on_device = (src_is_device & GPFLBM_ON_DEVICE) != 0;
+  const bool async = (src_is_device & GPFLBM_ASYNC) != 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t rs = h->ops->real_size;
   const size_t n = (size_t)h->cells;
@@ -489,7 +493,7 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   void* f_d = at(h, h->lay.f[h->cur]);
   cudaError_t e;
   bool staged = false;
-  if (!src_is_device) {
+  if (!on_device) {
     // pinned host sources are read by the load kernels in place
     void* mp = mapped_host(phi);
     void* mm = mapped_host(mu);
@@ -521,16 +525,27 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
       sf = stage;
     }
   }
-  // (the load launcher always rewrites f: from sf, or the fluid at rest)
-  e = h->ops->load(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
-  set_clock_kernel<<<1, 1, 0, s>>>(reinterpret_cast<double*>(at(h, h->lay.clock)), (double)t0);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: clock");
-  e = cudaMemsetAsync(at(h, h->lay.err), 0, sizeof(int), s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: error word");
-  e = cudaStreamSynchronize(s);  // host sources must outlive the copies and loads
-  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: synchronize");
+  double* clk = reinterpret_cast<double*>(at(h, h->lay.clock));
+  int* err = reinterpret_cast<int*>(at(h, h->lay.err));
+  if (staged) {
+    // (the load launcher always rewrites f: from sf, or the fluid at rest)
+    e = h->ops->load(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
+    set_clock_kernel<<<1, 1, 0, s>>>(clk, (double)t0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: clock");
+    e = cudaMemsetAsync(err, 0, sizeof(int), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: error word");
+  } else {
+    // device or pinned sources: every plane, the counters and the error word
+    // in one launch
+    e = h->ops->load_state(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, clk, (double)t0, err, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
+  }
+  if (staged || !async) {
+    e = cudaStreamSynchronize(s);  // host sources must outlive the copies and loads
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: synchronize");
+  }
   h->t = t0;
   h->has_state = true;
   return GPFLBM_OK;
@@ -643,6 +658,10 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "get_fields: no state loaded");
   if (field_mask & ~63u) return fail(h, GPFLBM_ERR_ARG, "get_fields: unknown field bit");
   if (field_mask && !dst) return fail(h, GPFLBM_ERR_ARG, "get_fields: dst is NULL");
+  if (dst_is_device & ~(GPFLBM_ON_DEVICE | GPFLBM_ASYNC))
+    return fail(h, GPFLBM_ERR_ARG, "get_fields: unknown flag");
+  const bool on_device = (dst_is_device & GPFLBM_ON_DEVICE) != 0;
+  const bool async = (dst_is_device & GPFLBM_ASYNC) != 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t rs = h->ops->real_size;
   const size_t n = (size_t)h->cells;
@@ -664,7 +683,7 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
     if (!(field_mask & (1u << bit))) continue;
     void* d = dst[slot++];
     if (!d) return fail(h, GPFLBM_ERR_ARG, "get_fields: a destination is NULL");
-    void* m = dst_is_device ? d : mapped_host(d);
+    void* m = on_device ? d : mapped_host(d);
     if (m) {
       *outs_direct[bit] = m;
       any_direct = true;
@@ -690,7 +709,9 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
     e = cudaStreamSynchronize(s);  // the stage area is reused by the next field
     if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: synchronize");
   }
-  if (!dst_is_device) {
+  bool any_staged = false;
+  for (int bit = 0; bit < 6; ++bit) any_staged = any_staged || staged_dst[bit] != nullptr;
+  if (!on_device && (any_staged || !async)) {
     e = cudaStreamSynchronize(s);  // host destinations are complete on return
     if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: synchronize");
   }

@@ -473,6 +473,81 @@ __global__ void load_f_kernel(long long cells, int nx, int px, long long plane,
   }
 }
 
+// V consecutive words as one access of V * sizeof(T) bytes (2, 4, 8 or 16),
+// at an address aligned to that size.
+template <int B>
+struct Bytes;
+template <>
+struct Bytes<2> { using type = unsigned short; };
+template <>
+struct Bytes<4> { using type = unsigned; };
+template <>
+struct Bytes<8> { using type = uint2; };
+template <>
+struct Bytes<16> { using type = uint4; };
+
+template <int V, class T>
+__device__ __forceinline__ void load_words(const T* __restrict__ p, T (&v)[V]) {
+  using W = typename Bytes<V * (int)sizeof(T)>::type;
+  const W w = *reinterpret_cast<const W*>(p);
+  memcpy(v, &w, sizeof(W));
+}
+
+template <int V, class T>
+__device__ __forceinline__ void store_words(T* __restrict__ p, const T (&v)[V]) {
+  using W = typename Bytes<V * (int)sizeof(T)>::type;
+  W w;
+  memcpy(&w, v, sizeof(W));
+  *reinterpret_cast<W*>(p) = w;
+}
+
+// The whole of S^n from exchange planes in one launch: phi (N planes, liquid
+// first; the stored planes), mu (K-1 planes), f (Q planes of populations, or
+// the fluid at rest when src_f is null) as deviations, and the two step
+// counters and the error word.  Each thread takes V consecutive cells of a
+// row (nx a multiple of V and, for V > 1, the sources 16-byte aligned), and
+// issues every load of its cells before the first store, so that the reads
+// of a host source over the host link are all in flight together.  The
+// arithmetic is that of load_phi_kernel, load_mu_kernel and load_f_kernel.
+template <int NP, int NC, int Q, class Real, class Store, int V>
+__global__ void load_state_kernel(long long cells, int nx, int px, long long plane,
+                                  const Real* __restrict__ src_phi, const Real* __restrict__ src_mu,
+                                  const Real* __restrict__ src_f, Real* __restrict__ phi,
+                                  Real* __restrict__ mu, Store* __restrict__ f,
+                                  double* __restrict__ clock, double t0, int* __restrict__ err) {
+  using Lat = Lattice<Q>;
+  using R = typename std::conditional<std::is_same<Store, double>::value, double, float>::type;
+  constexpr int NS = PhiStore<NP>::NS;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    clock[0] = t0;
+    clock[1] = t0;
+    *err = 0;
+  }
+  const long long x = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * V;
+  if (x >= cells) return;
+  const long long o = padded(x, nx, px);
+  Real vp[NS][V], vm[NC][V], vf[Q][V];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) load_words<V>(src_phi + (NP == 2 ? 1 : s) * cells + x, vp[s]);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) load_words<V>(src_mu + i * cells + x, vm[i]);
+  if (src_f) {
+#pragma unroll
+    for (int k = 0; k < Q; ++k) load_words<V>(src_f + k * cells + x, vf[k]);
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) store_words<V>(phi + s * plane + o, vp[s]);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) store_words<V>(mu + i * plane + o, vm[i]);
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    Store d[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) d[j] = Codec<Store>::put(src_f ? R(vf[k][j]) - R(Lat::w(k)) : R(0));
+    store_words<V>(f + k * plane + o, d);
+  }
+}
+
 // Exchange-format fields of the current state; any output may be null.
 // phi: N planes (liquid first); c_i = sum_a h_a (ceq_a,i(T) + mu_i / (2 A_a));
 // f = w + d; rho = 1 + sum d; U as in the step (force-corrected); dev = d.
@@ -515,6 +590,8 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
       o_c[i * cells + x] = Out(c);
     }
   }
+  // the populations only where an output needs them (uniform across the grid)
+  if (!o_f && !o_dev && !o_rho && !o_u) return;
   Real drho = Real(0), m[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) m[a] = Real(0);

@@ -52,6 +52,10 @@ struct Ops {
   // exchange planes (Real) -> stored state; src_f may be null (rest)
   cudaError_t (*load)(const void* params, const void* src_phi, const void* src_mu,
                       const void* src_f, void* phi, void* mu, void* f, cudaStream_t s);
+  // the whole state (src_f may be null) and the step counters, in one launch
+  cudaError_t (*load_state)(const void* params, const void* src_phi, const void* src_mu,
+                            const void* src_f, void* phi, void* mu, void* f, double* clock,
+                            double t0, int* err, cudaStream_t s);
   cudaError_t (*fields)(const void* params, const FieldsIO& io, cudaStream_t s);
   cudaError_t (*invariants)(const InvParams& p, const void* phi, const void* mu, const void* f,
                             double* partial, int blocks, double* out, cudaStream_t s);
@@ -136,6 +140,31 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  static cudaError_t load_state(const void* params, const void* src_phi, const void* src_mu,
+                                const void* src_f, void* phi, void* mu, void* f, double* clock,
+                                double t0, int* err, cudaStream_t s) {
+    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+    const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
+    constexpr int V = 16 / (int)sizeof(Real);  // one 16-byte word of each source plane
+    auto al16 = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    const bool vec = P.n[0] % V == 0 && al16(src_phi) && al16(src_mu) && al16(src_f);
+    const int threads = 256;
+    const long long items = vec ? cells / V : cells;
+    const unsigned blocks = (unsigned)((items + threads - 1) / threads);
+    const Real* sp = static_cast<const Real*>(src_phi);
+    const Real* sm = static_cast<const Real*>(src_mu);
+    const Real* sf = static_cast<const Real*>(src_f);
+    if (vec)
+      load_state_kernel<NP, NC, Q, Real, Store, V><<<blocks, threads, 0, s>>>(
+          cells, P.n[0], P.px, P.plane, sp, sm, sf, static_cast<Real*>(phi), static_cast<Real*>(mu),
+          static_cast<Store*>(f), clock, t0, err);
+    else
+      load_state_kernel<NP, NC, Q, Real, Store, 1><<<blocks, threads, 0, s>>>(
+          cells, P.n[0], P.px, P.plane, sp, sm, sf, static_cast<Real*>(phi), static_cast<Real*>(mu),
+          static_cast<Store*>(f), clock, t0, err);
+    return cudaGetLastError();
+  }
+
   static cudaError_t fields(const void* params, const FieldsIO& io, cudaStream_t s) {
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
@@ -172,6 +201,7 @@ struct Impl {
                             &Impl::step_pf,
                             &Impl::step_transport,
                             &Impl::load,
+                            &Impl::load_state,
                             &Impl::fields,
                             &Impl::invariants};
     return &ops;

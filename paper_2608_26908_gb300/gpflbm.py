@@ -14,6 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libgpflbm.so")
 
 OK = 0
+# exchange flags of gpflbm_set_state / gpflbm_get_fields (include/gpflbm.h)
+ON_DEVICE, ASYNC = 1, 2
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = (
     -1, -2, -3, -4, -5, -6, -7)
 PERIODIC, WALL = 0, 1

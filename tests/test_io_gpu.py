@@ -53,3 +53,60 @@ def test_pinned_host_exchange_matches_the_staged_path(name, size, prec):
         for n, o in zip(names, outs):
             np.testing.assert_array_equal(o.numpy(), want[n], err_msg=n)
             np.testing.assert_array_equal(dev[n].cpu().numpy(), want[n], err_msg=n)
+
+
+@pytest.mark.parametrize("name,size,prec", [
+    ("eutectic2d", dict(nx=72, ny=45), "fp32"),       # 4 | nx: 16-byte loads
+    ("eutectic2d", dict(nx=70, ny=45), "fp32_bf16"),  # word loads
+    ("dendrite2d", dict(nx=40, ny=36), "fp64"),       # 2 | nx: 16-byte loads
+    ("dendrite2d", dict(nx=41, ny=36), "fp64"),       # word loads
+    ("dendrite3d", dict(nx=20, ny=18, nz=16), "fp32_f16"),
+])
+def test_asynchronous_pinned_and_device_sources(name, size, prec):
+    """The one-launch load (device or pinned sources, with or without f) and
+    the asynchronous flag give the staged path's bits, before and after
+    steps; an unknown flag bit is refused."""
+    import torch
+    sc = inputs.scenario(name, precision=prec, **size)
+    phi0, mu0 = inputs.initial_state(sc)
+    f0 = oracle.rest_populations(sc) * (1.0 + 1e-3 * np.cos(np.arange(oracle.rest_populations(sc).size)))
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if dt == np.float64 else torch.float32
+    phi0, mu0, f0 = (np.asarray(a, dtype=dt) for a in (phi0, mu0, f0))
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    names = ["phi", "mu", "f"]
+    for with_f in (True, False):
+        a = gpflbm.Sim(sc)
+        a.set_state(phi0, mu0, f0 if with_f else None)  # pageable numpy: staged
+        want = a.fields(names)
+        # device sources through the binding
+        b = gpflbm.Sim(sc)
+        b.set_state(*(torch.from_numpy(x).cuda() for x in (phi0, mu0)),
+                    torch.from_numpy(f0).cuda() if with_f else None)
+        # pinned sources and destinations, asynchronous
+        c = gpflbm.Sim(sc)
+        src = [_pinned(x, torch) for x in (phi0, mu0, f0)]
+        st = gpflbm.lib().gpflbm_set_state(c.h, ctypes.c_void_p(src[0].data_ptr()),
+                                           ctypes.c_void_p(src[1].data_ptr()),
+                                           ctypes.c_void_p(src[2].data_ptr() if with_f else None),
+                                           gpflbm.ASYNC, 0, stream)
+        assert st == gpflbm.OK
+        bad = gpflbm.lib().gpflbm_set_state(c.h, ctypes.c_void_p(src[0].data_ptr()),
+                                            ctypes.c_void_p(src[1].data_ptr()), None, 4, 0, stream)
+        assert bad == gpflbm.ERR_ARG
+        for steps in (0, 5):
+            a.step(steps)
+            b.step(steps)
+            c.step(steps)
+            want = a.fields(names)
+            outs = [torch.empty(want[n].shape, dtype=tdt, pin_memory=True) for n in names]
+            mask = gpflbm.FIELD["phi"] | gpflbm.FIELD["mu"] | gpflbm.FIELD["f"]
+            ptrs = (ctypes.c_void_p * 3)(*[o.data_ptr() for o in outs])
+            assert gpflbm.lib().gpflbm_get_fields(c.h, mask, ptrs, gpflbm.ASYNC, stream) == gpflbm.OK
+            assert gpflbm.lib().gpflbm_get_fields(c.h, mask, ptrs, 8, stream) == gpflbm.ERR_ARG
+            torch.cuda.synchronize()
+            got_b = b.fields(names)
+            for n, o in zip(names, outs):
+                np.testing.assert_array_equal(o.numpy(), want[n], err_msg="pinned async " + n)
+                np.testing.assert_array_equal(got_b[n], want[n], err_msg="device " + n)
+        assert a.time() == b.time() == c.time() == 5
