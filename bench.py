@@ -163,6 +163,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.005)  # running before the region starts
+            self.skip = len(self.lines)
         except (OSError, ValueError):
             self.proc = None
         return self
@@ -183,7 +187,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in self.lines:
+        for line in self.lines[getattr(self, "skip", 0):]:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -223,6 +227,81 @@ def host_link(h_phi, h_mu, h_f, o_phi, o_mu, reps=5):
         b.record()
         torch.cuda.synchronize()
         out[key] = nbytes * reps / (a.elapsed_time(b) / 1e3) / 1e9
+    return out
+
+
+class NvmlSampler:
+    """SM clock and clock-event reasons read through NVML every ~0.2 ms while
+    running: the timed region of a small workload lasts a few milliseconds,
+    shorter than nvidia-smi's sampling period.  Read-only queries; absent
+    NVML, no samples."""
+
+    # clock-event reason bits of NVML
+    BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+            "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
+
+    def __init__(self, index):
+        import ctypes
+        self.ct = ctypes
+        self.samples = []
+        self.lib = None
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            h = ctypes.c_void_p()
+            if lib.nvmlInit_v2() == 0 and lib.nvmlDeviceGetHandleByIndex_v2(int(index), ctypes.byref(h)) == 0:
+                self.lib, self.h = lib, h
+                self.reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                    getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+        except OSError:
+            self.lib = None
+
+    def _run(self):
+        ct = self.ct
+        mhz, rs = ct.c_uint(), ct.c_ulonglong()
+        while not self.stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0:  # NVML_CLOCK_SM
+                r = self.reasons(self.h, ct.byref(rs)) if self.reasons else 1
+                self.samples.append((mhz.value, self.max_mhz, rs.value if r == 0 else 0))
+            time.sleep(0.0001)
+
+    def __enter__(self):
+        if self.lib:
+            mx = self.ct.c_uint()
+            self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, self.ct.byref(mx))
+            self.max_mhz = mx.value
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._run, daemon=True)
+            self.thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self.lib:
+            self.stop.set()
+            self.thread.join(timeout=5)
+        return False
+
+    def summary(self):
+        if not self.samples:
+            return {"nvml_samples": 0}
+        reasons = sorted(n for n, b in self.BITS.items() if any(s[2] & b for s in self.samples))
+        return {"nvml_sm_mhz": statistics.median(s[0] for s in self.samples),
+                "nvml_sm_max_mhz": max(s[1] for s in self.samples),
+                "nvml_reasons": reasons, "nvml_samples": len(self.samples)}
+
+
+def merge_clocks(smi, nv):
+    """One clocks record from the nvidia-smi and NVML samples of the region:
+    the median SM clock over NVML's samples when there are any (nvidia-smi's
+    period is longer than a small workload's region), the union of reasons."""
+    out = dict(smi)
+    out["smi_samples"] = smi.get("samples", 0)
+    if nv.get("nvml_samples"):
+        out["sm_mhz"] = nv["nvml_sm_mhz"]
+        out["sm_max_mhz"] = max(nv["nvml_sm_max_mhz"], smi.get("sm_max_mhz") or 0)
+        out["reasons"] = sorted(set(smi.get("reasons", [])) | set(nv["nvml_reasons"]))
+    out["samples"] = smi.get("samples", 0) + nv.get("nvml_samples", 0)
+    out.update(nv)
+    out["source"] = "NVML every ~0.1 ms and nvidia-smi every 20 ms during the timed region"
     return out
 
 
@@ -409,7 +488,7 @@ def our_arm(args):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
+    with ClockSampler(local) as clocks, NvmlSampler(local) as nvml:
         torch.cuda._sleep(BACKLOG_CYCLES)
         for i in range(args.steps):
             flush_l2()
@@ -514,7 +593,7 @@ def our_arm(args):
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": args.steps,
-        "clocks": clocks.summary(),
+        "clocks": merge_clocks(clocks.summary(), nvml.summary()),
         "invariants": {"mass": mass, "solute": list(solute), "solid_frac": frac},
     }
     if adjoint is not None:
