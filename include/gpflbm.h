@@ -168,8 +168,12 @@ gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params);
  * in place by one load kernel (over the host link for host memory);
  * pageable ones are staged through the workspace plane by plane.  Sets the
  * step counter to t0.  Host sources are read before return unless
- * GPFLBM_ASYNC is given with pinned sources.  GPFLBM_ERR_ARG for an unknown
- * flag bit. */
+ * GPFLBM_ASYNC is given with pinned sources.  With GPFLBM_ASYNC and device
+ * or pinned sources (and a state already loaded) the load goes into the
+ * handle's idle buffer on a stream of the library, after the work queued on
+ * `stream` by the last call other than get_fields, get_deviations and the
+ * invariants, so that it overlaps those read-only calls; `stream` then waits
+ * for the load.  GPFLBM_ERR_ARG for an unknown flag bit. */
 gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, const void* f,
                                int src_is_device, long long t0, void* stream);
 

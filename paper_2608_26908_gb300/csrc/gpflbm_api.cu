@@ -55,6 +55,16 @@ struct gpflbm_s {
   cudaEvent_t ev_fwd, ev_aux_end, ev_rec[2], ev_adj[2];
   cudaGraphExec_t chunk_graph[2];
   cudaGraphExec_t pair_graph[2];
+  // Asynchronous loads (GPFLBM_ASYNC from device or pinned sources) write the
+  // idle buffer on their own stream, so that they overlap the read-only calls
+  // (fields, deviations, invariants) that precede them on the caller's
+  // stream.  ev_mark is recorded on the caller's stream after every call that
+  // writes or reads both buffers (mut counts those calls; marked is the count
+  // at the last record); a load waits for it, and the caller's stream waits
+  // for the load.  Every entry point other than the read-only ones bumps mut.
+  cudaStream_t xfer;
+  cudaEvent_t ev_mark, ev_loaded;
+  unsigned long long mut, marked;
   // device parameters in the arithmetic type (only one is used)
   DevParams<double> pd;
   DevParams<float> pf;
@@ -78,6 +88,15 @@ gpflbm_status cuda_fail(gpflbm_t h, cudaError_t e, const char* where) {
 // the problem's phases has a nonzero tilt or an equilibrium composition
 // depends on temperature.
 const Ops* stepper(gpflbm_t h) { return h->pf.tilted || h->pf.tdep ? h->ops_ext : h->ops; }
+
+// Record the caller's stream's progress for asynchronous loads, once per
+// run of read-only calls (see gpflbm_s::ev_mark).
+void mark(gpflbm_t h, cudaStream_t s) {
+  if (h->xfer && h->marked != h->mut) {
+    cudaEventRecord(h->ev_mark, s);
+    h->marked = h->mut;
+  }
+}
 
 const Ops* find_ops(int D, int lattice, int precision, int NP, int NC, bool ext) {
   using namespace gpflbm;
@@ -471,6 +490,7 @@ gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params) {
   h->params = *params;
   set_device_params(h);
   drop_graphs(h);  // parameters are baked into captured launches
+  ++h->mut;
   return GPFLBM_OK;
 }
 
@@ -527,6 +547,37 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   }
   double* clk = reinterpret_cast<double*>(at(h, h->lay.clock));
   int* err = reinterpret_cast<int*>(at(h, h->lay.err));
+  if (!staged && async && h->has_state) {
+    // Load the idle buffer on the library's transfer stream once the caller's
+    // stream has finished the last call that used both buffers, so that the
+    // load overlaps the read-only calls queued since (a write-back of the
+    // current state over the host link runs beside the next state's load);
+    // the caller's stream then waits for the load.
+    if (!h->xfer) {
+      e = cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_mark, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_loaded, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        if (h->xfer) cudaStreamDestroy(h->xfer);
+        h->xfer = nullptr;
+        return cuda_fail(h, e, "set_state: transfer stream");
+      }
+      h->marked = h->mut + 1;  // nothing recorded yet
+    }
+    mark(h, s);
+    const int to = 1 - h->cur;
+    e = cudaStreamWaitEvent(h->xfer, h->ev_mark, 0);
+    if (e == cudaSuccess)
+      e = h->ops->load_state(dev_params(h), sp, sm, sf, at(h, h->lay.phi[to]), at(h, h->lay.mu[to]),
+                             at(h, h->lay.f[to]), clk + to, nullptr, (double)t0, err, h->xfer);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_loaded, h->xfer);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_loaded, 0);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
+    h->cur = to;
+    h->t = t0;
+    ++h->mut;
+    return GPFLBM_OK;
+  }
   if (staged) {
     // (the load launcher always rewrites f: from sf, or the fluid at rest)
     e = h->ops->load(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, s);
@@ -539,7 +590,7 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   } else {
     // device or pinned sources: every plane, the counters and the error word
     // in one launch
-    e = h->ops->load_state(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, clk, (double)t0, err, s);
+    e = h->ops->load_state(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, clk, clk + 1, (double)t0, err, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
   }
   if (staged || !async) {
@@ -548,6 +599,7 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   }
   h->t = t0;
   h->has_state = true;
+  ++h->mut;
   return GPFLBM_OK;
 }
 
@@ -556,6 +608,7 @@ gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream) {
   if (n_steps < 0) return fail(h, GPFLBM_ERR_ARG, "step: n_steps < 0");
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "step: no state loaded");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ++h->mut;
   int left = n_steps;
   while (left > 0) {
     cudaError_t e;
@@ -593,6 +646,7 @@ gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream) {
     return fail(h, GPFLBM_ERR_UNSUPPORTED, "shift_frame: obstacle rows on the vertical axis");
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "shift_frame: no state loaded");
   if (rows == 0) return GPFLBM_OK;
+  ++h->mut;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const long long layer = ax == 2 ? (long long)h->px * h->grid.ny : h->px;
   const long long n = layer * nv;
@@ -640,6 +694,7 @@ gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream) {
     return fail(h, GPFLBM_ERR_ARG, "step_timed: three events are required");
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "step_timed: no state loaded");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ++h->mut;
   const gpflbm::StepIO io = step_io(h, h->cur);
   cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(events[0]), s);
   if (e == cudaSuccess) e = stepper(h)->step_pf(dev_params(h), io, s);
@@ -663,6 +718,7 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
   const bool on_device = (dst_is_device & GPFLBM_ON_DEVICE) != 0;
   const bool async = (dst_is_device & GPFLBM_ASYNC) != 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mark(h, s);  // read-only: a later asynchronous load may overlap it
   const size_t rs = h->ops->real_size;
   const size_t n = (size_t)h->cells;
   const int planes[6] = {h->NP, h->NC, h->NC, h->Q, 1, h->D};
@@ -722,6 +778,7 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
   if (!h || !dst) return GPFLBM_ERR_ARG;
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "get_deviations: no state loaded");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mark(h, s);  // read-only
   void* target = dst_is_device ? dst : at(h, h->lay.stage);
   gpflbm::FieldsIO io;
   std::memset(&io, 0, sizeof(io));
@@ -746,6 +803,7 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
   if (!h) return GPFLBM_ERR_ARG;
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "invariants: no state loaded");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mark(h, s);  // read-only
   const long long want = (h->cells + gpflbm::kRedThreads - 1) / gpflbm::kRedThreads;
   const int blocks = (int)(want < gpflbm::kRedMaxBlocks ? want : gpflbm::kRedMaxBlocks);
   double* partial = reinterpret_cast<double*>(at(h, h->lay.partial));
@@ -783,6 +841,11 @@ void gpflbm_destroy(gpflbm_t h) {
   if (!h) return;
   drop_graphs(h);
   if (h->capture) cudaStreamDestroy(h->capture);
+  if (h->xfer) {
+    cudaStreamDestroy(h->xfer);
+    cudaEventDestroy(h->ev_mark);
+    cudaEventDestroy(h->ev_loaded);
+  }
   if (h->aux) {
     cudaStreamDestroy(h->aux);
     cudaEventDestroy(h->ev_fwd);
@@ -867,6 +930,7 @@ extern "C" gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, dou
   cudaError_t e = noalloc_scratch(&scratch);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: cudaGetSymbolAddress");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mark(h, s);  // read-only
   double* partial = scratch;
   double* red = scratch + (size_t)kNoAllocMaxBlocks * kNoAllocValues;
   e = (h->inv.theta_t = h->pd.theta0 - h->pd.GV * (double)h->t, h->ops->invariants)(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
@@ -1139,6 +1203,7 @@ gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizo
   gpflbm_status st = adj_check(h, horizon, ckpt_every);
   if (st != GPFLBM_OK) return st;
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "adjoint: no state loaded");
+  ++h->mut;
   if (!obj || obj->solid != 1 || obj->x0 < 0 || obj->x0 >= h->grid.nx || obj->y0 < 0 ||
       obj->y0 >= h->grid.ny || !std::isfinite(obj->kappa) || !std::isfinite(obj->w_frac) ||
       !std::isfinite(obj->w_tip))

@@ -52,10 +52,11 @@ struct Ops {
   // exchange planes (Real) -> stored state; src_f may be null (rest)
   cudaError_t (*load)(const void* params, const void* src_phi, const void* src_mu,
                       const void* src_f, void* phi, void* mu, void* f, cudaStream_t s);
-  // the whole state (src_f may be null) and the step counters, in one launch
+  // the whole state (src_f may be null) and the step counters (clock_b may
+  // be null), in one launch
   cudaError_t (*load_state)(const void* params, const void* src_phi, const void* src_mu,
-                            const void* src_f, void* phi, void* mu, void* f, double* clock,
-                            double t0, int* err, cudaStream_t s);
+                            const void* src_f, void* phi, void* mu, void* f, double* clock_a,
+                            double* clock_b, double t0, int* err, cudaStream_t s);
   cudaError_t (*fields)(const void* params, const FieldsIO& io, cudaStream_t s);
   cudaError_t (*invariants)(const InvParams& p, const void* phi, const void* mu, const void* f,
                             double* partial, int blocks, double* out, cudaStream_t s);
@@ -141,8 +142,8 @@ struct Impl {
   }
 
   static cudaError_t load_state(const void* params, const void* src_phi, const void* src_mu,
-                                const void* src_f, void* phi, void* mu, void* f, double* clock,
-                                double t0, int* err, cudaStream_t s) {
+                                const void* src_f, void* phi, void* mu, void* f, double* clock_a,
+                                double* clock_b, double t0, int* err, cudaStream_t s) {
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
     constexpr int V = 16 / (int)sizeof(Real);  // one 16-byte word of each source plane
@@ -157,11 +158,11 @@ struct Impl {
     if (vec)
       load_state_kernel<NP, NC, Q, Real, Store, V><<<blocks, threads, 0, s>>>(
           cells, P.n[0], P.px, P.plane, sp, sm, sf, static_cast<Real*>(phi), static_cast<Real*>(mu),
-          static_cast<Store*>(f), clock, t0, err);
+          static_cast<Store*>(f), clock_a, clock_b, t0, err);
     else
       load_state_kernel<NP, NC, Q, Real, Store, 1><<<blocks, threads, 0, s>>>(
           cells, P.n[0], P.px, P.plane, sp, sm, sf, static_cast<Real*>(phi), static_cast<Real*>(mu),
-          static_cast<Store*>(f), clock, t0, err);
+          static_cast<Store*>(f), clock_a, clock_b, t0, err);
     return cudaGetLastError();
   }
 

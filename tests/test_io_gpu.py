@@ -110,3 +110,54 @@ def test_asynchronous_pinned_and_device_sources(name, size, prec):
                 np.testing.assert_array_equal(o.numpy(), want[n], err_msg="pinned async " + n)
                 np.testing.assert_array_equal(got_b[n], want[n], err_msg="device " + n)
         assert a.time() == b.time() == c.time() == 5
+
+
+@pytest.mark.parametrize("name,size,prec", [
+    ("eutectic2d", dict(nx=72, ny=45), "fp32"),
+    ("dendrite2d", dict(nx=40, ny=36), "fp64"),
+    ("dendrite3d", dict(nx=20, ny=18, nz=16), "fp32_f16"),
+])
+def test_asynchronous_loads_overlapping_the_write_back(name, size, prec):
+    """An end-to-end loop with nothing but the final synchronise: each state
+    is loaded (asynchronously, into the idle buffer, beside the previous
+    write-back), stepped and written back; every written-back state equals,
+    bit for bit, the same load, steps and fields done one call at a time."""
+    import torch
+    dt = np.float64 if prec == "fp64" else np.float32
+    tdt = torch.float64 if dt == np.float64 else torch.float32
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    names = ["phi", "mu", "f"]
+    mask = gpflbm.FIELD["phi"] | gpflbm.FIELD["mu"] | gpflbm.FIELD["f"]
+    states = []
+    for k in range(4):
+        sc = inputs.scenario(name, precision=prec, seed=2000 + k, **size)
+        phi0, mu0 = inputs.initial_state(sc)
+        f0 = oracle.rest_populations(sc)
+        f0 = f0 * (1.0 + 1e-3 * np.cos(np.arange(f0.size) + k))
+        states.append([np.asarray(a, dtype=dt) for a in (phi0, mu0, f0)])
+    ref = gpflbm.Sim(sc)
+    want = []
+    for phi0, mu0, f0 in states:
+        ref.set_state(phi0, mu0, f0, t0=5)
+        ref.step(3)
+        want.append(ref.fields(names))
+    sim = gpflbm.Sim(sc)
+    src = [[_pinned(a, torch) for a in st] for st in states]
+    outs = [[torch.empty(want[0][n].shape, dtype=tdt, pin_memory=True) for n in names] for _ in states]
+    L = gpflbm.lib()
+    for k in range(len(states)):
+        assert L.gpflbm_set_state(sim.h, *[ctypes.c_void_p(t.data_ptr()) for t in src[k]],
+                                  gpflbm.ASYNC, 5, stream) == gpflbm.OK
+        assert L.gpflbm_step(sim.h, 3, stream) == gpflbm.OK
+        ptrs = (ctypes.c_void_p * 3)(*[o.data_ptr() for o in outs[k]])
+        assert L.gpflbm_get_fields(sim.h, mask, ptrs, gpflbm.ASYNC, stream) == gpflbm.OK
+    torch.cuda.synchronize()
+    for k in range(len(states)):
+        for n, o in zip(names, outs[k]):
+            np.testing.assert_array_equal(o.numpy(), want[k][n], err_msg="state %d %s" % (k, n))
+    assert sim.time() == 8
+    # a read-only call, then a synchronous load, then the async path again
+    m0, s0, _, _ = sim.invariants()
+    sim.set_state(*states[0], t0=5)
+    sim.step(3)
+    np.testing.assert_array_equal(sim.fields(["phi"])["phi"], want[0]["phi"])
