@@ -215,7 +215,10 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
                                 int dst_is_device, void* stream);
 
 /* Stored population deviations f_k - w_k of the current state, as Q planes
- * of the exchange type (float or double), for checks of the storage codec. */
+ * of the exchange type (float or double), for checks of the storage codec.
+ * dst_is_device: GPFLBM_ON_DEVICE for device memory, else host memory
+ * (staged; the call synchronises `stream`; GPFLBM_ASYNC is accepted and
+ * changes nothing).  GPFLBM_ERR_ARG for an unknown flag bit. */
 gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, void* stream);
 
 /* Global totals in FP64, by a fixed-order reduction (identical from run to
@@ -287,8 +290,10 @@ gpflbm_status gpflbm_adjoint_workspace_bytes(gpflbm_t h, int horizon, int ckpt_e
  * Outputs (each may be NULL): *J; dparams[0] = dJ/d(1/tau_phi),
  * dparams[1] = dJ/d delta_01, dparams[2] = dJ/d gbeta_c[0] (FP64,
  * accumulated per cell in FP64 and summed in a fixed order); dmu0 =
- * dJ/dmu(S^t0) as one plane in the exchange layout and type, device or host
- * memory per dst_is_device.  Every contribution is gathered in a fixed
+ * dJ/dmu(S^t0) as one plane in the exchange layout and type, device memory
+ * when dst_is_device has GPFLBM_ON_DEVICE, else host memory (GPFLBM_ASYNC is
+ * accepted and changes nothing; GPFLBM_ERR_ARG for an unknown flag bit).
+ * Every contribution is gathered in a fixed
  * order, so the results are the same from run to run.
  * The handle is left at S^{t0+H}, bit for bit as after gpflbm_step(h, H).
  * workspace: device memory of gpflbm_adjoint_workspace_bytes() bytes,

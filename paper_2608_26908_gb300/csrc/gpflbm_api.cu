@@ -777,9 +777,12 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
 gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, void* stream) {
   if (!h || !dst) return GPFLBM_ERR_ARG;
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "get_deviations: no state loaded");
+  if (dst_is_device & ~(GPFLBM_ON_DEVICE | GPFLBM_ASYNC))
+    return fail(h, GPFLBM_ERR_ARG, "get_deviations: unknown flag");
+  const bool on_device = (dst_is_device & GPFLBM_ON_DEVICE) != 0;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   mark(h, s);  // read-only
-  void* target = dst_is_device ? dst : at(h, h->lay.stage);
+  void* target = on_device ? dst : at(h, h->lay.stage);
   gpflbm::FieldsIO io;
   std::memset(&io, 0, sizeof(io));
   io.phi = at(h, h->lay.phi[h->cur]);
@@ -789,7 +792,7 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
   io.o_dev = target;
   cudaError_t e = h->ops->fields(dev_params(h), io, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_deviations: kernel");
-  if (!dst_is_device) {
+  if (!on_device) {
     e = cudaMemcpyAsync(dst, target, h->Q * (size_t)h->cells * h->ops->real_size,
                         cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -1151,9 +1154,10 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
 
   // outputs
   if (dmu0) {
-    void* target = dst_is_device ? dmu0 : at(h, h->lay.stage);
+    const bool on_device = (dst_is_device & GPFLBM_ON_DEVICE) != 0;
+    void* target = on_device ? dmu0 : at(h, h->lay.stage);
     e = A->export_plane(P, lam[cur] + pl, target, s);
-    if (e == cudaSuccess && !dst_is_device)
+    if (e == cudaSuccess && !on_device)
       e = cudaMemcpyAsync(dmu0, target, (size_t)h->cells * h->ops->real_size, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: dmu0");
   }
@@ -1203,6 +1207,8 @@ gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizo
   gpflbm_status st = adj_check(h, horizon, ckpt_every);
   if (st != GPFLBM_OK) return st;
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "adjoint: no state loaded");
+  if (dst_is_device & ~(GPFLBM_ON_DEVICE | GPFLBM_ASYNC))
+    return fail(h, GPFLBM_ERR_ARG, "adjoint: unknown flag");
   ++h->mut;
   if (!obj || obj->solid != 1 || obj->x0 < 0 || obj->x0 >= h->grid.nx || obj->y0 < 0 ||
       obj->y0 >= h->grid.ny || !std::isfinite(obj->kappa) || !std::isfinite(obj->w_frac) ||

@@ -104,6 +104,7 @@ def test_asynchronous_pinned_and_device_sources(name, size, prec):
             ptrs = (ctypes.c_void_p * 3)(*[o.data_ptr() for o in outs])
             assert gpflbm.lib().gpflbm_get_fields(c.h, mask, ptrs, gpflbm.ASYNC, stream) == gpflbm.OK
             assert gpflbm.lib().gpflbm_get_fields(c.h, mask, ptrs, 8, stream) == gpflbm.ERR_ARG
+            assert gpflbm.lib().gpflbm_get_deviations(c.h, ptrs[2], 4, stream) == gpflbm.ERR_ARG
             torch.cuda.synchronize()
             got_b = b.fields(names)
             for n, o in zip(names, outs):
