@@ -525,28 +525,31 @@ __global__ void load_state_kernel(long long cells, int nx, int px, long long pla
     if (clock_b) clock_b[0] = t0;
     *err = 0;
   }
-  const long long x = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * V;
-  if (x >= cells) return;
-  const long long o = padded(x, nx, px);
-  Real vp[NS][V], vm[NC][V], vf[Q][V];
+  // a grid-stride loop: the launcher caps the grid (two CTAs per SM), so
+  // that a load and a field write-back over the host link can share the SMs
+  const long long stride = (long long)gridDim.x * blockDim.x * V;
+  for (long long x = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * V; x < cells; x += stride) {
+    const long long o = padded(x, nx, px);
+    Real vp[NS][V], vm[NC][V], vf[Q][V];
 #pragma unroll
-  for (int s = 0; s < NS; ++s) load_words<V>(src_phi + (NP == 2 ? 1 : s) * cells + x, vp[s]);
+    for (int s = 0; s < NS; ++s) load_words<V>(src_phi + (NP == 2 ? 1 : s) * cells + x, vp[s]);
 #pragma unroll
-  for (int i = 0; i < NC; ++i) load_words<V>(src_mu + i * cells + x, vm[i]);
-  if (src_f) {
+    for (int i = 0; i < NC; ++i) load_words<V>(src_mu + i * cells + x, vm[i]);
+    if (src_f) {
 #pragma unroll
-    for (int k = 0; k < Q; ++k) load_words<V>(src_f + k * cells + x, vf[k]);
-  }
+      for (int k = 0; k < Q; ++k) load_words<V>(src_f + k * cells + x, vf[k]);
+    }
 #pragma unroll
-  for (int s = 0; s < NS; ++s) store_words<V>(phi + s * plane + o, vp[s]);
+    for (int s = 0; s < NS; ++s) store_words<V>(phi + s * plane + o, vp[s]);
 #pragma unroll
-  for (int i = 0; i < NC; ++i) store_words<V>(mu + i * plane + o, vm[i]);
+    for (int i = 0; i < NC; ++i) store_words<V>(mu + i * plane + o, vm[i]);
 #pragma unroll
-  for (int k = 0; k < Q; ++k) {
-    Store d[V];
+    for (int k = 0; k < Q; ++k) {
+      Store d[V];
 #pragma unroll
-    for (int j = 0; j < V; ++j) d[j] = Codec<Store>::put(src_f ? R(vf[k][j]) - R(Lat::w(k)) : R(0));
-    store_words<V>(f + k * plane + o, d);
+      for (int j = 0; j < V; ++j) d[j] = Codec<Store>::put(src_f ? R(vf[k][j]) - R(Lat::w(k)) : R(0));
+      store_words<V>(f + k * plane + o, d);
+    }
   }
 }
 
@@ -554,16 +557,14 @@ __global__ void load_state_kernel(long long cells, int nx, int px, long long pla
 // phi: N planes (liquid first); c_i = sum_a h_a (ceq_a,i(T) + mu_i / (2 A_a));
 // f = w + d; rho = 1 + sum d; U as in the step (force-corrected); dev = d.
 template <int D, int Q, int NP, int NC, class Real, class Store, class Out>
-__global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ phi,
-                              const Real* __restrict__ mu_in, const Store* __restrict__ f,
-                              const double* __restrict__ clock, Out* __restrict__ o_phi,
-                              Out* __restrict__ o_mu, Out* __restrict__ o_c, Out* __restrict__ o_f,
-                              Out* __restrict__ o_rho, Out* __restrict__ o_u,
-                              Out* __restrict__ o_dev) {
+__device__ __forceinline__ void fields_cell(const DevParams<Real>& P, const Real* __restrict__ phi,
+                                            const Real* __restrict__ mu_in, const Store* __restrict__ f,
+                                            const double* __restrict__ clock, Out* __restrict__ o_phi,
+                                            Out* __restrict__ o_mu, Out* __restrict__ o_c,
+                                            Out* __restrict__ o_f, Out* __restrict__ o_rho,
+                                            Out* __restrict__ o_u, Out* __restrict__ o_dev,
+                                            long long cells, long long x) {
   using Lat = Lattice<Q>;
-  const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
-  const long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (x >= cells) return;
   const int gx = (int)(x % P.n[0]);
   const int gy = (int)((x / P.n[0]) % P.n[1]);
   const int gz = (int)(x / ((long long)P.n[0] * P.n[1]));
@@ -622,6 +623,22 @@ __global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ 
 #pragma unroll
     for (int a = 0; a < D; ++a) o_u[a * cells + x] = Out((m[a] + (a == D - 1 ? Real(0.5) * FB : Real(0))) * inv);
   }
+}
+
+// One thread per cell, in a grid-stride loop over a grid the launcher caps
+// at two CTAs per SM (see load_state_kernel).
+template <int D, int Q, int NP, int NC, class Real, class Store, class Out>
+__global__ void fields_kernel(const DevParams<Real> P, const Real* __restrict__ phi,
+                              const Real* __restrict__ mu_in, const Store* __restrict__ f,
+                              const double* __restrict__ clock, Out* __restrict__ o_phi,
+                              Out* __restrict__ o_mu, Out* __restrict__ o_c, Out* __restrict__ o_f,
+                              Out* __restrict__ o_rho, Out* __restrict__ o_u,
+                              Out* __restrict__ o_dev) {
+  const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < cells; x += stride)
+    fields_cell<D, Q, NP, NC, Real, Store, Out>(P, phi, mu_in, f, clock, o_phi, o_mu, o_c, o_f,
+                                                o_rho, o_u, o_dev, cells, x);
 }
 
 // ------------------------------------------------------------------ invariants

@@ -62,6 +62,24 @@ struct Ops {
                             double* partial, int blocks, double* out, cudaStream_t s);
 };
 
+// Grid of the exchange kernels (state load, field write-back): two CTAs of
+// 256 threads per SM in a grid-stride loop.  That keeps enough accesses in
+// flight for the host link and for HBM, and leaves room on every SM for the
+// other of the two, which may run at the same time on another stream.
+inline unsigned exchange_blocks(long long items, int threads) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        v > 0)
+      sms = v;
+    else
+      return (unsigned)((items + threads - 1) / threads);  // one item per thread
+  }
+  const long long need = (items + threads - 1) / threads;
+  return (unsigned)(need < 2LL * sms ? need : 2LL * sms);
+}
+
 // QQ: lattice size (0 = D2Q9 in 2D, D3Q19 in 3D; 27 = D3Q27).
 // EXT: the step kernels of the extended model -- turned crystal axes and
 // temperature-dependent equilibrium compositions (a separate table, so that
@@ -151,7 +169,7 @@ struct Impl {
     const bool vec = P.n[0] % V == 0 && al16(src_phi) && al16(src_mu) && al16(src_f);
     const int threads = 256;
     const long long items = vec ? cells / V : cells;
-    const unsigned blocks = (unsigned)((items + threads - 1) / threads);
+    const unsigned blocks = exchange_blocks(items, threads);
     const Real* sp = static_cast<const Real*>(src_phi);
     const Real* sm = static_cast<const Real*>(src_mu);
     const Real* sf = static_cast<const Real*>(src_f);
@@ -170,7 +188,7 @@ struct Impl {
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
     const int threads = 256;
-    const unsigned blocks = (unsigned)((cells + threads - 1) / threads);
+    const unsigned blocks = exchange_blocks(cells, threads);
     fields_kernel<D, Q, NP, NC, Real, Store, Real><<<blocks, threads, 0, s>>>(
         P, static_cast<const Real*>(io.phi), static_cast<const Real*>(io.mu),
         static_cast<const Store*>(io.f), io.clock, static_cast<Real*>(io.o_phi),
