@@ -35,6 +35,16 @@ def test_header_declares_the_boundary():
         assert need in names
 
 
+def test_binding_constants_match_the_header():
+    """Status codes, field bits and exchange flags of the binding are the
+    header's."""
+    src = open(os.path.join(ROOT, "include", "gpflbm.h")).read()
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+(GPFLBM_\w+)\s+\(?(-?\d+)", src)}
+    assert defines["GPFLBM_ON_DEVICE"] == gpflbm.ON_DEVICE
+    assert defines["GPFLBM_ASYNC"] == gpflbm.ASYNC
+    assert gpflbm.ON_DEVICE & gpflbm.ASYNC == 0
+
+
 def test_library_exports_every_declared_symbol(L):
     for name in declared_functions():
         assert hasattr(L, name), name
