@@ -574,8 +574,14 @@ def our_arm(args):
     kernels_ms = {dom_name: statistics.mean(pf_ms)}
     dom_avg_s = statistics.mean(dom_ms) / 1e3
     achieved = dom_b * cells / dom_avg_s / 1e9
+    # the committed ncu summaries hold the traffic of a full-size launch of
+    # the workload's own kernel: none for a crop or another kernel variant
+    default_prec = inputs.scenario(args.workload)["precision"]
+    variant = (any(getattr(args, a, None) for a in ("nx", "ny", "nz", "lattice")) or args.eta or
+               args.tilt or args.dceq_dT or (args.precision or default_prec) != default_prec)
+    traffic = None if variant else profiled_traffic(dom_name, args.workload)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(dom_name, args.workload),
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": dom_name, "bytes_per_cell": dom_b,
                 "peak_source": ("measured: MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
                                 else "fallback 6.8 TB/s")}
