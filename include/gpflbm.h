@@ -309,7 +309,10 @@ gpflbm_status gpflbm_time(gpflbm_t h, long long* t);
 /* Human-readable description of the last failure on h ("" if none). */
 const char* gpflbm_last_error(gpflbm_t h);
 
-/* Release the handle (and the workspace if the library allocated it). */
+/* Release the handle (and the workspace if the library allocated it).
+ * Waits for the handle's own transfer stream (asynchronous loads); work the
+ * caller queued on its streams is the caller's to wait for before freeing a
+ * workspace it owns. */
 void gpflbm_destroy(gpflbm_t h);
 
 #ifdef __cplusplus

@@ -845,6 +845,9 @@ void gpflbm_destroy(gpflbm_t h) {
   drop_graphs(h);
   if (h->capture) cudaStreamDestroy(h->capture);
   if (h->xfer) {
+    // an asynchronous load may still write the workspace, which the caller
+    // may free once this returns
+    cudaStreamSynchronize(h->xfer);
     cudaStreamDestroy(h->xfer);
     cudaEventDestroy(h->ev_mark);
     cudaEventDestroy(h->ev_loaded);
