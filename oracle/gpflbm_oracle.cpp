@@ -855,6 +855,14 @@ int oracle_gradient_energy(const double* q, int dim, double delta, double theta,
   return 0;
 }
 
+// The Gibbs-simplex projection step of the phase-field update [R11], on one
+// vector of 1..4 values (in place).
+int oracle_project_simplex(double* u, int m) {
+  if (m < 1 || m > 4) return -1;
+  project_simplex(u, m);
+  return 0;
+}
+
 // Lattice weights w_k and velocities c_k (3 ints per direction) of the
 // lattice with q directions; f = w_k is the fluid at rest with rho = 1.
 int oracle_lattice(int q, double* w, int* c) {

@@ -86,6 +86,7 @@ def lib():
         L.oracle_gradient_energy.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, dp,
                                              dp]
+        L.oracle_project_simplex.argtypes = [dp, ctypes.c_int]
         L.oracle_set_threads.argtypes = [ctypes.c_int]
         L.oracle_max_threads.restype = ctypes.c_int
         _lib = L
@@ -145,6 +146,14 @@ def lattice(q):
     c = np.zeros(3 * q, dtype=np.int32)
     assert lib().oracle_lattice(q, _dp(w), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int))) == 0
     return w, c.reshape(q, 3)
+
+
+def project_simplex(v):
+    """The oracle's Euclidean projection of v (1..4 values) onto the simplex
+    {sum = 1, u >= 0}, the last step of the phase-field update."""
+    u = np.array(v, dtype=np.float64)
+    assert lib().oracle_project_simplex(_dp(u), len(u)) == 0
+    return u
 
 
 def gradient_energy(q, delta, q_floor=1e-12, theta=0.0):

@@ -990,3 +990,43 @@ def test_flop_counter_is_per_cell_and_per_step():
         for k in d:
             assert d[k] == pytest.approx(counts[0][k], rel=1e-15), k
     assert counts[0]["lattice_boltzmann"] > 100 and counts[0]["phase_field"] > 0
+
+
+# ----------------------------------------------------------------- simplex projection
+def _projection_by_enumeration(v):
+    """Euclidean projection onto {sum u = 1, u >= 0} by brute force: for every
+    support S, the closest point of the affine set {sum_S u = 1, u = 0 off S}
+    is u_S = v_S - (sum v_S - 1)/|S|; the projection is the nearest feasible
+    one of these (the projection lies on one of these faces)."""
+    import itertools
+    m = len(v)
+    best, best_d = None, np.inf
+    for r in range(1, m + 1):
+        for S in itertools.combinations(range(m), r):
+            u = np.zeros(m)
+            idx = list(S)
+            u[idx] = v[idx] - (v[idx].sum() - 1.0) / r
+            if (u >= -1e-15).all():
+                d = ((u - v) ** 2).sum()
+                if d < best_d - 1e-15:
+                    best, best_d = u, d
+    return best
+
+
+def test_simplex_projection_matches_enumeration_of_supports():
+    """The oracle's sort-and-threshold projection [R11] equals the projection
+    found by enumerating supports, on random vectors of 1..4 values and on the
+    special cases a phase-field update meets (already on the simplex, a tie,
+    one large value, all values equal, all negative)."""
+    rng = np.random.default_rng(7)
+    cases = [np.array(c, dtype=float) for c in (
+        [1.0], [0.3], [0.5, 0.5], [1.2, -0.2], [0.2, 0.3, 0.5], [0.4, 0.4, 0.4],
+        [2.0, 0.0, 0.0, 0.0], [-0.1, -0.2, -0.3, -0.4], [0.6, 0.6, -0.1, 0.0],
+        [0.25, 0.25, 0.25, 0.25], [1.0 + 1e-9, 0.0, -1e-9])]
+    for m in (2, 3, 4):
+        cases += [rng.normal(1.0 / m, 0.4, m) for _ in range(200)]
+    for v in cases:
+        got = oracle.project_simplex(v)
+        want = _projection_by_enumeration(v)
+        np.testing.assert_allclose(got, want, rtol=0, atol=1e-14, err_msg=str(v))
+        assert abs(got.sum() - 1.0) < 1e-14 and (got >= 0).all()
