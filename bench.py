@@ -2,12 +2,12 @@
 step on GB300.
 
 A step is one full time step (phase field, chemical potential, lattice
-Boltzmann) over the workload grid: by default the 2D binary eutectic under
-natural convection, 1024 x 512 cells, D2Q9, three phases, one solute, FP32.
-The state (2 x 52 MB) is smaller than L2, so L2 is flushed before every
-timed step (a 256 MB write, then a 256 MB read, so that the state is cold
-and the flush's own dirty lines are written back before the step, not
-during it) and each step is timed alone with CUDA events.  A spin kernel
+Boltzmann) over the workload grid: by default the largest single-GPU
+configuration, the 3D ternary eutectic (256 x 256 x 512 cells, D3Q19, four
+phases, two solutes, FP32).  L2 is flushed before every timed step (a 256 MB
+write, then a 256 MB read, so that the state is cold -- the 2D states are
+smaller than L2 -- and the flush's own dirty lines are written back before
+the step, not during it) and each step is timed alone with CUDA events.  A spin kernel
 queued ahead of the loop keeps the host ahead of the GPU, so that every
 event pair brackets device work only (not host submission latency).
 
@@ -21,8 +21,13 @@ Prints one JSON line (rank 0):
   clocks      nvidia-smi samples taken during the timed region
   adjoint     the adjoint/forward time ratio on the 512 x 512 differentiation
               workload (500 steps, checkpoints every 50)
+  configs     every other configuration (2D dendrite FP64, 2D eutectic, 3D
+              dendrite with FP32, FP16 and BF16 population storage, the 3D
+              eutectic, the 2D differentiation workload), each timed the same
+              way with its roofline and its oracle baseline
 
---impl reference times the FP64 CPU oracle on the same workload instead.
+--impl reference times the FP64 CPU oracle on the same configuration instead
+(each step one oracle step of the workload's parity crop).
 Under torchrun every rank runs its own replica of the workload (the path has
 no data-path exchange on one GPU per replica; weak scaling).
 """
@@ -53,14 +58,18 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="eutectic2d", choices=list(inputs.WORKLOADS))
+    ap.add_argument("--workload", default="eutectic3d", choices=list(inputs.WORKLOADS))
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp32_f16", "fp32_bf16"])
     ap.add_argument("--nx", type=int, default=None, help="override the grid (profiling runs)")
     ap.add_argument("--ny", type=int, default=None)
     ap.add_argument("--nz", type=int, default=None)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--config-cpu-seconds", type=float, default=4.0,
+                    help="oracle seconds per configuration record")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="time the headline workload only (profiling runs)")
     ap.add_argument("--adjoint-horizon", type=int, default=500)
     ap.add_argument("--adjoint-ckpt", type=int, default=50)
     ap.add_argument("--adjoint-reps", type=int, default=5)
@@ -305,39 +314,6 @@ def merge_clocks(smi, nv):
     return out
 
 
-def cpu_baseline(sc, seconds):
-    """FP64 oracle MLUPS on the host cores on a bounded sample (the
-    workload's grid, as many steps as fit in about `seconds`)."""
-    from oracle import oracle
-
-    threads = os.cpu_count() or 1
-    oracle.set_threads(threads)
-    phi, mu = inputs.initial_state(sc)
-    f = oracle.rest_populations(sc)
-    cells = inputs.cells(sc)
-    t0 = time.perf_counter()
-    phi, mu, f = oracle.run(sc, phi, mu, f, 1)
-    one = time.perf_counter() - t0
-    steps = max(1, min(200, int(seconds / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    oracle.run(sc, phi, mu, f, steps, n0=1)
-    dt = time.perf_counter() - t0
-    cores = oracle.max_threads()
-    # one thread, one step of the same grid, when that fits in about the
-    # same time
-    single = None
-    if one * cores <= seconds:
-        oracle.set_threads(1)
-        t0 = time.perf_counter()
-        oracle.run(sc, phi, mu, f, 1, n0=1 + steps)
-        single = cells / (time.perf_counter() - t0) / 1e6
-        oracle.set_threads(threads)
-    return {"value": cells * steps / dt / 1e6, "unit": "MLUPS", "cores": cores,
-            "kind": "oracle", "single_thread_value": single,
-            "sample": "%d steps of the full %s grid (%d cells) after one step; single thread: "
-                      "one step" % (steps, sc["name"], cells)}
-
-
 def adjoint_ratio(args):
     """Adjoint/forward time ratio on the differentiation workload: 2D
     dendrite 512 x 512, D2Q9, two phases, one solute, FP32, J = solid
@@ -409,13 +385,49 @@ def job_mlups(world, cells, steps, seconds):
     return world * cells * steps / seconds / 1e6
 
 
+# Every benchmark configuration besides the headline: (workload, precision,
+# parity crop the oracle is timed on).  The headline is the largest
+# single-GPU configuration, the ternary eutectic 256 x 256 x 512.
+CONFIGS = (
+    ("dendrite2d", "fp64", None),
+    ("eutectic2d", "fp32", None),
+    ("dendrite3d", "fp32", (64, 64, 64)),
+    ("dendrite3d", "fp32_f16", (64, 64, 64)),
+    ("dendrite3d", "fp32_bf16", (64, 64, 64)),
+    ("eutectic3d", "fp32", (64, 64, 128)),
+    ("adjoint2d", "fp32", (64, 64, 1)),
+)
+PARITY_CROP = {(w, p): c for w, p, c in CONFIGS}
+
+
+def run_config(desc, cells, world):
+    return {"workload": desc, "cells": cells, "steps_per_iteration": 1,
+            "l2": "flushed before every timed step (256 MB write, then 256 MB read)",
+            "parallelism": "replicas x%d" % world}
+
+
 def reference_arm(args):
+    """The FP64 oracle on the host cores, on this arm's configuration: each
+    timed step is one oracle step of the workload's parity crop (the same
+    recipe on a smaller grid; the full 3D grids take seconds per oracle
+    step), rank 0 only."""
     world, rank, _ = dist_setup(args)
     if rank != 0:
         return 0
     from oracle import oracle
 
-    sc, desc = workload(args)
+    sc_full, desc = workload(args)
+    prec = sc_full["precision"]
+    crop = PARITY_CROP.get((args.workload, prec)) or PARITY_CROP.get((args.workload, "fp32"))
+    kw = {}
+    if crop and not any(getattr(args, a, None) for a in ("nx", "ny", "nz")):
+        kw = dict(zip(("nx", "ny", "nz"), crop))
+        if crop[2] == 1:
+            kw.pop("nz")
+    else:
+        kw = {"nx": args.nx, "ny": args.ny, "nz": args.nz}
+    sc = inputs.scenario(args.workload, precision=prec, **kw)
+    sc["params"] = sc_full["params"]
     threads = os.cpu_count() or 1
     oracle.set_threads(threads)
     phi, mu = inputs.initial_state(sc)
@@ -431,23 +443,137 @@ def reference_arm(args):
         n += 1
     dt = time.perf_counter() - t0
     value = cells * args.steps / dt / 1e6
+    nx, ny, nz = inputs.dims(sc)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "cells": cells, "steps_per_iteration": 1},
+        "config": run_config(desc, inputs.cells(sc_full), world),
         "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.max_threads(),
                          "kind": "oracle",
-                         "sample": "%d full-grid steps of %s" % (args.steps, sc["name"])},
+                         "sample": "each step: one FP64 oracle step of the %s crop (%d cells) of %s"
+                                   % ("x".join(str(v) for v in (nx, ny, nz) if v > 1), cells,
+                                      sc["name"])},
         "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
+
+
+def timed_steps(sim, steps, warmup, flush_l2):
+    """Per-step kernel times (ms): each step launched alone after an L2
+    flush, bracketed by two CUDA events on the launching stream."""
+    import torch
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    warm = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for e in warm:
+        e.record()  # materialise the event objects
+    for row in ev:
+        for e in row:
+            e.record()
+    torch.cuda.synchronize()
+    torch.cuda._sleep(BACKLOG_CYCLES)
+    for _ in range(warmup):
+        flush_l2()
+        sim.step_timed(warm)
+    torch.cuda.synchronize()
+    torch.cuda._sleep(BACKLOG_CYCLES)
+    for i in range(steps):
+        flush_l2()
+        sim.step_timed(ev[i])
+    torch.cuda.synchronize()
+    return [row[0].elapsed_time(row[1]) for row in ev]
+
+
+def roofline_record(sc, cells, step_ms, traffic, kernel):
+    """The step kernel against the measured HBM copy bandwidth: algorithmic
+    bytes per cell-update (state read once, written once) x cells / the
+    kernel's mean event time."""
+    _, _, step_b = kernel_bytes_per_cell(sc)
+    peak, peak_kind = measured_peaks()
+    achieved = step_b * cells / (statistics.mean(step_ms) / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+            "bytes_per_cell": step_b,
+            "peak_source": ("measured: MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
+                            else "fallback 6.8 TB/s")}
+
+
+def oracle_rate(sc, seconds, threads):
+    """FP64 oracle MLUPS of `sc` on `threads` host threads: one step, then
+    as many steps as fit in about `seconds`."""
+    from oracle import oracle
+
+    oracle.set_threads(threads)
+    phi, mu = inputs.initial_state(sc)
+    f = oracle.rest_populations(sc)
+    cells = inputs.cells(sc)
+    t0 = time.perf_counter()
+    phi, mu, f = oracle.run(sc, phi, mu, f, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(200, int(seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(sc, phi, mu, f, steps, n0=1)
+    dt = time.perf_counter() - t0
+    return cells * steps / dt / 1e6, steps, oracle.max_threads()
+
+
+def cpu_baseline(name, precision, seconds):
+    """The FP64 oracle on the host cores on a bounded sample of the
+    workload: its parity crop (the same recipe on a smaller grid, as many
+    steps as fit in about `seconds`), on every core and on one thread."""
+    crop = PARITY_CROP.get((name, precision))
+    kw = dict(zip(("nx", "ny", "nz"), crop)) if crop else {}
+    if crop and crop[2] == 1:
+        kw.pop("nz")
+    sc = inputs.scenario(name, precision=precision, **kw)
+    cores = os.cpu_count() or 1
+    allc, steps, used = oracle_rate(sc, seconds, cores)
+    single, steps1, _ = oracle_rate(sc, seconds / 3.0, 1)
+    nx, ny, nz = inputs.dims(sc)
+    return {"value": allc, "unit": "MLUPS", "cores": used, "kind": "oracle",
+            "single_thread_value": single,
+            "sample": "%d steps (all cores) and %d steps (one thread) of %s on %s (%d cells), "
+                      "after one step" % (steps, steps1, name,
+                                          "x".join(str(n) for n in (nx, ny, nz) if n > 1),
+                                          inputs.cells(sc))}
+
+
+def measure_config(name, precision, args, flush_l2):
+    """One sub-record: the step of `name` at `precision` on its full grid,
+    timed like the headline, with its roofline and its oracle baseline."""
+    from paper_2608_26908_gb300 import gpflbm
+
+    sc = inputs.scenario(name, precision=precision)
+    cells = inputs.cells(sc)
+    phi0, mu0 = inputs.initial_state(sc)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0)
+    with NvmlSampler(0) as nvml:
+        ms = timed_steps(sim, args.steps, args.warmup, flush_l2)
+    st = sim.invariants(allow_nonfinite=True)[3]
+    sim.close()
+    if st != gpflbm.OK:
+        raise RuntimeError("%s %s: state is not finite after the timed steps" % (name, precision))
+    nx, ny, nz = inputs.dims(sc)
+    kernel = "step%dd_kernel" % (3 if nz > 1 else 2)
+    rec = {"workload": "%s %s D%dQ%d N=%d K-1=%d %s" % (
+               name, "x".join(str(n) for n in (nx, ny, nz) if n > 1), 3 if nz > 1 else 2,
+               lattice_q(sc), sc["n_phases"], sc["n_solutes"], precision),
+           "cells": cells, "steps": args.steps, "ms_per_step": statistics.mean(ms),
+           "mlups": cells * len(ms) / (sum(ms) / 1e3) / 1e6,
+           "roofline": roofline_record(sc, cells, ms, None, kernel),
+           "clocks": nvml.summary()}
+    if not args.no_cpu_baseline:
+        rec["cpu_baseline"] = cpu_baseline(name, precision, args.config_cpu_seconds)
+    return rec
+
+
 def our_arm(args):
-    import numpy as np
     import torch
 
     from paper_2608_26908_gb300 import gpflbm
@@ -472,35 +598,14 @@ def our_arm(args):
         flush.zero_()                               # 256 MB written: the state leaves L2
         torch.sum(evict, dim=0, out=evict_out)      # 256 MB read: the dirty lines drain now
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    warm = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-    for e in warm:
-        e.record()  # materialise the event objects
-    for row in ev:
-        for e in row:
-            e.record()
-    torch.cuda.synchronize()
-    torch.cuda._sleep(BACKLOG_CYCLES)
-    for _ in range(args.warmup):
-        flush_l2()
-        sim.step_timed(warm)
-    torch.cuda.synchronize()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks, NvmlSampler(local) as nvml:
-        torch.cuda._sleep(BACKLOG_CYCLES)
-        for i in range(args.steps):
-            flush_l2()
-            sim.step_timed(ev[i])
-        torch.cuda.synchronize()
+        step_ms = timed_steps(sim, args.steps, args.warmup, flush_l2)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    # a step is one fused launch, bracketed by the first two events (the third
-    # marks the empty slot of a second launch and is not part of the step)
-    pf_ms = [row[0].elapsed_time(row[1]) for row in ev]
-    step_ms = pf_ms
     total_s = max_over_ranks(sum(step_ms) / 1e3, pg, "cuda")
     mass, solute, frac, st = sim.invariants(allow_nonfinite=True)
     if st != gpflbm.OK:
@@ -519,6 +624,7 @@ def our_arm(args):
     h_phi.numpy()[:] = cur["phi"].reshape(-1)
     h_mu.numpy()[:] = cur["mu"].reshape(-1)
     h_f.numpy()[:] = cur["f"].reshape(-1)
+    del cur
     import ctypes
     L = gpflbm.lib()
     outs = (ctypes.c_void_p * 2)(o_phi.data_ptr(), o_mu.data_ptr())
@@ -551,7 +657,7 @@ def our_arm(args):
     h2d_b, d2h_b = (NP + NC + Q) * cells * esz, (NP + NC) * cells * esz
     link = host_link(h_phi, h_mu, h_f, o_phi, o_mu)
     # the step's transfers and its kernel back to back at the measured link rates
-    bound_s = h2d_b / (link["h2d_gbs"] * 1e9) + d2h_b / (link["d2h_gbs"] * 1e9) + statistics.mean(pf_ms) / 1e3
+    bound_s = h2d_b / (link["h2d_gbs"] * 1e9) + d2h_b / (link["d2h_gbs"] * 1e9) + statistics.mean(step_ms) / 1e3
     link["serial_bound_us"] = bound_s * 1e6
     link["frac"] = bound_s * args.e2e_steps / e2e_s
     e2e = {"value": job_mlups(world, cells, args.e2e_steps, e2e_s), "unit": "MLUPS",
@@ -561,41 +667,39 @@ def our_arm(args):
            "path": "gpflbm_set_state(pinned host, GPFLBM_ASYNC) + gpflbm_step(1) + "
                    "gpflbm_get_fields(pinned host, GPFLBM_ASYNC), one stream, synchronised at the end",
            "host_link": link}
+    sim.close()
+    del h_phi, h_mu, h_f, o_phi, o_mu
 
+    # every other configuration (rank 0 of a single-GPU run only: under
+    # torchrun the replicas time the headline alone)
+    configs = None
+    if world == 1 and not args.no_configs:
+        configs = [measure_config(n, p, args, flush_l2) for n, p, _ in CONFIGS]
     adjoint = None if args.no_adjoint else adjoint_ratio(args)
+    if configs is not None and adjoint is not None:
+        for rec in configs:
+            if rec["workload"].startswith("adjoint2d"):
+                rec["adjoint_forward_ratio"] = adjoint["ratio"]
     if rank != 0:
         pg.destroy_process_group() if pg else None
         return 0
-    pf_b, tr_b, step_b = kernel_bytes_per_cell(sc)
-    peak, peak_kind = measured_peaks()
-    # one fused launch per step: its algorithmic bytes are the step's
-    dom_name = "step%dd_kernel" % sim.dim
-    dom_b, dom_ms = step_b, pf_ms
-    kernels_ms = {dom_name: statistics.mean(pf_ms)}
-    dom_avg_s = statistics.mean(dom_ms) / 1e3
-    achieved = dom_b * cells / dom_avg_s / 1e9
+    nx_, ny_, nz_ = inputs.dims(sc)
+    dom_name = "step%dd_kernel" % (3 if nz_ > 1 else 2)
     # the committed ncu summaries hold the traffic of a full-size launch of
     # the workload's own kernel: none for a crop or another kernel variant
     default_prec = inputs.scenario(args.workload)["precision"]
     variant = (any(getattr(args, a, None) for a in ("nx", "ny", "nz", "lattice")) or args.eta or
                args.tilt or args.dceq_dT or (args.precision or default_prec) != default_prec)
     traffic = None if variant else profiled_traffic(dom_name, args.workload)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": dom_name, "bytes_per_cell": dom_b,
-                "peak_source": ("measured: MEASURED_PEAKS.json hbm_gbs" if peak_kind == "measured"
-                                else "fallback 6.8 TB/s")}
+    roofline = roofline_record(sc, cells, step_ms, traffic, dom_name)
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": dtype_name(sc), "data": "synthetic",
-        "config": {"workload": desc, "cells": cells, "steps_per_iteration": 1,
-                   "l2": "flushed before every timed step (256 MB write, then 256 MB read)",
-                   "parallelism": "replicas x%d" % world},
-        "hbm_roofline_frac_step": step_b * cells / (statistics.mean(step_ms) / 1e3) / 1e9 / peak,
-        "step_bytes_per_cell": step_b,
-        "kernels_ms": kernels_ms,
+        "config": run_config(desc, cells, world),
+        "step_bytes_per_cell": roofline["bytes_per_cell"],
+        "kernels_ms": {dom_name: statistics.mean(step_ms)},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": args.steps,
@@ -604,8 +708,10 @@ def our_arm(args):
     }
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if configs is not None:
+        line["configs"] = configs
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.workload, sc["precision"], args.cpu_seconds)
     print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()

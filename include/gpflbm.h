@@ -53,7 +53,7 @@ typedef enum {
   GPFLBM_ERR_OOM = -2,         /* workspace too small or device allocation failed */
   GPFLBM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   GPFLBM_ERR_NONFINITE = -4,   /* NaN or Inf found in the state by gpflbm_invariants */
-  GPFLBM_ERR_TIMEOUT = -5,     /* a bounded device wait (TMA copy) gave up during a step */
+  /* -5 is not used: no kernel of the library waits on another agent */
   GPFLBM_ERR_STATE = -6,       /* call out of order (e.g. step before set_state) */
   GPFLBM_ERR_UNSUPPORTED = -7  /* valid but not built: phase/solute count, lattice */
 } gpflbm_status;
@@ -195,12 +195,11 @@ gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream);
  * (wall_rows != 0 there); GPFLBM_ERR_STATE before set_state. */
 gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream);
 
-/* One step launched directly (not from a graph) that records three caller
+/* One step launched directly (not from a graph) that records two caller
  * CUDA events (cudaEvent_t) on `stream`: events[0] before the step kernel
- * (one fused launch for all three updates), events[1] after it, and
- * events[2] right after events[1] (the slot of a second launch, which the
- * fused step does not have), for kernel timing with cudaEventElapsedTime.
- * Same result as gpflbm_step(h, 1, stream). */
+ * (one fused launch for all three updates) and events[1] after it, for
+ * kernel timing with cudaEventElapsedTime.  Same result as
+ * gpflbm_step(h, 1, stream). */
 gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream);
 
 /* Copy fields of the current state out.  field_mask is an OR of
@@ -232,9 +231,7 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
  * xor-butterfly (offsets 16, 8, 4, 2, 1); lane 0 of warps 0..7 are then
  * added in order; the G block sums are added in order.  Synchronises
  * `stream`.  Returns GPFLBM_ERR_NONFINITE (totals still written) if any
- * cell of the state is NaN or Inf, and GPFLBM_ERR_TIMEOUT if a step since
- * the last gpflbm_set_state abandoned a bounded wait for its tile copies
- * (the state is then invalid).  Any output pointer may be NULL. */
+ * cell of the state is NaN or Inf.  Any output pointer may be NULL. */
 gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double* solid_frac,
                                 void* stream);
 
@@ -249,9 +246,12 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
  * totals are summed in blocks of up to 8192 cells, in a different order than
  * gpflbm_invariants, so they agree with it to FP64 rounding, not bit for
  * bit.  The first call on a device looks the array up (with that device
- * current) and should come before any stream capture.  Calls share the
- * array: calls that overlap on the GPU race.  Synchronises `stream`;
- * outputs and GPFLBM_ERR_NONFINITE as for gpflbm_invariants. */
+ * current) and should come before any stream capture; the address found is
+ * kept for the life of the process, so it does not survive a
+ * cudaDeviceReset (after one, handles and this entry point on that device
+ * are not usable).  Calls share the array: calls that overlap on the GPU
+ * race.  Synchronises `stream`; outputs and statuses (GPFLBM_ERR_NONFINITE,
+ * GPFLBM_ERR_STATE) as for gpflbm_invariants. */
 gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, double* solute,
                                         double* solid_frac, void* stream);
 

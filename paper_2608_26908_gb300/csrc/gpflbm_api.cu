@@ -29,7 +29,7 @@ constexpr int kChunk = 16;  // steps per replayed CUDA graph
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t phi[2], mu[2], f[2], stage, clock, err, partial, red;
+  size_t phi[2], mu[2], f[2], stage, clock, partial, red;
   size_t total;
 };
 
@@ -199,7 +199,6 @@ Layout make_layout(const Ops* ops, long long cells, long long plane) {
   for (int i = 0; i < 2; ++i) L.f[i] = take(ops->Q * plane * ops->store_size);
   L.stage = take(ops->Q * plane * ops->real_size);
   L.clock = take(2 * sizeof(double));
-  L.err = take(sizeof(int));
   L.partial = take(gpflbm::kRedMaxBlocks * (ops->NC + 3) * sizeof(double));
   L.red = take((ops->NC + 3) * sizeof(double));
   L.total = off;
@@ -336,7 +335,6 @@ gpflbm::StepIO step_io(gpflbm_t h, int from) {
   io.f_out = at(h, h->lay.f[1 - from]);
   io.clock_in = reinterpret_cast<const double*>(at(h, h->lay.clock)) + from;
   io.clock_out = reinterpret_cast<double*>(at(h, h->lay.clock)) + 1 - from;
-  io.err = reinterpret_cast<int*>(at(h, h->lay.err));
   return io;
 }
 
@@ -546,7 +544,6 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
     }
   }
   double* clk = reinterpret_cast<double*>(at(h, h->lay.clock));
-  int* err = reinterpret_cast<int*>(at(h, h->lay.err));
   if (!staged && async && h->has_state) {
     // Load the idle buffer on the library's transfer stream once the caller's
     // stream has finished the last call that used both buffers, so that the
@@ -569,7 +566,7 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
     e = cudaStreamWaitEvent(h->xfer, h->ev_mark, 0);
     if (e == cudaSuccess)
       e = h->ops->load_state(dev_params(h), sp, sm, sf, at(h, h->lay.phi[to]), at(h, h->lay.mu[to]),
-                             at(h, h->lay.f[to]), clk + to, nullptr, (double)t0, err, h->xfer);
+                             at(h, h->lay.f[to]), clk + to, nullptr, (double)t0, h->xfer);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_loaded, h->xfer);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_loaded, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
@@ -585,12 +582,9 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
     set_clock_kernel<<<1, 1, 0, s>>>(clk, (double)t0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: clock");
-    e = cudaMemsetAsync(err, 0, sizeof(int), s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "set_state: error word");
   } else {
-    // device or pinned sources: every plane, the counters and the error word
-    // in one launch
-    e = h->ops->load_state(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, clk, clk + 1, (double)t0, err, s);
+    // device or pinned sources: every plane and the counters in one launch
+    e = h->ops->load_state(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, clk, clk + 1, (double)t0, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
   }
   if (staged || !async) {
@@ -690,17 +684,15 @@ gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream) {
 }
 
 gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream) {
-  if (!h || !events || !events[0] || !events[1] || !events[2])
-    return fail(h, GPFLBM_ERR_ARG, "step_timed: three events are required");
+  if (!h || !events || !events[0] || !events[1])
+    return fail(h, GPFLBM_ERR_ARG, "step_timed: two events are required");
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "step_timed: no state loaded");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ++h->mut;
   const gpflbm::StepIO io = step_io(h, h->cur);
   cudaError_t e = cudaEventRecord(static_cast<cudaEvent_t>(events[0]), s);
-  if (e == cudaSuccess) e = stepper(h)->step_pf(dev_params(h), io, s);
+  if (e == cudaSuccess) e = stepper(h)->step(dev_params(h), io, s);
   if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(events[1]), s);
-  if (e == cudaSuccess) e = stepper(h)->step_transport(dev_params(h), io, s);
-  if (e == cudaSuccess) e = cudaEventRecord(static_cast<cudaEvent_t>(events[2]), s);
   if (e != cudaSuccess) return cuda_fail(h, e, "step_timed");
   h->cur = 1 - h->cur;
   h->t += 1;
@@ -815,14 +807,9 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
                                      at(h, h->lay.f[h->cur]), partial, blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: kernel");
   double out[GPFLBM_MAX_SOLUTES + 3];
-  int err_word = 0;
   e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&err_word, at(h, h->lay.err), sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: copy");
-  if (err_word != 0)
-    return fail(h, GPFLBM_ERR_TIMEOUT, "a bounded device wait gave up during a step");
   if (mass) *mass = out[0] + (double)h->cells;
   if (solute)
     for (int i = 0; i < h->NC; ++i) solute[i] = out[1 + i];
@@ -1022,7 +1009,6 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
   const size_t pl = (size_t)h->plane * h->ops->real_size;
   const int K = L.K, n_ck = L.n_ck;
   double* clk = reinterpret_cast<double*>(ws + L.clk);
-  int* err = reinterpret_cast<int*>(at(h, h->lay.err));
   cudaError_t e = A->configure();
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: configure");
   if (!h->aux) {
@@ -1069,7 +1055,6 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     io.f_out = out + 2 * pl;
     io.clock_in = forward_pass ? fw_clk(c, j) : clk_at(c, j);
     io.clock_out = forward_pass ? fw_clk(c, j + 1) : clk_at(c, j + 1);
-    io.err = err;
     return stepper(h)->step(P, io, st);
   };
   // copies of one stored state: handle -> slot, or slot -> handle
@@ -1168,16 +1153,12 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     e = A->sum(P, gacc + (size_t)j * h->plane, partial + (size_t)(j + 1) * gpflbm::kRedMaxBlocks, blocks, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: parameter sums");
   std::vector<double> host(4 * (size_t)gpflbm::kRedMaxBlocks + 1);
-  int err_word = 0;
   e = cudaMemcpyAsync(host.data(), partial, 4 * (size_t)gpflbm::kRedMaxBlocks * sizeof(double),
                       cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&host[4 * (size_t)gpflbm::kRedMaxBlocks], tip, sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&err_word, at(h, h->lay.err), sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: results");
-  if (err_word != 0) return fail(h, GPFLBM_ERR_TIMEOUT, "a bounded device wait gave up during a step");
   double sums[4];
   for (int j = 0; j < 4; ++j) {
     double t = 0.0;

@@ -504,8 +504,8 @@ __device__ __forceinline__ void store_words(T* __restrict__ p, const T (&v)[V]) 
 // The whole of S^n from exchange planes in one launch: phi (N planes, liquid
 // first; the stored planes), mu (K-1 planes), f (Q planes of populations, or
 // the fluid at rest when src_f is null) as deviations, the step counter of
-// the loaded buffer (clock_a) and of the other one (clock_b, when not null),
-// and the error word.  Each thread takes V consecutive cells of a
+// the loaded buffer (clock_a) and of the other one (clock_b, when not null).
+// Each thread takes V consecutive cells of a
 // row (nx a multiple of V and, for V > 1, the sources 16-byte aligned), and
 // issues every load of its cells before the first store, so that the reads
 // of a host source over the host link are all in flight together.  The
@@ -516,14 +516,13 @@ __global__ void load_state_kernel(long long cells, int nx, int px, long long pla
                                   const Real* __restrict__ src_f, Real* __restrict__ phi,
                                   Real* __restrict__ mu, Store* __restrict__ f,
                                   double* __restrict__ clock_a, double* __restrict__ clock_b,
-                                  double t0, int* __restrict__ err) {
+                                  double t0) {
   using Lat = Lattice<Q>;
   using R = typename std::conditional<std::is_same<Store, double>::value, double, float>::type;
   constexpr int NS = PhiStore<NP>::NS;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     clock_a[0] = t0;
     if (clock_b) clock_b[0] = t0;
-    *err = 0;
   }
   // a grid-stride loop: the launcher caps the grid (two CTAs per SM), so
   // that a load and a field write-back over the host link can share the SMs

@@ -20,7 +20,6 @@ struct StepIO {
   void* f_out;
   const double* clock_in;
   double* clock_out;
-  int* err;  // device error word (bounded waits)
 };
 
 struct FieldsIO {
@@ -41,14 +40,10 @@ struct Ops {
   int D, NP, NC, Q;
   size_t real_size, store_size;
   int stored_phi_planes;
-  int fused;  // 1: one launch per step (2D), 0: phase-field + transport launches (3D)
   // opts the step kernels in to their dynamic shared memory (once per process)
   cudaError_t (*configure)();
-  // one time step S^n -> S^{n+1}
+  // one time step S^n -> S^{n+1}: one fused launch
   cudaError_t (*step)(const void* params, const StepIO& io, cudaStream_t s);
-  // its two launches separately: phase field, then chemical potential + LBM
-  cudaError_t (*step_pf)(const void* params, const StepIO& io, cudaStream_t s);
-  cudaError_t (*step_transport)(const void* params, const StepIO& io, cudaStream_t s);
   // exchange planes (Real) -> stored state; src_f may be null (rest)
   cudaError_t (*load)(const void* params, const void* src_phi, const void* src_mu,
                       const void* src_f, void* phi, void* mu, void* f, cudaStream_t s);
@@ -56,7 +51,7 @@ struct Ops {
   // be null), in one launch
   cudaError_t (*load_state)(const void* params, const void* src_phi, const void* src_mu,
                             const void* src_f, void* phi, void* mu, void* f, double* clock_a,
-                            double* clock_b, double t0, int* err, cudaStream_t s);
+                            double* clock_b, double t0, cudaStream_t s);
   cudaError_t (*fields)(const void* params, const FieldsIO& io, cudaStream_t s);
   cudaError_t (*invariants)(const InvParams& p, const void* phi, const void* mu, const void* f,
                             double* partial, int blocks, double* out, cudaStream_t s);
@@ -132,12 +127,6 @@ struct Impl {
     return cudaGetLastError();
   }
 
-  // the step is one launch; the second half of a timed step is empty
-  static cudaError_t step_pf(const void* params, const StepIO& io, cudaStream_t s) {
-    return step_fused(params, io, s);
-  }
-  static cudaError_t step_transport(const void*, const StepIO&, cudaStream_t) { return cudaSuccess; }
-
   static cudaError_t step(const void* params, const StepIO& io, cudaStream_t s) {
     return step_fused(params, io, s);
   }
@@ -161,7 +150,7 @@ struct Impl {
 
   static cudaError_t load_state(const void* params, const void* src_phi, const void* src_mu,
                                 const void* src_f, void* phi, void* mu, void* f, double* clock_a,
-                                double* clock_b, double t0, int* err, cudaStream_t s) {
+                                double* clock_b, double t0, cudaStream_t s) {
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     const long long cells = (long long)P.n[0] * P.n[1] * P.n[2];
     constexpr int V = 16 / (int)sizeof(Real);  // one 16-byte word of each source plane
@@ -176,11 +165,11 @@ struct Impl {
     if (vec)
       load_state_kernel<NP, NC, Q, Real, Store, V><<<blocks, threads, 0, s>>>(
           cells, P.n[0], P.px, P.plane, sp, sm, sf, static_cast<Real*>(phi), static_cast<Real*>(mu),
-          static_cast<Store*>(f), clock_a, clock_b, t0, err);
+          static_cast<Store*>(f), clock_a, clock_b, t0);
     else
       load_state_kernel<NP, NC, Q, Real, Store, 1><<<blocks, threads, 0, s>>>(
           cells, P.n[0], P.px, P.plane, sp, sm, sf, static_cast<Real*>(phi), static_cast<Real*>(mu),
-          static_cast<Store*>(f), clock_a, clock_b, t0, err);
+          static_cast<Store*>(f), clock_a, clock_b, t0);
     return cudaGetLastError();
   }
 
@@ -214,11 +203,8 @@ struct Impl {
                             sizeof(Real),
                             sizeof(Store),
                             PhiStore<NP>::NS,
-                            1,
                             &Impl::configure,
                             &Impl::step,
-                            &Impl::step_pf,
-                            &Impl::step_transport,
                             &Impl::load,
                             &Impl::load_state,
                             &Impl::fields,

@@ -361,8 +361,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
         for (int a = 0; a < NP; ++a)
 #pragma unroll
           for (int b = a + 1; b < NP; ++b) {
+            // a pair with a phase absent from the stencil has q = 0: exactly 0
             const Real gab = P.gamma[a][b];
-            if (gab == Real(0)) continue;
+            if (gab == Real(0) || (grp & ((1u << a) | (1u << b))) != ((1u << a) | (1u << b))) continue;
             Real q[2];
             q[d] = pf[a] * gn[b] - pf[b] * gn[a];
             q[1 - d] = pf[a] * gt[b] - pf[b] * gt[a];
@@ -399,8 +400,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
       for (int a = 0; a < NP; ++a)
 #pragma unroll
         for (int b = a + 1; b < NP; ++b) {
+          // a phase absent from the 3x3 neighbourhood: q = 0, exactly 0
           const Real gab = P.gamma[a][b];
-          if (gab == Real(0)) continue;
+          if (gab == Real(0) || (act & ((1u << a) | (1u << b))) != ((1u << a) | (1u << b))) continue;
           Real q[2], v[2];
           q[0] = ph[a] * gc[b][0] - ph[b] * gc[a][0];
           q[1] = ph[a] * gc[b][1] - ph[b] * gc[a][1];

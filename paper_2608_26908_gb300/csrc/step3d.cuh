@@ -209,8 +209,15 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
             MK(pb, ib - st) | MK(pa - 1, ia) | MK(pb - 1, ib) | MK(pa + 1, ia) | MK(pb + 1, ib);
     }
     if (__popc(grp) < 2 || closed) return;
+    // A phase whose mask bit is clear in every cell the stencil reads is
+    // exactly 0 there: its face value and gradient are 0, so every pair it
+    // belongs to has q = 0 and contributes exactly 0.  Such phases and pairs
+    // are skipped (two or three of the four phases at most interfaces).
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
+      pf[a] = Real(0);
+      g3[a][0] = g3[a][1] = g3[a][2] = Real(0);
+      if (!(grp & (1u << a))) continue;
       const Real va = PH(pa, a, ia), vb = PH(pb, a, ib);
       pf[a] = Real(0.5) * (va + vb);
       if (d == 2) {
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
 #pragma unroll
       for (int b = a + 1; b < NP; ++b) {
         const Real gab = P.gamma[a][b];
-        if (gab == Real(0)) continue;
+        if (gab == Real(0) || (grp & ((1u << a) | (1u << b))) != ((1u << a) | (1u << b))) continue;
         Real q[3];
 #pragma unroll
         for (int t = 0; t < 3; ++t) q[t] = pf[a] * g3[b][t] - pf[b] * g3[a][t];
@@ -431,6 +438,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
           const Real* fa = s_flux + a * (S::PFX + S::PFY);
           div[a] = (fa[ty * (BX + 1) + tx + 1] - fa[ty * (BX + 1) + tx]) +
                    (fa[S::PFX + (ty + 1) * BX + tx] - fa[S::PFX + ty * BX + tx]) + (pfz_hi[a] - pfz_lo[a]);
+          // a phase absent from the 3x3x3 neighbourhood has a zero central
+          // gradient, and its pairs contribute exactly 0 below
+          gc[a][0] = gc[a][1] = gc[a][2] = Real(0);
+          if (!(act & (1u << a))) continue;
           gc[a][0] = Real(0.5) * (PH(C, a, r2 + 1) - PH(C, a, r2 - 1));
           gc[a][1] = Real(0.5) * (PH(C, a, r2 + W2) - PH(C, a, r2 - W2));
           gc[a][2] = Real(0.5) * (PH(C + 1, a, r2) - PH(C - 1, a, r2));
@@ -446,7 +457,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
 #pragma unroll
           for (int b = a + 1; b < NP; ++b) {
             const Real gab = P.gamma[a][b];
-            if (gab == Real(0)) continue;
+            if (gab == Real(0) || (act & ((1u << a) | (1u << b))) != ((1u << a) | (1u << b))) continue;
             Real q[3], v[3];
 #pragma unroll
             for (int t = 0; t < 3; ++t) q[t] = ph[a] * gc[b][t] - ph[b] * gc[a][t];
