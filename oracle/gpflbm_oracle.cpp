@@ -26,9 +26,10 @@
 // case, 1+delta*cos(4 theta) anisotropy, interpolation sum rule, FTCS heat
 // kernel for frozen liquid, Taylor-Green decay, Poiseuille between walls,
 // uniform body force, lattice moment identities, exact conservation,
-// quiescent melt.  The antitrapping coefficient has no closed-form pin:
-// parity unpinned for that single term (it is only checked to conserve
-// solute and to vanish at rest).
+// quiescent melt, the thin-interface chemical-potential jump of a slowly
+// moving planar front with and without the antitrapping current, a
+// manufactured solution for the anisotropic face fluxes, and the closed-form
+// soft-argmax of a sharp step for the objective.
 
 #include <algorithm>
 #include <cmath>

@@ -31,6 +31,15 @@ Parameter readings (lattice units, dx = dt = 1):
 * temperature coupling S_a = 2 A_a |c_l^eq - c_a^eq|^2, so that a melt at
   mu = 0 and undercooling u is the melt at supersaturation u;
 * drag: h = 2.757, W0 = eps;
+* antitrapping coefficient a_at = pi^2/16: for the current
+  -a_at eps phi_l [c_l - c_a] (dphi_a/dt) n_a with the mobility
+  M = D phi_l / (2 A) and h_l = phi_l^2 (3 - 2 phi_l) on the obstacle
+  profile, the solute balance across a slowly moving planar interface
+  leaves a chemical-potential jump proportional to
+  int (h_l / phi_l - Theta) dxi - a_at eps = (pi^2/16 - a_at) eps
+  (thin-interface analysis of the one-sided model), so pi^2/16 removes the
+  solute trapping of order V eps / D; the pi/4 of the obstacle-potential
+  literature belongs to a current weighted differently;
 * the eutectics' isotherm T = T_E sits theta0 / G above the top of the
   initial solid, theta0 the front undercooling at which that solid grows
   at about V under the model's capillarity (oracle runs of one lamella
@@ -77,7 +86,10 @@ def _blank_params():
         "tau_f": 0.8, "tau_phi": 1.0, "eps": 4.0,
         "gamma": [row[:] for row in z4], "delta": [row[:] for row in z4],
         "A": [1.0] * 4, "ceq": [[0.0, 0.0] for _ in range(4)], "S": [0.0] * 4,
-        "D_liq": 0.02, "a_at": math.pi / 4.0, "h_drag": 2.757, "W0": 4.0,
+        # antitrapping: pi^2/16 cancels the chemical-potential jump of the
+        # obstacle profile for this current (liquid-weighted, divided by the
+        # mobility D phi_l / (2 A)), see the module docstring
+        "D_liq": 0.02, "a_at": math.pi ** 2 / 16.0, "h_drag": 2.757, "W0": 4.0,
         "gbeta_c": [0.0, 0.0], "c_ref": [0.0, 0.0], "gbeta_T": 0.0, "T_ref": 1.0,
         "T_E": 1.0, "undercool": 0.0, "G": 0.0, "V": 0.0, "v0": 0.0,
         "q_floor": 1e-12,

@@ -1030,3 +1030,138 @@ def test_simplex_projection_matches_enumeration_of_supports():
         want = _projection_by_enumeration(v)
         np.testing.assert_allclose(got, want, rtol=0, atol=1e-14, err_msg=str(v))
         assert abs(got.sum() - 1.0) < 1e-14 and (got >= 0).all()
+
+
+# ----------------------------------------------------------------- antitrapping
+def test_antitrapping_current_cancels_the_thin_interface_trapping():
+    """Slow planar front pulled at V through a gradient (tests/thin_interface.py):
+    the chemical-potential jump across the interface, normalised by
+    2 A v dc eps / D, is -(pi^2/16 - a_at) + O(v eps / D) by the thin-interface
+    solute balance of the obstacle profile.  Without the current the jump is
+    the trapping level -pi^2/16 at every width; the current adds exactly
+    a_at (at a_at = pi^2/16 and pi/4); at a_at = pi^2/16 what is left is
+    small and falls with the Peclet number.  A wrong sign, a dropped liquid
+    weight, a wrong power of eps or a missing normal in the current fails."""
+    import concurrent.futures
+    import multiprocessing
+
+    import thin_interface
+
+    a_star = math.pi ** 2 / 16.0
+    runs = {("4", "0"): (4.0, 0.0, {}), ("4", "a*"): (4.0, a_star, {}),
+            ("8", "0"): (8.0, 0.0, {}), ("8", "a*"): (8.0, a_star, {}),
+            ("8", "pi/4"): (8.0, math.pi / 4.0, {}),
+            ("8", "a*", "slow"): (8.0, a_star, {"V": 5e-4, "steps": 48000, "L": 300})}
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(max_workers=min(len(runs), os.cpu_count() or 1),
+                                                mp_context=ctx) as pool:
+        fut = {k: pool.submit(thin_interface.case, e, a, **kw) for k, (e, a, kw) in runs.items()}
+        r = {k: f.result() for k, f in fut.items()}
+    for e in ("4", "8"):
+        j0, js = r[e, "0"]["jhat"], r[e, "a*"]["jhat"]
+        assert r[e, "0"]["jump"] < 0.0                         # the solid traps solute
+        assert abs(j0 + a_star) < 0.1, (e, j0)                 # trapping level -pi^2/16
+        tol = 0.08 if e == "4" else 0.05
+        assert abs((js - j0) / a_star - 1.0) < tol, (e, js - j0)  # the current adds a_at
+        assert abs(js) < 0.1 and abs(js) < abs(j0) / 5.0, (e, js)
+    jp = r["8", "pi/4"]["jhat"] - r["8", "0"]["jhat"]
+    assert abs(jp / (math.pi / 4.0) - 1.0) < 0.05, jp
+    assert r["8", "pi/4"]["jhat"] > 0.05                       # pi/4 over-corrects
+    slow, fast = r["8", "a*", "slow"], r["8", "a*"]
+    assert slow["p"] < 0.6 * fast["p"]
+    assert abs(slow["jhat"]) < 0.7 * abs(fast["jhat"]), (slow["jhat"], fast["jhat"])
+
+
+# ----------------------------------------------------------------- anisotropic faces
+def _manufactured_divergence(dim, n, delta, theta):
+    """Relative max error of the oracle's discrete divergence of dA/dq at the
+    faces, scaled by n^2, against the analytic div(dA/dq(grad S)) for a
+    smooth field S without critical points (sampled s(x) = S(x / n), walls
+    on every axis, cells at least three from a wall)."""
+    sp = pytest.importorskip("sympy")
+    q = sp.symbols("q0:%d" % dim, real=True)
+    c, s_ = sp.cos(theta), sp.sin(theta)
+    r = [c * q[0] + s_ * q[1], -s_ * q[0] + c * q[1]] + ([q[2]] if dim == 3 else [])
+    s2 = sum(v ** 2 for v in r)
+    s4 = sum(v ** 4 for v in r)
+    A = (1 - delta * (3 - 4 * s4 / s2 ** 2)) ** 2 * s2
+    hess_A = sp.lambdify(q, sp.hessian(A, q), "numpy")
+    X = sp.symbols("X0:%d" % dim, real=True)
+    nv = np.array([1.0, 0.7, 0.4][:dim])
+    nv /= np.linalg.norm(nv)
+    amp = sp.Rational(1, 50) if dim == 2 else sp.Rational(1, 125)
+    wave = sp.sin(2 * sp.pi * X[0]) * sp.cos(2 * sp.pi * X[1])
+    if dim == 3:
+        wave *= sp.sin(2 * sp.pi * X[2])
+    S = sp.Rational(1, 2) + sp.Rational(3, 20) * sum(float(nv[i]) * (X[i] - sp.Rational(1, 2))
+                                                     for i in range(dim)) + amp * wave
+    S_f = sp.lambdify(X, S, "numpy")
+    grad_f = [sp.lambdify(X, sp.diff(S, x), "numpy") for x in X]
+    hess_f = [[sp.lambdify(X, sp.diff(S, a, b), "numpy") for b in X] for a in X]
+
+    sc = inputs.scenario("dendrite3d" if dim == 3 else "dendrite2d", nx=n, ny=n,
+                         nz=n if dim == 3 else None, precision="fp64")
+    sc["grid"]["bc"] = [1, 1, 1]
+    sc["grid"]["wall_rows"] = [0, 0, 0]
+    p = sc["params"]
+    p["gbeta_c"], p["gbeta_T"], p["undercool"], p["G"] = [0.0, 0.0], 0.0, 0.0, 0.0
+    p["tau_phi"] = 50.0  # a small step: no value leaves (0, 1)
+    for a, b in ((0, 1), (1, 0)):
+        p["delta"][a][b] = delta
+        p["tilt"][a][b] = theta
+    idx = np.indices((n,) * dim)[::-1]  # x, y(, z), x fastest
+    Xs = [i.reshape(-1) / n for i in idx]
+    one = np.ones(n ** dim)
+    s0 = S_f(*Xs) * one
+    phi1, _, _ = oracle.run(sc, np.concatenate([1.0 - s0, s0]), np.zeros(n ** dim),
+                            oracle.rest_populations(sc), 1)
+    s1 = phi1[n ** dim:]
+    eps, gam, tau = p["eps"], p["gamma"][0][1], p["tau_phi"]
+    # N = 2 at mu = 0, T = T_E: tau eps ds/dt = (eps gam Dh - 16 gam (1 - 2 s) / (pi^2 eps)) / 2,
+    # Dh the discrete divergence of dA/dq at the faces (centre terms cancel)
+    Dh = (2.0 * tau * eps * (s1 - s0) + 16.0 * gam / (math.pi ** 2 * eps) * (1.0 - 2.0 * s0)) / (eps * gam)
+    g = [gf(*Xs) * one for gf in grad_f]
+    HA = np.array(hess_A(*g), dtype=np.float64)
+    div = sum(HA[a][b] * (hess_f[a][b](*Xs) * one) for a in range(dim) for b in range(dim))
+    inner = np.all([(i >= 3) & (i <= n - 4) for i in idx], axis=0).reshape(-1)
+    return np.abs(n * n * Dh - div)[inner].max() / np.abs(div[inner]).max()
+
+
+@pytest.mark.parametrize("dim,sizes", [(2, (32, 64, 128)), (3, (16, 32, 64))])
+def test_anisotropic_face_divergence_converges_at_second_order(dim, sizes):
+    """Manufactured solution for the face stencil [R9] with strong cubic
+    anisotropy (delta = 0.3) on turned axes (theta = 0.3): the anisotropic
+    flux's normal component depends on the transverse face gradients, so a
+    wrong transverse stencil (even one that keeps the cubic symmetry) stops
+    the convergence; the error falls four-fold per halving of the spacing."""
+    e = [_manufactured_divergence(dim, n, 0.3, 0.3) for n in sizes]
+    assert e[-1] < 0.01, e
+    assert e[-2] / e[-1] > 3.5 and e[0] / e[1] > 3.0, e
+
+
+# ----------------------------------------------------------------- objective
+def test_objective_of_a_sharp_step_has_the_closed_form():
+    """J = w_frac mean h_1 + w_tip tip / nx [R23].  For a sharp solid block the
+    mean of h_1 is the solid share of the cells, and along the ray the logits
+    are kappa r for r <= R and 0 beyond, so the soft-argmax is a ratio of
+    geometric sums: with x = e^kappa and M = nx - 1 - x0,
+    tip = [x (1 - (R+1) x^R + R x^(R+1)) / (1-x)^2 + (M(M+1) - R(R+1)) / 2]
+          / [(x^(R+1) - 1) / (x - 1) + M - R].
+    kappa = 0 gives the plain mean M / 2."""
+    nx, ny, x0, y0, R = 48, 20, 10, 9, 13
+    sc = inputs.scenario("dendrite2d", nx=nx, ny=ny, precision="fp64")
+    solid = np.zeros((ny, nx))
+    solid[4:15, 3:x0 + R + 1] = 1.0
+    phi = np.concatenate([(1.0 - solid).reshape(-1), solid.reshape(-1)])
+    M = nx - 1 - x0
+    for kappa in (2.0, 0.7):
+        x = math.exp(kappa)
+        num = x * (1 - (R + 1) * x ** R + R * x ** (R + 1)) / (1 - x) ** 2 + (M * (M + 1) - R * (R + 1)) / 2
+        den = (x ** (R + 1) - 1) / (x - 1) + M - R
+        for wf, wt in ((1.0, 0.0), (0.0, 1.0), (0.3, 2.0)):
+            obj = {"w_frac": wf, "w_tip": wt, "kappa": kappa, "x0": x0, "y0": y0, "solid": 1}
+            J = oracle.objective_value(sc, obj, phi)
+            want = wf * solid.sum() / solid.size + wt * (num / den) / nx
+            assert J == pytest.approx(want, rel=1e-13, abs=1e-15)
+    obj = {"w_frac": 0.0, "w_tip": 1.0, "kappa": 0.0, "x0": x0, "y0": y0, "solid": 1}
+    assert oracle.objective_value(sc, obj, phi) == pytest.approx(M / 2.0 / nx, rel=1e-14)
