@@ -303,6 +303,21 @@ gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizo
                              void* workspace, size_t workspace_bytes, double* J, double* dparams,
                              void* dmu0, int dst_is_device, void* stream);
 
+/* Vector-Jacobian product of the discrete map from the current state S^t0
+ * through `horizon` = H steps: the same reverse sweep, checkpointing and
+ * configurations as gpflbm_adjoint, for the linear functional
+ *   J = sum_x [ seed_s phi_1 + seed_mu mu + sum_k seed_k f_k ](S^{t0+H})
+ * instead of the objective.  seed: 11 planes in the exchange layout and type
+ * (phi_1, mu, f_0 .. f_8; phi_0 = 1 - phi_1 is not a free variable of the
+ * two-phase state).  grad (may be NULL): the 11 planes of dJ/dS^t0 in the
+ * same layout (dJ/dphi_1, dJ/dmu, dJ/df_k).  dparams (may be NULL): as in
+ * gpflbm_adjoint.  flags: GPFLBM_ON_DEVICE when seed and grad are device
+ * memory, else host memory (staged plane by plane); GPFLBM_ASYNC is
+ * accepted and changes nothing.  Workspace as for gpflbm_adjoint.  The
+ * handle is left at S^{t0+H}.  Synchronises `stream`. */
+gpflbm_status gpflbm_vjp(gpflbm_t h, int horizon, int ckpt_every, void* workspace, size_t workspace_bytes,
+                         const void* seed, void* grad, double* dparams, int flags, void* stream);
+
 /* Step counter of the current state (the t of T(v, t)). */
 gpflbm_status gpflbm_time(gpflbm_t h, long long* t);
 

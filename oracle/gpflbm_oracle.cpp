@@ -1024,6 +1024,42 @@ int oracle_objective(const OracleProblem* p, const OracleObjective* o, long n0, 
   return 0;
 }
 
+// Jacobian-vector product of n_steps steps: the state after n_steps and
+// its exact tangent along the initial-state tangent (dphi, dmu, df, each
+// NULL for zero) and the parameter tangent dcoef (as in oracle_objective),
+// by forward-mode dual numbers.  Outputs: t_phi, t_mu, t_f (N, K-1 and Q
+// planes of the tangent of the final state; any may be NULL).
+int oracle_tangent(const OracleProblem* p, long n0, int n_steps, const double* phi, const double* mu,
+                   const double* f, const double* dphi, const double* dmu, const double* df,
+                   const double* dcoef, double* t_phi, double* t_mu, double* t_f) {
+  if (check(p)) return -1;
+  Grid g(p);
+  Lattice L = make_lattice(p->q);
+  Coeffs<Dual> k;
+  k.inv_tau_phi = Dual(1.0 / p->tau_phi, dcoef ? dcoef[0] : 0.0);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      k.delta[a][b] = Dual(p->delta[a][b], (dcoef && p->delta[a][b] != 0.0) ? dcoef[1] : 0.0);
+  k.gbeta_c[0] = Dual(p->gbeta_c[0], dcoef ? dcoef[2] : 0.0);
+  k.gbeta_c[1] = Dual(p->gbeta_c[1], 0.0);
+  State<Dual> s;
+  const long cells = g.cells;
+  s.phi.resize((long)p->n_phases * cells);
+  s.mu.resize((long)p->n_solutes * cells);
+  s.f.resize((long)L.q * cells);
+  for (long i = 0; i < (long)s.phi.size(); ++i) s.phi[i] = Dual(phi[i], dphi ? dphi[i] : 0.0);
+  for (long i = 0; i < (long)s.mu.size(); ++i) s.mu[i] = Dual(mu[i], dmu ? dmu[i] : 0.0);
+  for (long i = 0; i < (long)s.f.size(); ++i) s.f[i] = Dual(f[i], df ? df[i] : 0.0);
+  for (int n = 0; n < n_steps; ++n) step(g, L, k, s, n0 + n);
+  if (t_phi)
+    for (long i = 0; i < (long)s.phi.size(); ++i) t_phi[i] = s.phi[i].d;
+  if (t_mu)
+    for (long i = 0; i < (long)s.mu.size(); ++i) t_mu[i] = s.mu[i].d;
+  if (t_f)
+    for (long i = 0; i < (long)s.f.size(); ++i) t_f[i] = s.f[i].d;
+  return 0;
+}
+
 // Plain-double objective of a given state (for finite differences).
 int oracle_objective_value(const OracleProblem* p, const OracleObjective* o, const double* phi,
                            double* J) {

@@ -82,6 +82,8 @@ def lib():
         L.oracle_invariants.argtypes = [P, ctypes.c_long, dp, dp, dp, dp]
         L.oracle_objective.argtypes = [P, O, ctypes.c_long, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp]
         L.oracle_objective_value.argtypes = [P, O, dp, dp]
+        L.oracle_tangent.argtypes = [P, ctypes.c_long, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp, dp,
+                                     dp, dp]
         L.oracle_lattice.argtypes = [ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int)]
         L.oracle_gradient_energy.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                              ctypes.c_double, dp,
@@ -284,3 +286,20 @@ def objective_value(sc, obj, phi):
     if lib().oracle_objective_value(ctypes.byref(p), ctypes.byref(o), _dp(phi), ctypes.byref(J)) != 0:
         raise ValueError("oracle_objective_value rejected the problem")
     return J.value
+
+
+def tangent(sc, phi, mu, f, n_steps, dphi=None, dmu=None, df=None, dcoef=None, n0=0):
+    """Jacobian-vector product of n_steps steps (forward-mode duals): the
+    tangent (phi, mu, f planes) of the state after n_steps along the initial
+    tangent (dphi, dmu, df; None = 0) and the parameter tangent dcoef
+    (1/tau_phi, delta, g beta_c)."""
+    p = problem(sc)
+    cells = p.nx * p.ny * (p.nz if p.dim == 3 else 1)
+    arr = [np.ascontiguousarray(a, dtype=np.float64) for a in (phi, mu, f)]
+    tan = [None if a is None else np.ascontiguousarray(a, dtype=np.float64) for a in (dphi, dmu, df, dcoef)]
+    out = (np.zeros(p.n_phases * cells), np.zeros(p.n_solutes * cells), np.zeros(p.q * cells))
+    rc = lib().oracle_tangent(ctypes.byref(p), int(n0), int(n_steps), *[_dp(a) for a in arr],
+                              *[_dp(a) for a in tan], *[_dp(a) for a in out])
+    if rc != 0:
+        raise ValueError("oracle_tangent rejected the problem")
+    return out

@@ -88,8 +88,15 @@ struct AdjImpl {
     return cudaGetLastError();
   }
 
+  static cudaError_t import_plane(const void* p, const void* src, void* dst, cudaStream_t st) {
+    const DevParams<Real>& P = par(p);
+    adj_import_kernel<Real><<<cell_blocks(P), kThreads, 0, st>>>(P, static_cast<const Real*>(src),
+                                                                 static_cast<Real*>(dst));
+    return cudaGetLastError();
+  }
+
   static const AdjOps* table() {
-    static const AdjOps t = {sizeof(Real), configure, init, tip, frac, step, sum, export_plane};
+    static const AdjOps t = {sizeof(Real), configure, init, tip, frac, step, sum, export_plane, import_plane};
     return &t;
   }
 };

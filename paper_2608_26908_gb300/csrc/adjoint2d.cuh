@@ -668,4 +668,15 @@ __global__ void adj_export_kernel(const DevParams<Real> P, const Real* __restric
   dst[c] = src[off2(P, x, y)];
 }
 
+// One plane from the exchange layout into the internal layout.
+template <class Real>
+__global__ void adj_import_kernel(const DevParams<Real> P, const Real* __restrict__ src, Real* __restrict__ dst) {
+  const long long cells = (long long)P.n[0] * P.n[1];
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= cells) return;
+  int x, y;
+  cell_xy(P, c, &x, &y);
+  dst[off2(P, x, y)] = src[c];
+}
+
 }  // namespace gpflbm

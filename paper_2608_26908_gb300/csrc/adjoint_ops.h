@@ -43,6 +43,8 @@ struct AdjOps {
   cudaError_t (*sum)(const void* P, const double* v, double* partial, int blocks, cudaStream_t st);
   // one plane to the exchange layout (x fastest, no padding)
   cudaError_t (*export_plane)(const void* P, const void* src, void* dst, cudaStream_t st);
+  // one plane from the exchange layout into the internal layout
+  cudaError_t (*import_plane)(const void* P, const void* src, void* dst, cudaStream_t st);
 };
 
 // Table for FP64 (fp64 != 0) or FP32 arithmetic.

@@ -1001,9 +1001,12 @@ gpflbm_status adj_check(gpflbm_t h, int H, int K) {
   return GPFLBM_OK;
 }
 
+// With obj the adjoint seed is dJ/dS of the objective of the final state;
+// with seed (obj NULL) it is the 11 given planes (a linear functional of
+// the final state), and grad receives all 11 planes of lambda^{t0}.
 gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const AdjLayout& L,
                           unsigned char* ws, double* J, double* dparams, void* dmu0, int dst_is_device,
-                          cudaStream_t s) {
+                          cudaStream_t s, const void* seed = nullptr, void* grad = nullptr) {
   const gpflbm::AdjOps* A = gpflbm::adjoint_ops(h->grid.precision == GPFLBM_FP64);
   const void* P = dev_params(h);
   const size_t pl = (size_t)h->plane * h->ops->real_size;
@@ -1089,10 +1092,27 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
   const long long want = (h->cells + gpflbm::kRedThreads - 1) / gpflbm::kRedThreads;
   const int blocks = (int)(want < gpflbm::kRedMaxBlocks ? want : gpflbm::kRedMaxBlocks);
   const void* s_fin = st_at(last, seg_len(last));
-  e = A->frac(P, s_fin, partial, blocks, s);
-  if (e == cudaSuccess) e = A->init(P, s_fin, obj->w_frac, lam[0], lam[0] + pl, lam[0] + 2 * pl, gacc, s);
-  if (e == cudaSuccess) e = A->tip(P, s_fin, obj->x0, obj->y0, obj->kappa, obj->w_tip, lam[0], tip, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: objective");
+  const bool on_device = (dst_is_device & GPFLBM_ON_DEVICE) != 0;
+  const size_t exch = (size_t)h->cells * h->ops->real_size;  // one exchange plane
+  if (obj) {
+    e = A->frac(P, s_fin, partial, blocks, s);
+    if (e == cudaSuccess) e = A->init(P, s_fin, obj->w_frac, lam[0], lam[0] + pl, lam[0] + 2 * pl, gacc, s);
+    if (e == cudaSuccess) e = A->tip(P, s_fin, obj->x0, obj->y0, obj->kappa, obj->w_tip, lam[0], tip, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: objective");
+  } else {
+    // lambda^{t0+H} = seed, plane by plane (host planes through the stage area)
+    e = cudaMemsetAsync(lam[0], 0, L.state, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(gacc, 0, 3 * (size_t)h->plane * sizeof(double), s);
+    for (int k = 0; k < 11 && e == cudaSuccess; ++k) {
+      const unsigned char* src = static_cast<const unsigned char*>(seed) + (size_t)k * exch;
+      if (!on_device) {
+        e = cudaMemcpyAsync(at(h, h->lay.stage), src, exch, cudaMemcpyHostToDevice, s);
+        src = static_cast<const unsigned char*>(at(h, h->lay.stage));
+      }
+      if (e == cudaSuccess) e = A->import_plane(P, src, lam[0] + (size_t)k * pl, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "vjp: seed");
+  }
 
   // backward: segment c's adjoint steps on `s` while segment c-1 is
   // recomputed on the auxiliary stream
@@ -1141,8 +1161,16 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint: stream order");
 
   // outputs
+  if (grad) {
+    for (int k = 0; k < 11 && e == cudaSuccess; ++k) {
+      unsigned char* dst = static_cast<unsigned char*>(grad) + (size_t)k * exch;
+      e = A->export_plane(P, lam[cur] + (size_t)k * pl, on_device ? dst : at(h, h->lay.stage), s);
+      if (e == cudaSuccess && !on_device)
+        e = cudaMemcpyAsync(dst, at(h, h->lay.stage), exch, cudaMemcpyDeviceToHost, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "vjp: gradient");
+  }
   if (dmu0) {
-    const bool on_device = (dst_is_device & GPFLBM_ON_DEVICE) != 0;
     void* target = on_device ? dmu0 : at(h, h->lay.stage);
     e = A->export_plane(P, lam[cur] + pl, target, s);
     if (e == cudaSuccess && !on_device)
@@ -1166,7 +1194,7 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     sums[j] = t;
   }
   const double tip_v = host[4 * (size_t)gpflbm::kRedMaxBlocks];
-  if (J) *J = obj->w_frac * (sums[0] / (double)h->cells) + obj->w_tip * tip_v / (double)h->grid.nx;
+  if (J && obj) *J = obj->w_frac * (sums[0] / (double)h->cells) + obj->w_tip * tip_v / (double)h->grid.nx;
   if (dparams)
     for (int j = 0; j < 3; ++j) dparams[j] = sums[j + 1];
   return GPFLBM_OK;
@@ -1219,6 +1247,41 @@ gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizo
   st = adjoint_run(h, obj, horizon, L, ws, J, dparams, dmu0, dst_is_device, s);
   if (own) {
     cudaStreamSynchronize(s);  // nothing may still use the block
+    cudaFree(ws);
+  }
+  return st;
+}
+
+gpflbm_status gpflbm_vjp(gpflbm_t h, int horizon, int ckpt_every, void* workspace, size_t workspace_bytes,
+                         const void* seed, void* grad, double* dparams, int flags, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  gpflbm_status st = adj_check(h, horizon, ckpt_every);
+  if (st != GPFLBM_OK) return st;
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "vjp: no state loaded");
+  if (flags & ~(GPFLBM_ON_DEVICE | GPFLBM_ASYNC)) return fail(h, GPFLBM_ERR_ARG, "vjp: unknown flag");
+  if (!seed) return fail(h, GPFLBM_ERR_ARG, "vjp: seed is NULL");
+  ++h->mut;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const AdjLayout L = adj_layout(h, horizon, ckpt_every);
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  bool own = false;
+  if (ws) {
+    if (workspace_bytes < L.total) return fail(h, GPFLBM_ERR_OOM, "vjp: workspace too small");
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign != 0)
+      return fail(h, GPFLBM_ERR_ARG, "vjp: workspace not 256-byte aligned");
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, GPFLBM_ERR_OOM, "vjp: cudaMalloc of the workspace failed");
+    }
+    ws = static_cast<unsigned char*>(p);
+    own = true;
+  }
+  st = adjoint_run(h, nullptr, horizon, L, ws, nullptr, dparams, nullptr, flags, s, seed, grad);
+  if (own) {
+    cudaStreamSynchronize(s);
     cudaFree(ws);
   }
   return st;

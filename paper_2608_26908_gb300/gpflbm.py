@@ -95,6 +95,7 @@ def lib():
         L.gpflbm_time.argtypes = [vp, ctypes.POINTER(ll)]
         L.gpflbm_adjoint_workspace_bytes.argtypes = [vp, i, i, ctypes.POINTER(sz)]
         L.gpflbm_adjoint.argtypes = [vp, ctypes.POINTER(Objective), i, i, vp, sz, dp, dp, vp, i, vp]
+        L.gpflbm_vjp.argtypes = [vp, i, i, vp, sz, vp, vp, dp, i, vp]
         L.gpflbm_last_error.argtypes = [vp]
         L.gpflbm_last_error.restype = ctypes.c_char_p
         L.gpflbm_destroy.argtypes = [vp]
@@ -102,7 +103,7 @@ def lib():
         for name in ("gpflbm_workspace_bytes", "gpflbm_create", "gpflbm_set_params",
                      "gpflbm_set_state", "gpflbm_step", "gpflbm_step_timed", "gpflbm_get_fields",
                      "gpflbm_get_deviations", "gpflbm_invariants", "gpflbm_time",
-                     "gpflbm_adjoint_workspace_bytes", "gpflbm_adjoint"):
+                     "gpflbm_adjoint_workspace_bytes", "gpflbm_adjoint", "gpflbm_vjp"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -327,6 +328,20 @@ class Sim:
                                          wbytes, ctypes.byref(J), dpar, dptr, int(device),
                                          _stream(torch)), "adjoint")
         return J.value, np.array(dpar[:]), dmu
+
+    def vjp(self, seed, horizon, ckpt_every):
+        """Vector-Jacobian product of `horizon` steps from the current state:
+        seed is an (11, cells) array of the exchange type (planes phi_1, mu,
+        f_0..f_8 of the final state); returns (grad, dparams) with grad the
+        (11, cells) planes of d<seed, S^{t0+H}>/dS^{t0} and dparams its
+        derivatives by (1/tau_phi, delta_01, gbeta_c[0]).  Host buffers."""
+        seed = np.ascontiguousarray(seed, dtype=self.dtype).reshape(11, self.cells)
+        grad = np.empty((11, self.cells), dtype=self.dtype)
+        dpar = (ctypes.c_double * 3)()
+        self._check(lib().gpflbm_vjp(self.h, int(horizon), int(ckpt_every), None, 0,
+                                     ctypes.c_void_p(seed.ctypes.data), ctypes.c_void_p(grad.ctypes.data),
+                                     dpar, 0, _stream(self.torch)), "vjp")
+        return grad, np.array(dpar[:])
 
 
 def with_parameters(sc, mobility=None, delta=None, gbeta=None):

@@ -228,3 +228,124 @@ def test_full_workload_fp32_gradients_match_fp64():
     assert J32 == pytest.approx(J64, rel=1e-6)
     np.testing.assert_allclose(p32, p64, rtol=1e-4)
     assert np.abs(m32 - m64).max() <= 1e-4 * np.abs(m64).max()
+
+
+# ------------------------------------------------------------------ dot-product tests
+def _dot_case():
+    """40 x 36 FP64 dendrite with a perturbed flow field (f = w + noise), so
+    that every block of the step's Jacobian is exercised."""
+    sc = _case(40, 36, "fp64")
+    phi0, mu0 = inputs.initial_state(sc)
+    w, _ = oracle.lattice(9)
+    cells = inputs.cells(sc)
+    rng = np.random.default_rng(5)
+    f0 = (w[:, None] * (1.0 + 1e-3 * rng.normal(size=(9, cells)))).reshape(-1)
+    return sc, phi0, mu0, f0
+
+
+@pytest.mark.parametrize("block,H,K", [("phase_field", 1, 1), ("chemical_potential", 1, 1),
+                                       ("lattice_boltzmann", 1, 1), ("all", 3, 2)])
+def test_vjp_dot_product_per_stencil(block, H, K):
+    """<J v, w> = <v, J^T w> for each transposed stencil on its own: v and w
+    on the phase field only, on mu only, on the populations only, and on
+    everything over three steps (checkpointed).  J v comes from the oracle's
+    forward-mode dual numbers (an independent code), J^T w from the GPU's
+    gpflbm_vjp.  v is zero on phi where a cell is pure (0 or 1): there the
+    oracle's projection and the GPU's untouched cell are two subgradients of
+    the same kink.  FP64 on both sides."""
+    sc, phi0, mu0, f0 = _dot_case()
+    cells = inputs.cells(sc)
+    rng = np.random.default_rng({"phase_field": 1, "chemical_potential": 2,
+                                 "lattice_boltzmann": 3, "all": 4}[block])
+    v = rng.normal(size=(11, cells))
+    wt = rng.normal(size=(11, cells))
+    s0 = phi0.reshape(2, cells)[1]
+    v[0][(s0 <= 0.0) | (s0 >= 1.0)] = 0.0
+    keep = {"phase_field": [0], "chemical_potential": [1], "lattice_boltzmann": list(range(2, 11)),
+            "all": list(range(11))}[block]
+    for arr in (v, wt):
+        for k in range(11):
+            if k not in keep:
+                arr[k] = 0.0
+    t_phi, t_mu, t_f = oracle.tangent(sc, phi0, mu0, f0, H, dphi=np.concatenate([-v[0], v[0]]),
+                                      dmu=v[1], df=v[2:].reshape(-1))
+    jv_w = (float(np.dot(wt[0], t_phi.reshape(2, cells)[1])) + float(np.dot(wt[1], t_mu)) +
+            float(np.dot(wt[2:].reshape(-1), t_f)))
+    sim = gpflbm.Sim(sc)
+    sim.set_state(phi0, mu0, f0)
+    grad, dpar = sim.vjp(wt, H, K)
+    v_jtw = float(np.sum(v * grad))
+    scale = float(np.abs(v * grad).sum())
+    assert scale > 0.0
+    assert abs(jv_w - v_jtw) <= 1e-10 * scale, (block, jv_w, v_jtw, scale)
+    if block == "all":
+        for j in range(3):
+            dc = np.zeros(3)
+            dc[j] = 1.0
+            tp, tm, tf = oracle.tangent(sc, phi0, mu0, f0, H, dcoef=dc)
+            want = (float(np.dot(wt[0], tp.reshape(2, cells)[1])) + float(np.dot(wt[1], tm)) +
+                    float(np.dot(wt[2:].reshape(-1), tf)))
+            assert dpar[j] == pytest.approx(want, rel=1e-9, abs=1e-12), (j, dpar[j], want)
+
+
+def test_vjp_rejects_unsupported_and_invalid():
+    sc = inputs.scenario("eutectic2d", nx=40, ny=30)
+    sim = gpflbm.Sim(sc)
+    sim.set_state(*inputs.initial_state(sc))
+    with pytest.raises(gpflbm.GpflbmError) as e:
+        sim.vjp(np.zeros((11, inputs.cells(sc))), 2, 1)
+    assert e.value.status == gpflbm.ERR_UNSUPPORTED
+    sc = _case(40, 36, "fp32")
+    sim = gpflbm.Sim(sc)
+    with pytest.raises(gpflbm.GpflbmError) as e:
+        sim.vjp(np.zeros((11, inputs.cells(sc))), 2, 1)  # no state yet
+    assert e.value.status == gpflbm.ERR_STATE
+
+
+# ------------------------------------------------------------------ stated FD check
+def test_fp32_gradients_match_fp64_central_differences_at_the_stated_horizon():
+    """The differentiation workload's own check, on its 64 x 64 crop: FP32
+    adjoint gradients (the configuration's arithmetic) over a 500-step
+    horizon with checkpoints every 50, against FP64 central differences of
+    the GPU forward with step 1e-6 -- dJ/d(1/tau_phi), dJ/d delta, dJ/d g beta_c
+    and dJ/dmu0 along 8 random directions, 1e-4 relative.  Cells whose
+    phase value crosses the clamp between the +h and -h runs (a kink inside
+    the difference) are counted and reported."""
+    H, K, h = 500, 50, 1e-6
+    sc32 = _case(64, 64, "fp32")
+    sc64 = _case(64, 64, "fp64")
+    phi0, mu0 = inputs.initial_state(sc64)
+    _, J32, dpar, dmu = _gpu_adjoint(sc32, H, K)
+    obj = _obj(sc64)
+
+    def J_of(sc, mu, kinks=None):
+        s = gpflbm.Sim(sc)
+        s.set_state(phi0, mu)
+        if kinks is not None:
+            for _ in range(H):
+                s.step(1)
+                ph = s.fields(("phi",))["phi"][1]
+                kinks.append((ph == 0.0) | (ph == 1.0))
+            s.set_state(phi0, mu)
+        return s.adjoint(obj, H, K)[0]
+
+    rng = np.random.default_rng(7)
+    crossed = np.zeros(inputs.cells(sc64), dtype=bool)
+    for i in range(8):
+        v = rng.normal(size=mu0.shape)
+        kp, km = [], []
+        fd = (J_of(sc64, mu0 + h * v, kp) - J_of(sc64, mu0 - h * v, km)) / (2 * h)
+        for a, b in zip(kp, km):
+            crossed |= a != b
+        assert float(np.dot(v, dmu)) == pytest.approx(fd, rel=1e-4), (i, float(np.dot(v, dmu)), fd)
+    base = (1.0 / sc64["params"]["tau_phi"], sc64["params"]["delta"][0][1], sc64["params"]["gbeta_c"][0])
+    for j in range(3):
+        vals = []
+        for sgn in (+1, -1):
+            p = list(base)
+            p[j] += sgn * h
+            vals.append(J_of(gpflbm.with_parameters(sc64, *p), mu0))
+        fdp = (vals[0] - vals[1]) / (2 * h)
+        assert dpar[j] == pytest.approx(fdp, rel=1e-4), (j, dpar[j], fdp)
+    print("cells crossing a clamp kink within +-h over %d steps (8 mu0 directions): %d"
+          % (H, int(crossed.sum())))

@@ -1165,3 +1165,28 @@ def test_objective_of_a_sharp_step_has_the_closed_form():
             assert J == pytest.approx(want, rel=1e-13, abs=1e-15)
     obj = {"w_frac": 0.0, "w_tip": 1.0, "kappa": 0.0, "x0": x0, "y0": y0, "solid": 1}
     assert oracle.objective_value(sc, obj, phi) == pytest.approx(M / 2.0 / nx, rel=1e-14)
+
+
+def test_state_tangent_matches_central_differences():
+    """The oracle's Jacobian-vector product of the whole state (phi, mu, f
+    tangents, forward-mode duals) against central differences of its plain
+    steps on a small dendrite with flow, in a direction that keeps the
+    phase values away from the clamp."""
+    sc = inputs.scenario("dendrite2d", nx=24, ny=20, precision="fp64")
+    sc["params"]["gbeta_c"] = [2e-3, 0.0]
+    phi0, mu0 = inputs.initial_state(sc)
+    w, _ = oracle.lattice(9)
+    cells = 24 * 20
+    rng = np.random.default_rng(9)
+    f0 = (w[:, None] * (1.0 + 1e-3 * rng.normal(size=(9, cells)))).reshape(-1)
+    s = phi0.reshape(2, cells)[1]
+    ds = rng.normal(size=cells) * ((s > 0.05) & (s < 0.95))
+    dphi = np.concatenate([-ds, ds])
+    dmu, df = rng.normal(size=cells), 1e-3 * rng.normal(size=9 * cells)
+    tp, tm, tf = oracle.tangent(sc, phi0, mu0, f0, 2, dphi=dphi, dmu=dmu, df=df)
+    h = 1e-6
+    a = oracle.run(sc, phi0 + h * dphi, mu0 + h * dmu, f0 + h * df, 2)
+    b = oracle.run(sc, phi0 - h * dphi, mu0 - h * dmu, f0 - h * df, 2)
+    for got, pa, pb in zip((tp, tm, tf), a, b):
+        fd = (pa - pb) / (2 * h)
+        assert np.abs(got - fd).max() <= 1e-6 * max(np.abs(fd).max(), 1e-12)

@@ -9,10 +9,13 @@ Tolerances (relative L-infinity per field, see parity.rel_err):
     every population, ~1e-14 after 100 steps, against deviations and momenta
     of 1e-6..1e-5 -- up to ~1e-8 relative.
   FP32 arithmetic: 1e-5 for every field (the stated target).
-  16-bit population storage with FP32 arithmetic: FP16 (x 2^10) 2e-3 for
-    every field but the deviations themselves; BF16 keeps 8 mantissa bits, a
-    relative rounding of 2^-9 = 1.95e-3 on every stored deviation, so U (a sum
-    of them) gets 5e-3 there.
+  16-bit population storage with FP32 arithmetic: 2e-3 for every field,
+    the stored deviations included (the stated target).  FP16 (x 2^10) meets
+    it.  BF16 keeps 8 mantissa bits, a relative rounding of 2^-9 = 1.95e-3 on
+    every stored deviation each step, so it misses the target on U and the
+    deviations (measured 2.4e-3 and 5.4e-3 on the 64^3 crop): those cases
+    are expected failures at the target, and BF16 is a non-conforming
+    variant checked at 6e-3 beside them.
 """
 import numpy as np
 import pytest
@@ -22,7 +25,8 @@ from paper_2608_26908_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-5, "fp32_f16": 2e-3, "fp32_bf16": 5e-3}
+TOL = {"fp64": 1e-10, "fp32": 1e-5, "fp32_f16": 2e-3, "fp32_bf16": 2e-3}
+BF16_MEASURED = 6e-3  # what BF16 storage reaches (U, deviations), above the 2e-3 target
 FP64_LBM = 1e-8  # U and deviations in FP64, see above
 
 
@@ -61,13 +65,27 @@ def test_parity_100_steps(name, prec):
         assert e <= _tol(prec, k), (k, e)
 
 
-@pytest.mark.parametrize("prec", ["fp32_f16", "fp32_bf16"])
+BF16_XFAIL = pytest.mark.xfail(strict=True, reason="BF16 storage misses the 2e-3 target (U 2.4e-3, "
+                                                    "deviations 5.4e-3 on the 64^3 crop)")
+
+
+@pytest.mark.parametrize("prec", ["fp32_f16", pytest.param("fp32_bf16", marks=BF16_XFAIL)])
 def test_parity_reduced_storage(prec):
     sc = _case("dendrite3d", prec)
     errs, sim, got, ref = errors(sc, 100)
     _report("dendrite3d", prec, errs)
-    for k in ("phi", "mu", "c", "rho", "u"):
-        assert errs[k] <= TOL[prec], (k, errs[k])
+    for k, e in errs.items():
+        assert e <= TOL[prec], (k, e)
+
+
+def test_bf16_storage_stated_accuracy():
+    """BF16 storage, the non-conforming 16-bit variant, at what it reaches."""
+    for name, size in (("dendrite3d", CASES["dendrite3d"]), ("dendrite3d", dict(nx=64, ny=64, nz=64))):
+        sc = inputs.scenario(name, precision="fp32_bf16", **size)
+        errs, sim, got, ref = errors(sc, 100)
+        _report(name, "fp32_bf16", errs)
+        for k, e in errs.items():
+            assert e <= (TOL["fp32_bf16"] if k in ("phi", "mu", "c", "rho") else BF16_MEASURED), (k, e)
 
 
 @pytest.mark.parametrize("np_nc", [(4, 2), (3, 2), (2, 2), (4, 1)])
@@ -109,12 +127,14 @@ def test_parity_other_phase_and_solute_counts(np_nc, dim):
         assert e <= _tol("fp64", k), (k, e)
 
 
-def test_bench_workload_full_size_fp32():
-    """The benchmark's workload (2D eutectic, 1024 x 512, FP32) at full size,
-    through the same graph-replayed launches bench.py times."""
-    sc = inputs.scenario("eutectic2d")
-    errs, sim, got, ref = errors(sc, 20, chunks=[16, 3, 1])
-    _report("eutectic2d-full", "fp32", errs)
+@pytest.mark.parametrize("name", ["eutectic2d", "adjoint2d"])
+def test_2d_workloads_full_size_100_steps_fp32(name):
+    """The 2D eutectic (1024 x 512) and the differentiation workload's grid
+    (512 x 512) at full size, FP32, after 100 steps, through the
+    graph-replayed launches (chunks of 16 and 2 and single steps)."""
+    sc = inputs.scenario(name)
+    errs, sim, got, ref = errors(sc, 100, chunks=[16] * 5 + [2, 16, 1, 1])
+    _report(name + "-full", "fp32", errs)
     for k, e in errs.items():
         assert e <= TOL["fp32"], (k, e)
 
@@ -150,18 +170,17 @@ def test_3d_workloads_full_size_fp32(name, steps):
 @pytest.mark.parametrize("name,size,prec", [
     ("dendrite3d", dict(nx=64, ny=64, nz=64), "fp32"),
     ("dendrite3d", dict(nx=64, ny=64, nz=64), "fp32_f16"),
-    ("dendrite3d", dict(nx=64, ny=64, nz=64), "fp32_bf16"),
+    pytest.param("dendrite3d", dict(nx=64, ny=64, nz=64), "fp32_bf16", marks=BF16_XFAIL),
     ("eutectic3d", dict(nx=64, ny=64, nz=128), "fp32"),
 ])
 def test_parity_on_the_stated_3d_crops(name, size, prec):
     """The 3D dendrite on a 64^3 crop (FP32 and both 16-bit storages) and the
-    ternary eutectic on a 64 x 64 x 128 crop, 100 steps."""
+    ternary eutectic on a 64 x 64 x 128 crop, 100 steps, every field at the
+    target (the stored deviations included)."""
     sc = inputs.scenario(name, precision=prec, **size)
     errs, sim, got, ref = errors(sc, 100)
     _report(name + "-crop", prec, errs)
     for k, e in errs.items():
-        if k == "dev" and prec.startswith("fp32_"):
-            continue  # stored populations are rounded to 16 bits
         assert e <= TOL[prec], (k, e)
 
 
