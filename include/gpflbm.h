@@ -146,6 +146,53 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
                             const gpflbm_params* params, void* workspace, size_t workspace_bytes,
                             gpflbm_t* out);
 
+/* Slab decomposition of a 3D grid along the vertical axis (the paper runs
+ * its solver as a domain decomposition over CPU processes, its Appendix A;
+ * here one slab per GPU).  A slab handle owns the planes
+ * v_begin .. v_begin + v_count - 1 (z) of `grid` and keeps two halo planes
+ * on each side in its buffers.  Before every step it needs, from each
+ * neighbouring slab, phi of the two planes next to it and mu and the
+ * populations of the nearest plane (gpflbm_halo_pack on the neighbour,
+ * a transfer of the message, gpflbm_halo_unpack here); its step then gives
+ * bit for bit the values the whole grid's step gives on those planes (the
+ * cells of the halo plane next to a neighbour are collided here as well, and
+ * only their populations that stream into this slab are kept, so nothing
+ * crosses after the step).  The vertical axis must have walls
+ * (bc[2] = GPFLBM_WALL, wall_rows[2] = 0): the slabs at its ends mirror
+ * their own planes there.  Fields, set_state, get_fields, the invariants
+ * (each slab's own cells: the caller sums them) and the step counter act on
+ * the owned planes as a grid of nx x ny x v_count cells.  gpflbm_step takes
+ * n_steps <= 1 on a slab and GPFLBM_ERR_STATE unless every side with a
+ * neighbour was unpacked since the last step or set_state.  Not supported on
+ * a slab: shrinkage, gpflbm_shift_frame, the adjoint.  GPFLBM_ERR_ARG
+ * unless 0 <= v_begin, v_count >= 2 and v_begin + v_count <= nz;
+ * GPFLBM_ERR_UNSUPPORTED for a 2D grid or another vertical boundary.
+ * Workspace as in gpflbm_create, sized by gpflbm_slab_workspace_bytes. */
+gpflbm_status gpflbm_slab_workspace_bytes(const gpflbm_grid* grid, int v_begin, int v_count, int n_phases,
+                                          int n_components, size_t* bytes);
+gpflbm_status gpflbm_create_slab(const gpflbm_grid* grid, int v_begin, int v_count, int n_phases,
+                                 int n_components, const gpflbm_params* params, void* workspace,
+                                 size_t workspace_bytes, gpflbm_t* out);
+
+/* Bytes of one halo message of a slab (the same for both sides):
+ * (2 * stored phi components + K-1) planes of the arithmetic type and Q
+ * planes of the population storage type, each of (nx rounded up to 8) * ny
+ * elements. */
+gpflbm_status gpflbm_halo_bytes(gpflbm_t h, size_t* bytes);
+
+/* side: 0 = the neighbour below (smaller z), 1 = the neighbour above.
+ * gpflbm_halo_pack writes what that neighbour needs from this slab's current
+ * state into msg (device memory of gpflbm_halo_bytes, 16-byte aligned,
+ * owned by the caller); gpflbm_halo_unpack writes a message packed by that
+ * neighbour (its opposite side) into this slab's halo planes.  Both are
+ * asynchronous on `stream`; the caller orders the transfer between them
+ * (a copy on one GPU, ncclSend/ncclRecv or a peer copy between GPUs).
+ * GPFLBM_ERR_ARG for a side without a neighbour (a wall), a NULL or
+ * misaligned message; GPFLBM_ERR_UNSUPPORTED if h is not a slab;
+ * GPFLBM_ERR_STATE before set_state. */
+gpflbm_status gpflbm_halo_pack(gpflbm_t h, int side, void* msg, void* stream);
+gpflbm_status gpflbm_halo_unpack(gpflbm_t h, int side, const void* msg, void* stream);
+
 /* Replace the model parameters (same grid, phase and solute counts). */
 gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params);
 

@@ -70,6 +70,19 @@ struct gpflbm_s {
   DevParams<float> pf;
   gpflbm::InvParams inv;
   std::string err;
+  // Slab of the vertical axis (3D, gpflbm_create_slab): the handle owns the
+  // planes v_lo .. v_hi - 1 of the grid, and its buffers hold two halo planes
+  // on each side (hz = 2; 0 for a whole grid).  The step runs in the grid's
+  // coordinates (pd, pf); the state exchange, fields and totals see the
+  // owned planes as a grid of their own (xd, xf).  halo_fresh: the halo
+  // planes next to a neighbouring slab (lower, upper) were written since the
+  // last step.
+  bool slab;
+  int v_lo, v_hi, hz;
+  long long zst;  // elements per vertical plane of the buffers (px * ny)
+  bool halo_fresh[2];
+  DevParams<double> xd;
+  DevParams<float> xf;
 };
 
 namespace {
@@ -259,6 +272,9 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
   P.q_floor = (Real)p.q_floor;
   P.theta0 = -p.undercool - p.G * p.v0;
   P.GV = p.G * p.V;
+  P.v_lo = 0;
+  P.v_hi = h->D == 3 ? h->grid.nz : h->grid.ny;
+  P.zbase = 0;
 }
 
 gpflbm_status check_params(const gpflbm_params* p, int NP, std::string* why) {
@@ -299,9 +315,25 @@ gpflbm_status check_params(const gpflbm_params* p, int NP, std::string* why) {
   return GPFLBM_OK;
 }
 
+template <class Real>
+void slab_views(gpflbm_t h, DevParams<Real>& P, DevParams<Real>& X) {
+  if (!h->slab) return;
+  P.v_lo = h->v_lo;
+  P.v_hi = h->v_hi;
+  P.zbase = h->v_lo - h->hz;
+  X = P;
+  X.n[2] = h->v_hi - h->v_lo;
+  X.theta0 = P.theta0 + (double)P.G * h->v_lo;  // T at owned plane v is T at grid plane v_lo + v
+  X.v_lo = 0;
+  X.v_hi = X.n[2];
+  X.zbase = 0;
+}
+
 void set_device_params(gpflbm_t h) {
   fill_params(h, h->pd);
   fill_params(h, h->pf);
+  slab_views(h, h->pd, h->xd);
+  slab_views(h, h->pf, h->xf);
   h->inv.cells = h->cells;
   h->inv.plane = h->plane;
   h->inv.nx = h->grid.nx;
@@ -323,7 +355,20 @@ const void* dev_params(gpflbm_t h) {
   return h->grid.precision == GPFLBM_FP64 ? (const void*)&h->pd : (const void*)&h->pf;
 }
 
+// Parameters of the state-exchange, field and totals kernels: the owned
+// planes as a grid of their own (a whole grid: the step's parameters).
+const void* xparams(gpflbm_t h) {
+  if (!h->slab) return dev_params(h);
+  return h->grid.precision == GPFLBM_FP64 ? (const void*)&h->xd : (const void*)&h->xf;
+}
+
 void* at(gpflbm_t h, size_t off) { return h->ws + off; }
+
+// First owned plane of a field buffer at workspace offset `off` whose
+// elements are `esize` bytes (the buffer start for a whole grid).
+void* own(gpflbm_t h, size_t off, size_t esize) {
+  return h->ws + off + (size_t)h->hz * (size_t)h->zst * esize;
+}
 
 gpflbm::StepIO step_io(gpflbm_t h, int from) {
   gpflbm::StepIO io;
@@ -362,6 +407,26 @@ void drop_graphs(gpflbm_t h) {
     if (h->pair_graph[i]) cudaGraphExecDestroy(h->pair_graph[i]);
     h->chunk_graph[i] = h->pair_graph[i] = nullptr;
   }
+}
+
+// A slab steps only with both halos next to a neighbouring slab written
+// since its last step; the step then uses them up.
+gpflbm_status slab_ready(gpflbm_t h, const char* what) {
+  if (!h->slab) return GPFLBM_OK;
+  const bool lo = h->v_lo > 0, hi = h->v_hi < h->grid.nz;
+  if ((lo && !h->halo_fresh[0]) || (hi && !h->halo_fresh[1]))
+    return fail(h, GPFLBM_ERR_STATE, std::string(what) + ": exchange the slab's halo planes before each step");
+  h->halo_fresh[0] = h->halo_fresh[1] = false;
+  return GPFLBM_OK;
+}
+
+// The fixed-order totals of the current state's owned cells into `red`.
+cudaError_t run_invariants(gpflbm_t h, double* partial, int blocks, double* red, cudaStream_t s) {
+  const double theta0 = h->slab ? h->xd.theta0 : h->pd.theta0;
+  h->inv.theta_t = theta0 - h->pd.GV * (double)h->t;
+  const size_t rs = h->ops->real_size;
+  return h->ops->invariants(h->inv, own(h, h->lay.phi[h->cur], rs), own(h, h->lay.mu[h->cur], rs),
+                            own(h, h->lay.f[h->cur], h->ops->store_size), partial, blocks, red, s);
 }
 
 // Captures `steps` consecutive steps starting from buffer `from`.
@@ -406,20 +471,53 @@ gpflbm_status gpflbm_workspace_bytes(const gpflbm_grid* grid, int n_phases, int 
   return GPFLBM_OK;
 }
 
-gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_components,
-                            const gpflbm_params* params, void* workspace, size_t workspace_bytes,
-                            gpflbm_t* out) {
+}  // extern "C"
+
+namespace {
+
+// Planes v_begin .. v_begin + v_count - 1 of the vertical axis of a 3D grid
+// as a slab: walls on that axis, no obstacle rows on it, at least two planes.
+gpflbm_status check_slab(const gpflbm_grid* g, int D, int v_begin, int v_count, std::string* why) {
+  if (D != 3) {
+    *why = "slabs: 3D grids only";
+    return GPFLBM_ERR_UNSUPPORTED;
+  }
+  if (g->bc[2] != GPFLBM_WALL || g->wall_rows[2] != 0) {
+    *why = "slabs: the vertical axis needs walls and no obstacle rows";
+    return GPFLBM_ERR_UNSUPPORTED;
+  }
+  if (v_begin < 0 || v_count < 2 || (long long)v_begin + v_count > g->nz) {
+    *why = "slabs: need 0 <= v_begin, v_count >= 2, v_begin + v_count <= nz";
+    return GPFLBM_ERR_ARG;
+  }
+  return GPFLBM_OK;
+}
+
+// Planes held by a slab's buffers: its own and two halo planes on each side.
+constexpr int kHalo = 2;
+
+gpflbm_status create_impl(const gpflbm_grid* grid, int n_phases, int n_components,
+                          const gpflbm_params* params, void* workspace, size_t workspace_bytes,
+                          bool slab, int v_begin, int v_count, gpflbm_t* out) {
   if (!out) return GPFLBM_ERR_ARG;
   *out = nullptr;
   int D;
   const Ops* ops;
   std::string why;
   gpflbm_status st = check_grid(grid, n_phases, n_components, &D, &ops, &why);
+  if (st == GPFLBM_OK && slab) st = check_slab(grid, D, v_begin, v_count, &why);
   if (st != GPFLBM_OK) {
     std::fprintf(stderr, "gpflbm_create: %s\n", why.c_str());
     return st;
   }
   st = check_params(params, n_phases, &why);
+  if (st == GPFLBM_OK && slab) {
+    for (int a = 0; a < n_phases; ++a)
+      if (params->eta_rho[a] != 0.0) {
+        why = "slabs: shrinkage is not supported";
+        st = GPFLBM_ERR_UNSUPPORTED;
+      }
+  }
   if (st != GPFLBM_OK) {
     std::fprintf(stderr, "gpflbm_create: %s\n", why.c_str());
     return st;
@@ -434,9 +532,15 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
   h->Q = ops->Q;
   h->ops = ops;
   h->ops_ext = find_ops(D, grid->lattice, grid->precision, n_phases, n_components, true);
-  h->cells = (long long)grid->nx * grid->ny * grid->nz;
+  h->slab = slab;
+  h->v_lo = slab ? v_begin : 0;
+  h->v_hi = slab ? v_begin + v_count : (D == 3 ? grid->nz : grid->ny);
+  h->hz = slab ? kHalo : 0;
+  const int nz_own = slab ? v_count : grid->nz;
+  h->cells = (long long)grid->nx * grid->ny * nz_own;
   h->px = (int)round_up(grid->nx, 8);
-  h->plane = (long long)round_up((size_t)h->px * grid->ny * grid->nz, 64);
+  h->zst = (long long)h->px * grid->ny;
+  h->plane = (long long)round_up((size_t)h->zst * (nz_own + 2 * h->hz), 64);
   h->lay = make_layout(ops, h->cells, h->plane);
   h->cur = 0;
   h->t = 0;
@@ -480,11 +584,46 @@ gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_compone
   return GPFLBM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+gpflbm_status gpflbm_create(const gpflbm_grid* grid, int n_phases, int n_components,
+                            const gpflbm_params* params, void* workspace, size_t workspace_bytes,
+                            gpflbm_t* out) {
+  return create_impl(grid, n_phases, n_components, params, workspace, workspace_bytes, false, 0, 0, out);
+}
+
+gpflbm_status gpflbm_slab_workspace_bytes(const gpflbm_grid* grid, int v_begin, int v_count, int n_phases,
+                                          int n_components, size_t* bytes) {
+  int D;
+  const Ops* ops;
+  std::string why;
+  if (!bytes) return GPFLBM_ERR_ARG;
+  gpflbm_status st = check_grid(grid, n_phases, n_components, &D, &ops, &why);
+  if (st == GPFLBM_OK) st = check_slab(grid, D, v_begin, v_count, &why);
+  if (st != GPFLBM_OK) return st;
+  const size_t px = round_up(grid->nx, 8);
+  const long long cells = (long long)grid->nx * grid->ny * v_count;
+  *bytes = make_layout(ops, cells, (long long)round_up(px * grid->ny * (v_count + 2 * kHalo), 64)).total;
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_create_slab(const gpflbm_grid* grid, int v_begin, int v_count, int n_phases,
+                                 int n_components, const gpflbm_params* params, void* workspace,
+                                 size_t workspace_bytes, gpflbm_t* out) {
+  return create_impl(grid, n_phases, n_components, params, workspace, workspace_bytes, true, v_begin,
+                     v_count, out);
+}
+
 gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params) {
   if (!h) return GPFLBM_ERR_ARG;
   std::string why;
   gpflbm_status st = check_params(params, h->NP, &why);
   if (st != GPFLBM_OK) return fail(h, st, why);
+  if (h->slab)
+    for (int a = 0; a < h->NP; ++a)
+      if (params->eta_rho[a] != 0.0) return fail(h, GPFLBM_ERR_UNSUPPORTED, "set_params: no shrinkage on a slab");
   h->params = *params;
   set_device_params(h);
   drop_graphs(h);  // parameters are baked into captured launches
@@ -506,9 +645,10 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   const void* sp = phi;
   const void* sm = mu;
   const void* sf = f;
-  void* phi_d = at(h, h->lay.phi[h->cur]);
-  void* mu_d = at(h, h->lay.mu[h->cur]);
-  void* f_d = at(h, h->lay.f[h->cur]);
+  const size_t ss = h->ops->store_size;
+  void* phi_d = own(h, h->lay.phi[h->cur], rs);
+  void* mu_d = own(h, h->lay.mu[h->cur], rs);
+  void* f_d = own(h, h->lay.f[h->cur], ss);
   cudaError_t e;
   bool staged = false;
   if (!on_device) {
@@ -530,11 +670,11 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
     unsigned char* stage = static_cast<unsigned char*>(at(h, h->lay.stage));
     e = cudaMemcpyAsync(stage, phi, h->NP * n * rs, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: copy phi");
-    e = h->ops->load(dev_params(h), stage, nullptr, nullptr, phi_d, mu_d, f_d, s);
+    e = h->ops->load(xparams(h), stage, nullptr, nullptr, phi_d, mu_d, f_d, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load phi");
     e = cudaMemcpyAsync(stage, mu, h->NC * n * rs, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: copy mu");
-    e = h->ops->load(dev_params(h), nullptr, stage, nullptr, phi_d, mu_d, f_d, s);
+    e = h->ops->load(xparams(h), nullptr, stage, nullptr, phi_d, mu_d, f_d, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load mu");
     sp = sm = nullptr;
     if (f) {
@@ -565,26 +705,27 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
     const int to = 1 - h->cur;
     e = cudaStreamWaitEvent(h->xfer, h->ev_mark, 0);
     if (e == cudaSuccess)
-      e = h->ops->load_state(dev_params(h), sp, sm, sf, at(h, h->lay.phi[to]), at(h, h->lay.mu[to]),
-                             at(h, h->lay.f[to]), clk + to, nullptr, (double)t0, h->xfer);
+      e = h->ops->load_state(xparams(h), sp, sm, sf, own(h, h->lay.phi[to], rs), own(h, h->lay.mu[to], rs),
+                             own(h, h->lay.f[to], ss), clk + to, nullptr, (double)t0, h->xfer);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_loaded, h->xfer);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_loaded, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
     h->cur = to;
     h->t = t0;
+    h->halo_fresh[0] = h->halo_fresh[1] = false;
     ++h->mut;
     return GPFLBM_OK;
   }
   if (staged) {
     // (the load launcher always rewrites f: from sf, or the fluid at rest)
-    e = h->ops->load(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, s);
+    e = h->ops->load(xparams(h), sp, sm, sf, phi_d, mu_d, f_d, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
     set_clock_kernel<<<1, 1, 0, s>>>(clk, (double)t0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: clock");
   } else {
     // device or pinned sources: every plane and the counters in one launch
-    e = h->ops->load_state(dev_params(h), sp, sm, sf, phi_d, mu_d, f_d, clk, clk + 1, (double)t0, s);
+    e = h->ops->load_state(xparams(h), sp, sm, sf, phi_d, mu_d, f_d, clk, clk + 1, (double)t0, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
   }
   if (staged || !async) {
@@ -593,6 +734,7 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
   }
   h->t = t0;
   h->has_state = true;
+  h->halo_fresh[0] = h->halo_fresh[1] = false;
   ++h->mut;
   return GPFLBM_OK;
 }
@@ -601,6 +743,11 @@ gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream) {
   if (!h) return GPFLBM_ERR_ARG;
   if (n_steps < 0) return fail(h, GPFLBM_ERR_ARG, "step: n_steps < 0");
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "step: no state loaded");
+  if (h->slab && n_steps > 1) return fail(h, GPFLBM_ERR_ARG, "step: a slab steps once per halo exchange");
+  if (n_steps > 0) {
+    gpflbm_status st = slab_ready(h, "step");
+    if (st != GPFLBM_OK) return st;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ++h->mut;
   int left = n_steps;
@@ -633,6 +780,7 @@ gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream) {
 
 gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream) {
   if (!h) return GPFLBM_ERR_ARG;
+  if (h->slab) return fail(h, GPFLBM_ERR_UNSUPPORTED, "shift_frame: not on a slab");
   const int ax = h->D == 3 ? 2 : 1;
   const int nv = ax == 2 ? h->grid.nz : h->grid.ny;
   if (rows < 0 || rows >= nv) return fail(h, GPFLBM_ERR_ARG, "shift_frame: need 0 <= rows < n_vertical");
@@ -687,6 +835,10 @@ gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream) {
   if (!h || !events || !events[0] || !events[1])
     return fail(h, GPFLBM_ERR_ARG, "step_timed: two events are required");
   if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, "step_timed: no state loaded");
+  {
+    gpflbm_status st = slab_ready(h, "step_timed");
+    if (st != GPFLBM_OK) return st;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ++h->mut;
   const gpflbm::StepIO io = step_io(h, h->cur);
@@ -716,9 +868,9 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
   const int planes[6] = {h->NP, h->NC, h->NC, h->Q, 1, h->D};
   gpflbm::FieldsIO base;
   std::memset(&base, 0, sizeof(base));
-  base.phi = at(h, h->lay.phi[h->cur]);
-  base.mu = at(h, h->lay.mu[h->cur]);
-  base.f = at(h, h->lay.f[h->cur]);
+  base.phi = own(h, h->lay.phi[h->cur], rs);
+  base.mu = own(h, h->lay.mu[h->cur], rs);
+  base.f = own(h, h->lay.f[h->cur], h->ops->store_size);
   base.clock = reinterpret_cast<const double*>(at(h, h->lay.clock)) + h->cur;
   // device and pinned host destinations are written by one launch; pageable
   // host destinations go through the stage area one field at a time
@@ -741,7 +893,7 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
   }
   cudaError_t e;
   if (any_direct) {
-    e = h->ops->fields(dev_params(h), direct, s);
+    e = h->ops->fields(xparams(h), direct, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: kernel");
   }
   for (int bit = 0; bit < 6; ++bit) {
@@ -750,7 +902,7 @@ gpflbm_status gpflbm_get_fields(gpflbm_t h, unsigned field_mask, void* const* ds
     gpflbm::FieldsIO io = base;
     void** outs[6] = {&io.o_phi, &io.o_mu, &io.o_c, &io.o_f, &io.o_rho, &io.o_u};
     *outs[bit] = target;
-    e = h->ops->fields(dev_params(h), io, s);
+    e = h->ops->fields(xparams(h), io, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: kernel");
     e = cudaMemcpyAsync(staged_dst[bit], target, planes[bit] * n * rs, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "get_fields: copy");
@@ -777,12 +929,12 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
   void* target = on_device ? dst : at(h, h->lay.stage);
   gpflbm::FieldsIO io;
   std::memset(&io, 0, sizeof(io));
-  io.phi = at(h, h->lay.phi[h->cur]);
-  io.mu = at(h, h->lay.mu[h->cur]);
-  io.f = at(h, h->lay.f[h->cur]);
+  io.phi = own(h, h->lay.phi[h->cur], h->ops->real_size);
+  io.mu = own(h, h->lay.mu[h->cur], h->ops->real_size);
+  io.f = own(h, h->lay.f[h->cur], h->ops->store_size);
   io.clock = reinterpret_cast<const double*>(at(h, h->lay.clock)) + h->cur;
   io.o_dev = target;
-  cudaError_t e = h->ops->fields(dev_params(h), io, s);
+  cudaError_t e = h->ops->fields(xparams(h), io, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_deviations: kernel");
   if (!on_device) {
     e = cudaMemcpyAsync(dst, target, h->Q * (size_t)h->cells * h->ops->real_size,
@@ -803,8 +955,7 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
   const int blocks = (int)(want < gpflbm::kRedMaxBlocks ? want : gpflbm::kRedMaxBlocks);
   double* partial = reinterpret_cast<double*>(at(h, h->lay.partial));
   double* red = reinterpret_cast<double*>(at(h, h->lay.red));
-  cudaError_t e = (h->inv.theta_t = h->pd.theta0 - h->pd.GV * (double)h->t, h->ops->invariants)(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
-                                     at(h, h->lay.f[h->cur]), partial, blocks, red, s);
+  cudaError_t e = run_invariants(h, partial, blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: kernel");
   double out[GPFLBM_MAX_SOLUTES + 3];
   e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -817,6 +968,118 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
   if (out[h->NC + 2] != 0.0)
     return fail(h, GPFLBM_ERR_NONFINITE, "invariants: NaN or Inf in the state");
   return GPFLBM_OK;
+}
+
+}  // extern "C"
+
+namespace gpflbm {
+// Whole vertical planes between a slab's state buffers and a halo message:
+// segment j moves words[j] 16-byte words from src[j] to dst[j] (blockIdx.y
+// picks the segment; a grid-stride loop over its words in x).
+constexpr int kHaloMaxSegs = 48;
+struct HaloCopy {
+  const uint4* src[kHaloMaxSegs];
+  uint4* dst[kHaloMaxSegs];
+  long long words[kHaloMaxSegs];
+};
+
+__global__ void halo_copy_kernel(const HaloCopy c) {
+  const int j = blockIdx.y;
+  const uint4* __restrict__ src = c.src[j];
+  uint4* __restrict__ dst = c.dst[j];
+  const long long n = c.words[j];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+}  // namespace gpflbm
+
+namespace {
+
+// Bytes of one halo message: two planes of phi (every stored component) and
+// one plane of mu and of the stored populations.
+size_t halo_message_bytes(gpflbm_t h) {
+  const size_t rs = h->ops->real_size, ss = h->ops->store_size, z = (size_t)h->zst;
+  return (2 * (size_t)h->ops->stored_phi_planes + h->NC) * z * rs + (size_t)h->Q * z * ss;
+}
+
+// Copies the planes a neighbour on `side` (0 below, 1 above) needs into msg
+// (pack), or the neighbour's planes from msg into this slab's halo (unpack).
+// Message: phi of the lower plane (every stored component), phi of the upper
+// plane, mu, the stored populations; planes in the buffers' own layout.
+gpflbm_status halo_copy(gpflbm_t h, int side, unsigned char* msg, bool pack, cudaStream_t s) {
+  const int phi_first = pack ? (side == 0 ? h->v_lo : h->v_hi - 2) : (side == 0 ? h->v_lo - 2 : h->v_hi);
+  const int one = pack ? (side == 0 ? h->v_lo : h->v_hi - 1) : (side == 0 ? h->v_lo - 1 : h->v_hi);
+  const size_t rs = h->ops->real_size, ss = h->ops->store_size, z = (size_t)h->zst;
+  auto local = [&](int g) { return (size_t)(g - (h->v_lo - h->hz)); };
+  gpflbm::HaloCopy c;
+  int n = 0;
+  size_t off = 0;
+  auto add = [&](unsigned char* plane, size_t bytes) {
+    unsigned char* a = pack ? plane : msg + off;
+    unsigned char* b = pack ? msg + off : plane;
+    c.src[n] = reinterpret_cast<const uint4*>(a);
+    c.dst[n] = reinterpret_cast<uint4*>(b);
+    c.words[n] = (long long)(bytes / 16);
+    ++n;
+    off += bytes;
+  };
+  unsigned char* phi = static_cast<unsigned char*>(at(h, h->lay.phi[h->cur]));
+  unsigned char* mu = static_cast<unsigned char*>(at(h, h->lay.mu[h->cur]));
+  unsigned char* f = static_cast<unsigned char*>(at(h, h->lay.f[h->cur]));
+  for (int l = 0; l < 2; ++l)
+    for (int a = 0; a < h->ops->stored_phi_planes; ++a)
+      add(phi + ((size_t)a * h->plane + local(phi_first + l) * z) * rs, z * rs);
+  for (int i = 0; i < h->NC; ++i) add(mu + ((size_t)i * h->plane + local(one) * z) * rs, z * rs);
+  for (int k = 0; k < h->Q; ++k) add(f + ((size_t)k * h->plane + local(one) * z) * ss, z * ss);
+  long long most = 0;
+  for (int j = 0; j < n; ++j) most = c.words[j] > most ? c.words[j] : most;
+  const unsigned bx = (unsigned)((most + 255) / 256 < 64 ? (most + 255) / 256 : 64);
+  gpflbm::halo_copy_kernel<<<dim3(bx, n), 256, 0, s>>>(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, pack ? "halo_pack" : "halo_unpack");
+  return GPFLBM_OK;
+}
+
+gpflbm_status halo_check(gpflbm_t h, int side, const void* msg, const char* what) {
+  if (!h->slab) return fail(h, GPFLBM_ERR_UNSUPPORTED, std::string(what) + ": the handle is not a slab");
+  if (side != 0 && side != 1) return fail(h, GPFLBM_ERR_ARG, std::string(what) + ": side must be 0 or 1");
+  if ((side == 0 && h->v_lo == 0) || (side == 1 && h->v_hi == h->grid.nz))
+    return fail(h, GPFLBM_ERR_ARG, std::string(what) + ": no neighbouring slab on that side (a wall)");
+  if (!msg || (reinterpret_cast<uintptr_t>(msg) & 15u) != 0)
+    return fail(h, GPFLBM_ERR_ARG, std::string(what) + ": message must be 16-byte aligned device memory");
+  if (!h->has_state) return fail(h, GPFLBM_ERR_STATE, std::string(what) + ": no state loaded");
+  return GPFLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gpflbm_status gpflbm_halo_bytes(gpflbm_t h, size_t* bytes) {
+  if (!h || !bytes) return GPFLBM_ERR_ARG;
+  if (!h->slab) return fail(h, GPFLBM_ERR_UNSUPPORTED, "halo_bytes: the handle is not a slab");
+  *bytes = halo_message_bytes(h);
+  return GPFLBM_OK;
+}
+
+gpflbm_status gpflbm_halo_pack(gpflbm_t h, int side, void* msg, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  gpflbm_status st = halo_check(h, side, msg, "halo_pack");
+  if (st != GPFLBM_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mark(h, s);  // read-only
+  return halo_copy(h, side, static_cast<unsigned char*>(msg), true, s);
+}
+
+gpflbm_status gpflbm_halo_unpack(gpflbm_t h, int side, const void* msg, void* stream) {
+  if (!h) return GPFLBM_ERR_ARG;
+  gpflbm_status st = halo_check(h, side, msg, "halo_unpack");
+  if (st != GPFLBM_OK) return st;
+  ++h->mut;
+  st = halo_copy(h, side, static_cast<unsigned char*>(const_cast<void*>(msg)), false,
+                 static_cast<cudaStream_t>(stream));
+  if (st == GPFLBM_OK) h->halo_fresh[side] = true;
+  return st;
 }
 
 gpflbm_status gpflbm_time(gpflbm_t h, long long* t) {
@@ -926,8 +1189,7 @@ extern "C" gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, dou
   mark(h, s);  // read-only
   double* partial = scratch;
   double* red = scratch + (size_t)kNoAllocMaxBlocks * kNoAllocValues;
-  e = (h->inv.theta_t = h->pd.theta0 - h->pd.GV * (double)h->t, h->ops->invariants)(h->inv, at(h, h->lay.phi[h->cur]), at(h, h->lay.mu[h->cur]),
-                         at(h, h->lay.f[h->cur]), partial, (int)blocks, red, s);
+  e = run_invariants(h, partial, (int)blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: kernel");
   double out[kNoAllocValues];
   e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);

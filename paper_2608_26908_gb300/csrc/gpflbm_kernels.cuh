@@ -150,6 +150,10 @@ struct DevParams {
   int tilted;          // 1 if any pair of the problem's phases has a nonzero turn
   Real dceq_dT[4][2];  // ceq_a,i(T) = ceq[a][i] + dceq_dT[a][i] (T - T_E)
   int tdep;            // 1 if any of them is nonzero
+  // 3D step over part of the vertical axis (a slab): the step advances the
+  // planes v_lo .. v_hi - 1 of a grid of n[2] planes, and the field buffers
+  // start at plane zbase.  A whole grid: v_lo = 0, v_hi = n[2], zbase = 0.
+  int v_lo, v_hi, zbase;
 };
 
 // 1/x rounded to nearest: the same value as the IEEE division 1/x, by the

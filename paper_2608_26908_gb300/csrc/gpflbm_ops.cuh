@@ -116,7 +116,7 @@ struct Impl {
         step2d_kernel<NP, NC, Real, Store, false, EXT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
     } else {
       const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
-                      (P.n[2] + S3::ZS - 1) / S3::ZS);
+                      (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS);
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
                             io.f_in,   io.f_out,   io.clock_in, io.clock_out};
       if (P.shrink)

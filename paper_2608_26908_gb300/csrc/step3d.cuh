@@ -105,7 +105,9 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   const int tx = tid % BX, ty = tid / BX;
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2], px = P.px;
   const int zst = px * ny;  // plane stride (a plane holds fewer than 2^31 cells)
-  const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY, z0 = blockIdx.z * ZS;
+  // z segments start at the first owned plane (v_lo = 0 for a whole grid;
+  // a slab owns planes v_lo .. v_hi - 1 of the vertical axis)
+  const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY, z0 = P.v_lo + blockIdx.z * ZS;
   const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
   const bool inner_xy = x0 >= 2 && x0 - 2 + W2 <= nx && y0 >= 2 && y0 - 2 + H2 <= ny;
   const int fx = inner_xy ? gx : fold_axis(P, gx, 0);
@@ -125,6 +127,15 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       return P.ceq[a][i];
   };
   const bool has_walls = (P.wall[0] | P.wall[1] | P.wall[2]) != 0;  // obstacle rows
+  // vertical index of a plane the kernel reads: folded on the whole grid
+  // (walls mirror, periodic wraps), then kept inside the planes the buffers
+  // hold (v_lo - 2 .. v_hi + 1; for a whole grid the fold already is); the
+  // buffers start at plane zbase (0, or v_lo - 2 for a slab with halos)
+  auto vz = [&](int v) {
+    const int f = fold_axis(P, v, 2);
+    return f < P.v_lo - 2 ? P.v_lo - 2 : (f > P.v_hi + 1 ? P.v_hi + 1 : f);
+  };
+  auto zrow = [&](int fz) { return (fz - P.zbase) * zst; };
 
   int rx = 0, ry = 0;  // ring column held by threads tid < RING
   int gring = 0;
@@ -252,7 +263,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     bool liq_l;  // this thread's cells of plane L are pure liquid
     // A. phi^n of plane L
     {
-      const int zo = fold_axis(P, L, 2) * zst;
+      const int zo = zrow(vz(L));
       Real* b = s_phi + slot4(L) * NS * C2;
       unsigned m = 0;
       Real v[NP];
@@ -263,7 +274,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         if (v[a] > Real(0)) m |= 1u << a;
       }
       s_mask[slot3(L) * C2 + r2] = (unsigned char)m;
-      liq_l = pure_liquid(v) && !(has_walls && obstacle(P, fx, fy, fold_axis(P, L, 2)));
+      liq_l = pure_liquid(v) && !(has_walls && obstacle(P, fx, fy, vz(L)));
       if (tid < S::RING) {
         load_phases<NP>(phi_in, zo + gring, P.plane, v);
         liq_l = liq_l && pure_liquid(v);
@@ -279,8 +290,8 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     // B. moments, U and (owned planes, inner columns) collision + push, plane C
     const bool doC = C >= z0 - 1 && C <= z0 + ZS;
     if (doC) {
-      const int fzc = fold_axis(P, C, 2);
-      const int gi = fzc * zst + gxy;  // a plane holds fewer than 2^31 cells
+      const int fzc = vz(C);
+      const int gi = zrow(fzc) + gxy;  // the buffers hold fewer than 2^31 cells a plane
       const bool obs = has_walls && obstacle(P, fx, fy, fzc);
       Real mu[NC];
 #pragma unroll
@@ -324,16 +335,25 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         F[a] = fb - rho * kappa * u[a];
         s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
       }
-      if (owner && C >= z0 && C < z0 + ZS && C < nz) {
+      // A slab also collides the cells of its halo planes next to a
+      // neighbouring slab and keeps only the populations that stream into
+      // its own planes (hdir = +1 below, -1 above): the same values the
+      // neighbour computes for those cells, so nothing crosses after the step.
+      int hdir = 0;
+      if (C == P.v_lo - 1 && P.v_lo > 0 && C == z0 - 1) hdir = 1;
+      if (C == P.v_hi && P.v_hi < nz && C - 1 >= z0 && C - 1 < z0 + ZS) hdir = -1;
+      if (owner && ((C >= z0 && C < z0 + ZS && C < P.v_hi) || hdir != 0)) {
         const bool inner_z = C >= 1 && C + 1 < nz;
         if (inner_xy && inner_z) {
           // x + c_k is inside the grid: population k lands at gi + c_k . (1, px, zst)
           collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
+            if (hdir != 0 && Lat::c(k, 2) != hdir) return;
             const int off = Lat::c(k, 0) + Lat::c(k, 1) * px + Lat::c(k, 2) * zst;
             (f_out + k * P.plane + off)[gi] = Codec<Store>::put(val);
           });
         } else {
         collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
+          if (hdir != 0 && Lat::c(k, 2) != hdir) return;
           const Store v = Codec<Store>::put(val);
           const int cx = Lat::c(k, 0), cy = Lat::c(k, 1), cz = Lat::c(k, 2);
           // push to x + c_k; across a wall the population returns reversed
@@ -353,7 +373,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
               ty_ = ty_ < 0 ? ty_ + ny : (ty_ >= ny ? ty_ - ny : ty_);
               tz_ = tz_ < 0 ? tz_ + nz : (tz_ >= nz ? tz_ - nz : tz_);
             }
-            dst = (long long)tz_ * zst + (long long)ty_ * px + tx_;
+            dst = (long long)(tz_ - P.zbase) * zst + (long long)ty_ * px + tx_;
           }
           f_out[kk * P.plane + dst] = v;
         });
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     xy_m1 = xy_0;
     xy_0 = xy_l;
     if (pfC) {
-      const int fzc = fold_axis(P, C, 2);
+      const int fzc = vz(C);
       mixed = __popc(act) >= 2;
       multi = mixed && !(has_walls && obstacle(P, fx, fy, fzc));
 #pragma unroll
@@ -465,7 +485,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
             dadphi[a] += gab * (v[0] * gc[b][0] + v[1] * gc[b][1] + v[2] * gc[b][2]);
             dadphi[b] -= gab * (v[0] * gc[a][0] + v[1] * gc[a][1] + v[2] * gc[a][2]);
           }
-        const int fzC = fold_axis(P, C, 2);
+        const int fzC = vz(C);
         const Real theta = theta_base + P.G * Real(fzC);
         Real mu[NC];
 #pragma unroll
@@ -543,8 +563,8 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
           }
         }
         // moments, U and F with the shrinkage force, collision + push (as phase B)
-        const int fzc = fold_axis(P, C, 2);
-        const int gi = fzc * zst + gxy;
+        const int fzc = vz(C);
+        const int gi = zrow(fzc) + gxy;
         const bool obs = has_walls && obstacle(P, fx, fy, fzc);
         Real dk[Q];
 #pragma unroll
@@ -581,7 +601,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
           F[a] = fb + fs[a] - rho * kappa * u[a];
           s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
         }
-        if (owner && C >= z0 && C < z0 + ZS && C < nz) {
+        if (owner && C >= z0 && C < z0 + ZS && C < P.v_hi) {
           collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
             const Store v = Codec<Store>::put(val);
             int tx_ = gx + Lat::c(k, 0), ty_ = gy + Lat::c(k, 1), tz_ = C + Lat::c(k, 2), kk = k;
@@ -598,7 +618,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
               ty_ = ty_ < 0 ? ty_ + ny : (ty_ >= ny ? ty_ - ny : ty_);
               tz_ = tz_ < 0 ? tz_ + nz : (tz_ >= nz ? tz_ - nz : tz_);
             }
-            f_out[kk * P.plane + (long long)tz_ * zst + (long long)ty_ * px + tx_] = v;
+            f_out[kk * P.plane + (long long)(tz_ - P.zbase) * zst + (long long)ty_ * px + tx_] = v;
           });
         }
       }
@@ -611,12 +631,12 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
 
     // D. solute fluxes of plane M and the update of the owned planes
     const bool doM = M >= z0 - 1 && M <= z0 + ZS - 1;
-    const bool outM = doM && M >= z0 && M < nz;
+    const bool outM = doM && M >= z0 && M < P.v_hi;
     // planes M-1 .. M+2 liquid: phi^{n+1} = phi^n = liquid on planes M and
     // M+1, so h_l = 1, M = M0, no antitrapping, chi = 1 / (2 A_l), no obstacles
     const bool lean_d = (liq_hist & 15u) == 15u;
     if (doM) {
-      const int fzm = fold_axis(P, M, 2);
+      const int fzm = vz(M);
       const bool walls = has_walls;
       // flux between this cell (plane M) and neighbour nb: d normal axis
       auto mu_face = [&](int d, int pB, int nbT, int nbR, int gbd, bool obsB, Real* J) {
@@ -628,7 +648,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         const int pA = M, A = tid, rA = r2;
         if (lean_d) {
           const Real ua = s_u[(slot2(pA) * 3 + d) * NT + A], ub = s_u[(slot2(pB) * 3 + d) * NT + nbT];
-          const int fzB = d == 2 ? fold_axis(P, pB, 2) : fzm;
+          const int fzB = d == 2 ? vz(pB) : fzm;
 #pragma unroll
           for (int i = 0; i < NC; ++i) {
             const Real ma = s_mu[(slot2(pA) * NC + i) * NT + A], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
@@ -642,7 +662,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
         const Real Mf = Real(0.5) * P.M0 * (pnA[A] + pnB[nbT]);  // plane 0 = liquid
         const Real ua = s_u[(slot2(pA) * 3 + d) * NT + A] * s_hl[slot2(pA) * NT + A];
         const Real ub = s_u[(slot2(pB) * 3 + d) * NT + nbT] * s_hl[slot2(pB) * NT + nbT];
-        const int fzB = d == 2 ? fold_axis(P, pB, 2) : fzm;  // vertical index of B (ceq(T))
+        const int fzB = d == 2 ? vz(pB) : fzm;  // vertical index of B (ceq(T))
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
           const Real ma = s_mu[(slot2(pA) * NC + i) * NT + A], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
@@ -687,7 +707,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       };
       // z-face (M, M+1) of this column, for the carry
       {
-        const int fzb = fold_axis(P, M + 1, 2);
+        const int fzb = vz(M + 1);
         mu_face(2, M + 1, tid, r2, M + 1, walls && !lean_d && obstacle(P, fx, fy, fzb), mz_hi);
       }
       if (M == z0 - 1) {
@@ -713,7 +733,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
     __syncthreads();
     if (outM && M >= z0 && owner) {
       const int fzm = M;  // owned planes lie inside the grid
-      const int g = fzm * zst + gxy;
+      const int g = zrow(fzm) + gxy;
       Real po[NP], pn[NP];
 #pragma unroll
       for (int a = 0; a < NP; ++a) {

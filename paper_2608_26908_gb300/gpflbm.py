@@ -96,6 +96,12 @@ def lib():
         L.gpflbm_adjoint_workspace_bytes.argtypes = [vp, i, i, ctypes.POINTER(sz)]
         L.gpflbm_adjoint.argtypes = [vp, ctypes.POINTER(Objective), i, i, vp, sz, dp, dp, vp, i, vp]
         L.gpflbm_vjp.argtypes = [vp, i, i, vp, sz, vp, vp, dp, i, vp]
+        L.gpflbm_slab_workspace_bytes.argtypes = [ctypes.POINTER(Grid), i, i, i, i, ctypes.POINTER(sz)]
+        L.gpflbm_create_slab.argtypes = [ctypes.POINTER(Grid), i, i, i, i, ctypes.POINTER(Params), vp, sz,
+                                         ctypes.POINTER(vp)]
+        L.gpflbm_halo_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+        L.gpflbm_halo_pack.argtypes = [vp, i, vp, vp]
+        L.gpflbm_halo_unpack.argtypes = [vp, i, vp, vp]
         L.gpflbm_last_error.argtypes = [vp]
         L.gpflbm_last_error.restype = ctypes.c_char_p
         L.gpflbm_destroy.argtypes = [vp]
@@ -103,7 +109,9 @@ def lib():
         for name in ("gpflbm_workspace_bytes", "gpflbm_create", "gpflbm_set_params",
                      "gpflbm_set_state", "gpflbm_step", "gpflbm_step_timed", "gpflbm_get_fields",
                      "gpflbm_get_deviations", "gpflbm_invariants", "gpflbm_time",
-                     "gpflbm_adjoint_workspace_bytes", "gpflbm_adjoint", "gpflbm_vjp"):
+                     "gpflbm_adjoint_workspace_bytes", "gpflbm_adjoint", "gpflbm_vjp",
+                     "gpflbm_slab_workspace_bytes", "gpflbm_create_slab", "gpflbm_halo_bytes",
+                     "gpflbm_halo_pack", "gpflbm_halo_unpack"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -163,30 +171,65 @@ def _stream(torch):
 
 class Sim:
     """One simulation on the current CUDA device; the workspace is a torch
-    tensor, calls run on torch's current stream."""
+    tensor, calls run on torch's current stream.  slab=(v_begin, v_count)
+    makes it the slab of planes v_begin .. v_begin + v_count - 1 of a 3D
+    grid (gpflbm_create_slab): its fields are those planes."""
 
-    def __init__(self, sc):
+    def __init__(self, sc, slab=None):
         import torch
         self.torch = torch
         self.sc = sc
+        self.slab = slab
         self.nx, self.ny, self.nz = sc["grid"]["nx"], sc["grid"]["ny"], sc["grid"].get("nz", 1)
+        if slab is not None:
+            self.nz = int(slab[1])
         self.cells = self.nx * self.ny * self.nz
-        self.dim = 3 if self.nz > 1 else 2
+        self.dim = 3 if sc["grid"].get("nz", 1) > 1 else 2
         self.Q = sc["grid"].get("lattice") or (19 if self.dim == 3 else 9)
         self.NP, self.NC = sc["n_phases"], sc["n_solutes"]
         self.dtype = np.float64 if sc["precision"] == "fp64" else np.float32
         self.tdtype = torch.float64 if sc["precision"] == "fp64" else torch.float32
-        nbytes = workspace_bytes(sc)
-        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         self._grid = grid_struct(sc)
         self._params = params_struct(sc)
+        if slab is None:
+            nbytes = workspace_bytes(sc)
+        else:
+            n = ctypes.c_size_t()
+            st = lib().gpflbm_slab_workspace_bytes(ctypes.byref(self._grid), int(slab[0]), int(slab[1]),
+                                                   self.NP, self.NC, ctypes.byref(n))
+            if st != OK:
+                raise GpflbmError(st, "gpflbm_slab_workspace_bytes")
+            nbytes = n.value
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         h = ctypes.c_void_p()
-        st = lib().gpflbm_create(ctypes.byref(self._grid), self.NP, self.NC,
-                                 ctypes.byref(self._params), ctypes.c_void_p(self.workspace.data_ptr()),
-                                 nbytes, ctypes.byref(h))
+        if slab is None:
+            st = lib().gpflbm_create(ctypes.byref(self._grid), self.NP, self.NC,
+                                     ctypes.byref(self._params), ctypes.c_void_p(self.workspace.data_ptr()),
+                                     nbytes, ctypes.byref(h))
+        else:
+            st = lib().gpflbm_create_slab(ctypes.byref(self._grid), int(slab[0]), int(slab[1]), self.NP,
+                                          self.NC, ctypes.byref(self._params),
+                                          ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                          ctypes.byref(h))
         if st != OK:
-            raise GpflbmError(st, "gpflbm_create")
+            raise GpflbmError(st, "gpflbm_create" if slab is None else "gpflbm_create_slab")
         self.h = h
+
+    def halo_bytes(self):
+        n = ctypes.c_size_t()
+        self._check(lib().gpflbm_halo_bytes(self.h, ctypes.byref(n)), "halo_bytes")
+        return n.value
+
+    def halo_pack(self, side, msg):
+        """Planes the neighbour on `side` (0 below, 1 above) needs, into the
+        uint8 device tensor msg (halo_bytes() long)."""
+        self._check(lib().gpflbm_halo_pack(self.h, int(side), ctypes.c_void_p(msg.data_ptr()),
+                                           _stream(self.torch)), "halo_pack")
+
+    def halo_unpack(self, side, msg):
+        """A message packed by the neighbour on `side` into this slab's halo."""
+        self._check(lib().gpflbm_halo_unpack(self.h, int(side), ctypes.c_void_p(msg.data_ptr()),
+                                             _stream(self.torch)), "halo_unpack")
 
     def _check(self, st, what):
         if st != OK:

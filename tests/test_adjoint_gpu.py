@@ -303,19 +303,28 @@ def test_vjp_rejects_unsupported_and_invalid():
 
 
 # ------------------------------------------------------------------ stated FD check
-def test_fp32_gradients_match_fp64_central_differences_at_the_stated_horizon():
-    """The differentiation workload's own check, on its 64 x 64 crop: FP32
-    adjoint gradients (the configuration's arithmetic) over a 500-step
-    horizon with checkpoints every 50, against FP64 central differences of
-    the GPU forward with step 1e-6 -- dJ/d(1/tau_phi), dJ/d delta, dJ/d g beta_c
-    and dJ/dmu0 along 8 random directions, 1e-4 relative.  Cells whose
-    phase value crosses the clamp between the +h and -h runs (a kink inside
-    the difference) are counted and reported."""
+@pytest.mark.parametrize("prec,flow,rtol", [("fp32", "workload", 1e-4), ("fp64", "strong", 1e-6)])
+def test_gradients_match_fp64_central_differences_at_the_stated_horizon(prec, flow, rtol):
+    """The differentiation workload's check on its 64 x 64 crop over the
+    500-step horizon with checkpoints every 50: adjoint gradients against
+    FP64 central differences of the GPU forward with step 1e-6 --
+    dJ/d(1/tau_phi), dJ/d delta, dJ/d g beta_c and dJ/dmu0 along 8 random
+    directions.  FP32 gradients (the configuration's arithmetic) with the
+    workload's parameters at the stated 1e-4; FP64 gradients under a flow 200
+    times stronger (g beta_c = 2e-3) at 1e-6, which pins the long-horizon
+    reverse sweep itself.  Cells whose phase value crosses the clamp between
+    the +h and -h runs (a kink inside the difference) are counted."""
     H, K, h = 500, 50, 1e-6
-    sc32 = _case(64, 64, "fp32")
-    sc64 = _case(64, 64, "fp64")
+
+    def crop(p):
+        sc = inputs.scenario("adjoint2d", nx=64, ny=64, precision=p)
+        if flow == "strong":
+            sc["params"]["gbeta_c"] = [2e-3, 0.0]
+        return sc
+
+    sc_g, sc64 = crop(prec), crop("fp64")
     phi0, mu0 = inputs.initial_state(sc64)
-    _, J32, dpar, dmu = _gpu_adjoint(sc32, H, K)
+    _, J, dpar, dmu = _gpu_adjoint(sc_g, H, K)
     obj = _obj(sc64)
 
     def J_of(sc, mu, kinks=None):
@@ -331,14 +340,16 @@ def test_fp32_gradients_match_fp64_central_differences_at_the_stated_horizon():
 
     rng = np.random.default_rng(7)
     crossed = np.zeros(inputs.cells(sc64), dtype=bool)
+    errs = []
     for i in range(8):
         v = rng.normal(size=mu0.shape)
         kp, km = [], []
         fd = (J_of(sc64, mu0 + h * v, kp) - J_of(sc64, mu0 - h * v, km)) / (2 * h)
         for a, b in zip(kp, km):
             crossed |= a != b
-        assert float(np.dot(v, dmu)) == pytest.approx(fd, rel=1e-4), (i, float(np.dot(v, dmu)), fd)
+        errs.append(abs(float(np.dot(v, dmu)) - fd) / abs(fd))
     base = (1.0 / sc64["params"]["tau_phi"], sc64["params"]["delta"][0][1], sc64["params"]["gbeta_c"][0])
+    perr = []
     for j in range(3):
         vals = []
         for sgn in (+1, -1):
@@ -346,6 +357,9 @@ def test_fp32_gradients_match_fp64_central_differences_at_the_stated_horizon():
             p[j] += sgn * h
             vals.append(J_of(gpflbm.with_parameters(sc64, *p), mu0))
         fdp = (vals[0] - vals[1]) / (2 * h)
-        assert dpar[j] == pytest.approx(fdp, rel=1e-4), (j, dpar[j], fdp)
-    print("cells crossing a clamp kink within +-h over %d steps (8 mu0 directions): %d"
-          % (H, int(crossed.sum())))
+        perr.append((dpar[j], fdp, abs(dpar[j] - fdp) / abs(fdp)))
+    print("%s %s flow: cells crossing a clamp kink within +-h over %d steps (8 mu0 directions): %d; "
+          "mu0 relative errors %s; parameters %s" % (prec, flow, H, int(crossed.sum()),
+                                                     ["%.1e" % e for e in errs], perr))
+    assert max(errs) <= rtol, errs
+    assert all(e <= rtol for _, _, e in perr), perr
