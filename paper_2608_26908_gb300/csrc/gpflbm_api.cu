@@ -29,7 +29,7 @@ constexpr int kChunk = 16;  // steps per replayed CUDA graph
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t phi[2], mu[2], f[2], stage, clock, partial, red;
+  size_t phi[2], mu[2], f[2], stage, clock, partial, red, flags[2];
   size_t total;
 };
 
@@ -198,7 +198,18 @@ gpflbm_status check_grid(const gpflbm_grid* g, int NP, int NC, int* D, const Ops
   return GPFLBM_OK;
 }
 
-Layout make_layout(const Ops* ops, long long cells, long long plane) {
+// Tiles of the 3D step grid (an upper bound over the arithmetic types):
+// one liquid flag each.
+long long step_tiles(const gpflbm_grid* g, int nz_own) {
+  using F = gpflbm::Block3D<float>;
+  using Dd = gpflbm::Block3D<double>;
+  const long long ox = F::BX - 2 < Dd::BX - 2 ? F::BX - 2 : Dd::BX - 2;
+  const long long oy = F::BY - 2 < Dd::BY - 2 ? F::BY - 2 : Dd::BY - 2;
+  const long long zs = F::ZS < Dd::ZS ? F::ZS : Dd::ZS;
+  return ((g->nx + ox - 1) / ox) * ((g->ny + oy - 1) / oy) * ((nz_own + zs - 1) / zs);
+}
+
+Layout make_layout(const Ops* ops, long long cells, long long plane, long long tiles) {
   (void)cells;
   Layout L;
   size_t off = 0;
@@ -214,6 +225,7 @@ Layout make_layout(const Ops* ops, long long cells, long long plane) {
   L.clock = take(2 * sizeof(double));
   L.partial = take(gpflbm::kRedMaxBlocks * (ops->NC + 3) * sizeof(double));
   L.red = take((ops->NC + 3) * sizeof(double));
+  for (int i = 0; i < 2; ++i) L.flags[i] = take((size_t)tiles);
   L.total = off;
   return L;
 }
@@ -329,9 +341,29 @@ void slab_views(gpflbm_t h, DevParams<Real>& P, DevParams<Real>& X) {
   X.zbase = 0;
 }
 
+// Liquid tiles take the lean kernel in 3D, except on slabs (their halo
+// planes come from another handle), with shrinkage or obstacle rows, and
+// where a periodic axis ends in a tile of one cell (a tile's reach would
+// then wrap past its neighbour tiles).
+bool liquid_dispatch(gpflbm_t h) {
+  if (h->D != 3 || h->slab || h->pf.shrink) return false;
+  const gpflbm_grid& g = h->grid;
+  if (g.wall_rows[0] | g.wall_rows[1] | g.wall_rows[2]) return false;
+  const bool fp64 = g.precision == GPFLBM_FP64;
+  const int o[3] = {(fp64 ? gpflbm::Block3D<double>::BX : gpflbm::Block3D<float>::BX) - 2,
+                    (fp64 ? gpflbm::Block3D<double>::BY : gpflbm::Block3D<float>::BY) - 2,
+                    fp64 ? gpflbm::Block3D<double>::ZS : gpflbm::Block3D<float>::ZS};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  for (int a = 0; a < 3; ++a)
+    if (g.bc[a] == GPFLBM_PERIODIC && n[a] % o[a] == 1) return false;
+  return true;
+}
+
 void set_device_params(gpflbm_t h) {
   fill_params(h, h->pd);
   fill_params(h, h->pf);
+  const int liq = liquid_dispatch(h) ? 1 : 0;
+  h->pd.liq_dispatch = h->pf.liq_dispatch = liq;
   slab_views(h, h->pd, h->xd);
   slab_views(h, h->pf, h->xf);
   h->inv.cells = h->cells;
@@ -380,6 +412,8 @@ gpflbm::StepIO step_io(gpflbm_t h, int from) {
   io.f_out = at(h, h->lay.f[1 - from]);
   io.clock_in = reinterpret_cast<const double*>(at(h, h->lay.clock)) + from;
   io.clock_out = reinterpret_cast<double*>(at(h, h->lay.clock)) + 1 - from;
+  io.flags_in = static_cast<const unsigned char*>(at(h, h->lay.flags[from]));
+  io.flags_out = static_cast<unsigned char*>(at(h, h->lay.flags[1 - from]));
   return io;
 }
 
@@ -407,6 +441,14 @@ void drop_graphs(gpflbm_t h) {
     if (h->pair_graph[i]) cudaGraphExecDestroy(h->pair_graph[i]);
     h->chunk_graph[i] = h->pair_graph[i] = nullptr;
   }
+}
+
+// Liquid flags of the tiles of state buffer `buf` (3D with the liquid
+// dispatch; nothing otherwise).
+cudaError_t classify(gpflbm_t h, int buf, cudaStream_t s) {
+  if (!h->pf.liq_dispatch) return cudaSuccess;
+  return h->ops->classify(dev_params(h), at(h, h->lay.phi[buf]),
+                          static_cast<unsigned char*>(at(h, h->lay.flags[buf])), s);
 }
 
 // A slab steps only with both halos next to a neighbouring slab written
@@ -467,7 +509,8 @@ gpflbm_status gpflbm_workspace_bytes(const gpflbm_grid* grid, int n_phases, int 
   if (st != GPFLBM_OK) return st;
   const long long cells = (long long)grid->nx * grid->ny * grid->nz;
   const size_t px = round_up(grid->nx, 8);
-  *bytes = make_layout(ops, cells, (long long)round_up(px * grid->ny * grid->nz, 64)).total;
+  *bytes = make_layout(ops, cells, (long long)round_up(px * grid->ny * grid->nz, 64),
+                       step_tiles(grid, grid->nz)).total;
   return GPFLBM_OK;
 }
 
@@ -541,7 +584,7 @@ gpflbm_status create_impl(const gpflbm_grid* grid, int n_phases, int n_component
   h->px = (int)round_up(grid->nx, 8);
   h->zst = (long long)h->px * grid->ny;
   h->plane = (long long)round_up((size_t)h->zst * (nz_own + 2 * h->hz), 64);
-  h->lay = make_layout(ops, h->cells, h->plane);
+  h->lay = make_layout(ops, h->cells, h->plane, step_tiles(grid, nz_own));
   h->cur = 0;
   h->t = 0;
   h->has_state = false;
@@ -605,7 +648,8 @@ gpflbm_status gpflbm_slab_workspace_bytes(const gpflbm_grid* grid, int v_begin, 
   if (st != GPFLBM_OK) return st;
   const size_t px = round_up(grid->nx, 8);
   const long long cells = (long long)grid->nx * grid->ny * v_count;
-  *bytes = make_layout(ops, cells, (long long)round_up(px * grid->ny * (v_count + 2 * kHalo), 64)).total;
+  *bytes = make_layout(ops, cells, (long long)round_up(px * grid->ny * (v_count + 2 * kHalo), 64),
+                       step_tiles(grid, v_count)).total;
   return GPFLBM_OK;
 }
 
@@ -625,9 +669,16 @@ gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params) {
     for (int a = 0; a < h->NP; ++a)
       if (params->eta_rho[a] != 0.0) return fail(h, GPFLBM_ERR_UNSUPPORTED, "set_params: no shrinkage on a slab");
   h->params = *params;
+  const int had = h->pf.liq_dispatch;
   set_device_params(h);
   drop_graphs(h);  // parameters are baked into captured launches
   ++h->mut;
+  if (h->has_state && h->pf.liq_dispatch && !had) {
+    // the flags were not kept while every tile took the general kernel
+    cudaError_t e = classify(h, h->cur, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) return cuda_fail(h, e, "set_params: liquid tiles");
+  }
   return GPFLBM_OK;
 }
 
@@ -707,6 +758,7 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
     if (e == cudaSuccess)
       e = h->ops->load_state(xparams(h), sp, sm, sf, own(h, h->lay.phi[to], rs), own(h, h->lay.mu[to], rs),
                              own(h, h->lay.f[to], ss), clk + to, nullptr, (double)t0, h->xfer);
+    if (e == cudaSuccess) e = classify(h, to, h->xfer);
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_loaded, h->xfer);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, h->ev_loaded, 0);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
@@ -728,6 +780,8 @@ gpflbm_status gpflbm_set_state(gpflbm_t h, const void* phi, const void* mu, cons
     e = h->ops->load_state(xparams(h), sp, sm, sf, phi_d, mu_d, f_d, clk, clk + 1, (double)t0, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: load");
   }
+  e = classify(h, h->cur, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state: liquid tiles");
   if (staged || !async) {
     e = cudaStreamSynchronize(s);  // host sources must outlive the copies and loads
     if (e != cudaSuccess) return cuda_fail(h, e, "set_state: synchronize");
@@ -827,6 +881,8 @@ gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream) {
   h->cur = to;
   h->params.v0 -= rows;
   set_device_params(h);
+  e = classify(h, to, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "shift_frame: liquid tiles");
   drop_graphs(h);  // v0 is baked into captured launches
   return GPFLBM_OK;
 }
@@ -1320,6 +1376,8 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     io.f_out = out + 2 * pl;
     io.clock_in = forward_pass ? fw_clk(c, j) : clk_at(c, j);
     io.clock_out = forward_pass ? fw_clk(c, j + 1) : clk_at(c, j + 1);
+    io.flags_in = nullptr;  // 2D: no liquid-tile flags
+    io.flags_out = nullptr;
     return stepper(h)->step(P, io, st);
   };
   // copies of one stored state: handle -> slot, or slot -> handle

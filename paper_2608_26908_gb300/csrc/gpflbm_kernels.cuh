@@ -154,6 +154,9 @@ struct DevParams {
   // planes v_lo .. v_hi - 1 of a grid of n[2] planes, and the field buffers
   // start at plane zbase.  A whole grid: v_lo = 0, v_hi = n[2], zbase = 0.
   int v_lo, v_hi, zbase;
+  // 3D: tiles whose reach is pure liquid go to step3d_liquid_kernel (per-tile
+  // flags of the state); 0 = every tile takes the general kernel
+  int liq_dispatch;
 };
 
 // 1/x rounded to nearest: the same value as the IEEE division 1/x, by the
@@ -177,6 +180,34 @@ __device__ __forceinline__ bool obstacle(const DevParams<Real>& P, int x, int y,
   for (int a = 0; a < 3; ++a)
     if (P.wall[a] > 0 && (c[a] < P.wall[a] || c[a] >= P.n[a] - P.wall[a])) return true;
   return false;
+}
+
+// ------------------------------------------------------------------ liquid tiles
+// All 27 tiles around (bx, by, bz) -- wrapped on periodic axes, skipped
+// beyond walls (a wall mirrors the tile's own cells) -- are flagged pure
+// liquid.  Every thread of the CTA calls it; the answer is uniform.
+template <class Real>
+__device__ __forceinline__ bool liquid_reach(const DevParams<Real>& P, const unsigned char* __restrict__ flags,
+                                             int bx, int by, int bz, int gx, int gy, int gz) {
+  __shared__ int s_all;
+  if (threadIdx.x == 0) s_all = 1;
+  __syncthreads();
+  if (threadIdx.x < 27) {
+    const int t = threadIdx.x;
+    int c[3] = {bx + t % 3 - 1, by + (t / 3) % 3 - 1, bz + t / 9 - 1};
+    const int n[3] = {gx, gy, gz};
+    bool skip = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (c[a] < 0 || c[a] >= n[a]) {
+        if (P.bc[a] == kWall) skip = true;
+        c[a] = c[a] < 0 ? c[a] + n[a] : c[a] - n[a];
+      }
+    }
+    if (!skip && !flags[((long long)c[2] * gy + c[1]) * gx + c[0]]) s_all = 0;
+  }
+  __syncthreads();
+  return s_all != 0;
 }
 
 // ------------------------------------------------------------------ thermodynamics

@@ -8,6 +8,7 @@
 #include "gpflbm_kernels.cuh"
 #include "step2d.cuh"
 #include "step3d.cuh"
+#include "step3d_liquid.cuh"
 
 namespace gpflbm {
 
@@ -20,6 +21,8 @@ struct StepIO {
   void* f_out;
   const double* clock_in;
   double* clock_out;
+  const unsigned char* flags_in;  // 3D: liquid flag per tile of the input state
+  unsigned char* flags_out;       // ... of the output state
 };
 
 struct FieldsIO {
@@ -55,6 +58,8 @@ struct Ops {
   cudaError_t (*fields)(const void* params, const FieldsIO& io, cudaStream_t s);
   cudaError_t (*invariants)(const InvParams& p, const void* phi, const void* mu, const void* f,
                             double* partial, int blocks, double* out, cudaStream_t s);
+  // 3D: the liquid flag of every tile of a state (its phi buffer); 2D: nothing
+  cudaError_t (*classify)(const void* params, const void* phi, unsigned char* flags, cudaStream_t s);
 };
 
 // Grid of the exchange kernels (state load, field write-back): two CTAs of
@@ -85,6 +90,7 @@ struct Impl {
 
   using SZ = Step2D<NP, NC, Real, Store>;
   using S3 = Step3D<NP, NC, Real, Store, (D == 3 ? Q : 19)>;
+  using SL = Liquid3D<NP, NC, Real, Store, (D == 3 ? Q : 19), EXT>;
 
   static cudaError_t configure() {
     cudaError_t e;
@@ -100,6 +106,9 @@ struct Impl {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q, EXT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL::bytes);
     }
     return e;
   }
@@ -117,12 +126,15 @@ struct Impl {
     } else {
       const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
                       (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS);
-      const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
-                            io.f_in,   io.f_out,   io.clock_in, io.clock_out};
+      const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in,    io.mu_out,    io.f_in,
+                            io.f_out,  io.clock_in, io.clock_out, io.flags_in, io.flags_out};
       if (P.shrink)
         step3d_kernel<NP, NC, Real, Store, true, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
       else
         step3d_kernel<NP, NC, Real, Store, false, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+      // the tiles whose reach is pure liquid (the general kernel returned there)
+      if (P.liq_dispatch)
+        step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<grid, SL::NT, SL::bytes, s>>>(P, sio);
     }
     return cudaGetLastError();
   }
@@ -186,6 +198,22 @@ struct Impl {
     return cudaGetLastError();
   }
 
+  static cudaError_t classify(const void* params, const void* phi, unsigned char* flags, cudaStream_t s) {
+    if constexpr (D == 3) {
+      const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+      const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
+                      (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS);
+      liquid_flags_kernel<NP, Real><<<grid, 256, 0, s>>>(P, static_cast<const Real*>(phi), flags);
+      return cudaGetLastError();
+    } else {
+      (void)params;
+      (void)phi;
+      (void)flags;
+      (void)s;
+      return cudaSuccess;
+    }
+  }
+
   static cudaError_t invariants(const InvParams& p, const void* phi, const void* mu, const void* f,
                                 double* partial, int blocks, double* out, cudaStream_t s) {
     invariants_kernel<Q, NP, NC, Real, Store><<<blocks, kRedThreads, 0, s>>>(
@@ -208,7 +236,8 @@ struct Impl {
                             &Impl::load,
                             &Impl::load_state,
                             &Impl::fields,
-                            &Impl::invariants};
+                            &Impl::invariants,
+                            &Impl::classify};
     return &ops;
   }
 };

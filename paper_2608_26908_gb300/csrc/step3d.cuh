@@ -71,6 +71,8 @@ struct Step3DIO {
   void* f_out;
   const double* clock_in;
   double* clock_out;
+  const unsigned char* flags_in;  // liquid flag per tile of the input state
+  unsigned char* flags_out;       // ... of the output state
 };
 
 // EXT: the extended model -- pairs' crystal axes turned about z (dAdq_pair)
@@ -84,6 +86,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   using Lat = Lattice<QQ>;
   constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
   constexpr int W2 = S::W2, H2 = S::H2, C2 = S::C2, NS = S::NS;
+  // a tile whose reach is pure liquid belongs to step3d_liquid_kernel
+  if (P.liq_dispatch && liquid_reach(P, io.flags_in, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x,
+                                     gridDim.y, gridDim.z))
+    return;
   extern __shared__ __align__(16) unsigned char smem[];
   Real* s_phi = reinterpret_cast<Real*>(smem + S::phi);
   unsigned char* s_mask = smem + S::mask;
@@ -187,6 +193,9 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   // are already spent on the deferred collision).
   constexpr bool LIQ = !SHRINK;
   unsigned liq_hist = 0;
+
+  // every phase value this thread writes is pure liquid (for the tile's flag)
+  bool out_liq = true;
 
   // OR of the phase masks over the 3x3 in-plane neighbourhood of this
   // column, for planes C-1 and C (carried) and L (new)
@@ -742,6 +751,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       }
 #pragma unroll
       for (int sidx = 0; sidx < NS; ++sidx) phi_out[sidx * P.plane + g] = pn[NP == 2 ? 1 : sidx];
+      out_liq = out_liq && pure_liquid(pn);
       if (lean_d) {
         // unchanged liquid cell: chi = 1 / (2 A_l); the source is the
         // temperature term alone (extended model)
@@ -811,6 +821,10 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
     }
     __syncthreads();
+  }
+  if (P.liq_dispatch) {
+    const bool all = __syncthreads_and(out_liq);
+    if (tid == 0) io.flags_out[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = all;
   }
 }
 

@@ -1,0 +1,255 @@
+// Liquid tiles of the 3D step.  Away from the solid the phase field is
+// pure liquid (phi_l = 1, every other phase 0) in a tile's whole reach, and
+// Algorithm 1 reduces there to: phi^{n+1} = phi^n (only one phase is present
+// in every 3x3x3 neighbourhood, so it has no rate), the chemical potential
+// diffusing with M = D_liq / (2 A_l) and advected by U^n with h_l = 1 and
+// chi = 1 / (2 A_l), and the lattice Boltzmann step with phi_l = 1 (no drag,
+// the full buoyancy).  step3d_liquid_kernel advances such tiles with the
+// same arithmetic, term for term, as step3d_kernel's liquid-plane path --
+// the results are bit-identical -- but without the phase-field machinery,
+// so it needs far fewer registers and instructions.
+//
+// Which tiles are liquid: a flag per tile of the step grid (x tile, y tile,
+// z segment) says that every cell the tile owns is pure liquid.  A tile whose
+// own flag and its 26 neighbours' flags are set reads only pure liquid (its
+// reach is two cells and two planes), so the liquid kernel takes it and the
+// general kernel returns at once; otherwise the general kernel takes it and
+// the liquid kernel returns.  Both write the flag of the tile's new state.
+#pragma once
+
+#include "gpflbm_kernels.cuh"
+#include "step3d.cuh"
+
+namespace gpflbm {
+
+template <int NP, int NC, class Real, class Store, int QQ = 19, bool EXT = false>
+struct Liquid3D {
+  static constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZS;
+  static constexpr int NT = BX * BY;
+  static constexpr int OX = BX - 2, OY = BY - 2;
+  static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
+  static constexpr size_t u = 0;                                    // 2 planes x 3 x NT
+  static constexpr size_t mu = al(u + sizeof(Real) * 2 * 3 * NT);   // 2 planes x NC x NT
+  static constexpr size_t flux = al(mu + sizeof(Real) * 2 * NC * NT);  // 2 x NC x NT (x, y faces)
+  static constexpr size_t bytes = al(flux + sizeof(Real) * 2 * NC * NT);
+};
+
+template <int NP, int NC, class Real, class Store, int QQ = 19, bool EXT = false>
+__global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
+    step3d_liquid_kernel(const DevParams<Real> P, const Step3DIO io) {
+  using S = Liquid3D<NP, NC, Real, Store, QQ, EXT>;
+  using Lat = Lattice<QQ>;
+  constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
+  constexpr int NS = PhiStore<NP>::NS;
+  const int gxt = gridDim.x, gyt = gridDim.y, gzt = gridDim.z;
+  if (!liquid_reach(P, io.flags_in, blockIdx.x, blockIdx.y, blockIdx.z, gxt, gyt, gzt)) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  Real* s_u = reinterpret_cast<Real*>(smem + S::u);
+  Real* s_mu = reinterpret_cast<Real*>(smem + S::mu);
+  Real* s_flux = reinterpret_cast<Real*>(smem + S::flux);
+
+  const Real* __restrict__ mu_in = static_cast<const Real*>(io.mu_in);
+  const Store* __restrict__ f_in = static_cast<const Store*>(io.f_in);
+  Real* __restrict__ phi_out = static_cast<Real*>(io.phi_out);
+  Real* __restrict__ mu_out = static_cast<Real*>(io.mu_out);
+  Store* __restrict__ f_out = static_cast<Store*>(io.f_out);
+
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = tid / BX;
+  const int nx = P.n[0], ny = P.n[1], nz = P.n[2], px = P.px;
+  const int zst = px * ny;
+  const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY, z0 = P.v_lo + blockIdx.z * ZS;
+  const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
+  const bool inner_xy = x0 >= 2 && x0 - 2 + BX + 2 <= nx && y0 >= 2 && y0 - 2 + BY + 2 <= ny;
+  const int fx = inner_xy ? gx : fold_axis(P, gx, 0);
+  const int fy = inner_xy ? gy : fold_axis(P, gy, 1);
+  const int gxy = fy * px + fx;
+  const bool owner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && gx < nx && gy < ny;
+  const double t_now = io.clock_in[0];
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
+  const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
+  auto ceq_of = [&](int a, int i, int v) -> Real {
+    if constexpr (EXT)
+      return P.ceq[a][i] + P.dceq_dT[a][i] * (theta_base + P.G * Real(v));
+    else
+      return P.ceq[a][i];
+  };
+  auto vz = [&](int v) {
+    const int f = fold_axis(P, v, 2);
+    return f < P.v_lo - 2 ? P.v_lo - 2 : (f > P.v_hi + 1 ? P.v_hi + 1 : f);
+  };
+  auto zrow = [&](int fz) { return (fz - P.zbase) * zst; };
+  auto slot2 = [](int p) { return p & 1; };
+
+  // solute z-face fluxes of this column: (M-1, M) carried, (M, M+1) new
+  Real mz_lo[NC], mz_hi[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i] = Real(0);
+
+  for (int C = z0 - 1; C <= z0 + ZS; ++C) {
+    const int M = C - 1;
+    // B. moments, U and (owned planes) collision + push, plane C
+    {
+      const int fzc = vz(C);
+      const int gi = zrow(fzc) + gxy;
+      Real mu[NC];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        mu[i] = (mu_in + i * P.plane)[gi];
+        s_mu[(slot2(C) * NC + i) * NT + tid] = mu[i];
+      }
+      Real dk[Q];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
+      Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        drho += dk[k];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (Lat::c(k, a) != 0) m3[a] += Real(Lat::c(k, a)) * dk[k];
+      }
+      const Real rho = Real(1) + drho;
+      // the general path's arithmetic with phi_l = 1
+      const Real phl = Real(1);
+      const Real sl = Real(1) - phl;
+      const Real kappa = P.kappa0 * sl * sl;
+      Real drive = P.gbeta_T * (theta_base + P.G * Real(fzc) + P.dT_ref);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        if constexpr (EXT)
+          drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * (theta_base + P.G * Real(fzc)) +
+                                   mu[i] * P.inv2A[0]);
+        else
+          drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
+      }
+      const Real FB = rho * phl * drive;
+      const Real inv = rcp_rn(rho * (Real(1) + Real(0.5) * kappa));
+      Real u[3], F[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const Real fb = a == 2 ? FB : Real(0);
+        u[a] = (m3[a] + Real(0.5) * fb) * inv;
+        F[a] = fb - rho * kappa * u[a];
+        s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
+      }
+      if (owner && C >= z0 && C < z0 + ZS && C < P.v_hi) {
+        const bool inner_z = C >= 1 && C + 1 < nz;
+        if (inner_xy && inner_z) {
+          collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
+            const int off = Lat::c(k, 0) + Lat::c(k, 1) * px + Lat::c(k, 2) * zst;
+            (f_out + k * P.plane + off)[gi] = Codec<Store>::put(val);
+          });
+        } else {
+          collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
+            const Store v = Codec<Store>::put(val);
+            int tx_ = gx + Lat::c(k, 0), ty_ = gy + Lat::c(k, 1), tz_ = C + Lat::c(k, 2), kk = k;
+            const bool bx = P.bc[0] == kWall && (tx_ < 0 || tx_ >= nx);
+            const bool by = P.bc[1] == kWall && (ty_ < 0 || ty_ >= ny);
+            const bool bz = P.bc[2] == kWall && (tz_ < 0 || tz_ >= nz);
+            if (bx || by || bz) {  // across a wall the population returns reversed
+              kk = Lat::opp(k);
+              tx_ = gx;
+              ty_ = gy;
+              tz_ = C;
+            } else {
+              tx_ = tx_ < 0 ? tx_ + nx : (tx_ >= nx ? tx_ - nx : tx_);
+              ty_ = ty_ < 0 ? ty_ + ny : (ty_ >= ny ? ty_ - ny : ty_);
+              tz_ = tz_ < 0 ? tz_ + nz : (tz_ >= nz ? tz_ - nz : tz_);
+            }
+            f_out[kk * P.plane + (long long)(tz_ - P.zbase) * zst + (long long)ty_ * px + tx_] = v;
+          });
+        }
+      }
+    }
+    __syncthreads();
+    // D. solute fluxes of plane M (M-1 .. M+1 liquid: M = M0, h_l = 1)
+    const bool doM = M >= z0 - 1 && M <= z0 + ZS - 1;
+    if (doM) {
+      const int fzm = vz(M);
+      auto face = [&](int d, int pB, int nbT, int gbd, Real* J) {
+        const bool closed = (P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) J[i] = Real(0);
+        if (closed) return;
+        const Real ua = s_u[(slot2(M) * 3 + d) * NT + tid], ub = s_u[(slot2(pB) * 3 + d) * NT + nbT];
+        const int fzB = d == 2 ? vz(pB) : fzm;
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+          const Real ma = s_mu[(slot2(M) * NC + i) * NT + tid], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
+          J[i] = -P.M0 * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fzm) + ma * P.inv2A[0]) +
+                                                  ub * (ceq_of(0, i, fzB) + mb * P.inv2A[0]));
+        }
+      };
+      face(2, M + 1, tid, M + 1, mz_hi);
+      if (M == z0 - 1) {
+#pragma unroll
+        for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
+      } else {
+        Real J[NC];
+        if (tx < BX - 1) {
+          face(0, M, tid + 1, gx + 1, J);
+#pragma unroll
+          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 0) * NT + tid] = J[i];
+        }
+        if (ty < BY - 1) {
+          face(1, M, tid + BX, gy + 1, J);
+#pragma unroll
+          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 1) * NT + tid] = J[i];
+        }
+      }
+    }
+    __syncthreads();
+    if (doM && M >= z0 && M < P.v_hi && owner) {
+      const int g = zrow(M) + gxy;
+#pragma unroll
+      for (int sidx = 0; sidx < NS; ++sidx)
+        phi_out[sidx * P.plane + g] = (NP != 2 && sidx == 0) ? Real(1) : Real(0);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        const Real* Jx = s_flux + (i * 2 + 0) * NT;
+        const Real* Jy = s_flux + (i * 2 + 1) * NT;
+        const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
+        const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
+        Real src = Real(0);
+        if constexpr (EXT) {
+#pragma unroll
+          for (int a = 0; a < NP; ++a) src -= Real(P.GV) * P.dceq_dT[a][i] * (a == 0 ? Real(1) : Real(0));
+        }
+        mu_out[i * P.plane + g] = mu + (-div - src) * P.chi_pure[0];
+      }
+    }
+    if (doM && M >= z0) {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) io.flags_out[((long long)blockIdx.z * gyt + blockIdx.y) * gxt + blockIdx.x] = 1;
+}
+
+// The liquid flag of every tile of a state (after a load or a frame shift):
+// one CTA per tile, set when every cell the tile owns is pure liquid.
+template <int NP, class Real>
+__global__ void liquid_flags_kernel(const DevParams<Real> P, const Real* __restrict__ phi,
+                                    unsigned char* __restrict__ flags) {
+  constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZS;
+  constexpr int OX = BX - 2, OY = BY - 2;
+  const int x0 = blockIdx.x * OX, y0 = blockIdx.y * OY, z0 = P.v_lo + blockIdx.z * ZS;
+  const int wx = min(OX, P.n[0] - x0), wy = min(OY, P.n[1] - y0), wz = min(ZS, P.v_hi - z0);
+  const int zst = P.px * P.n[1];
+  bool liq = true;
+  for (int c = threadIdx.x; c < wx * wy * wz; c += blockDim.x) {
+    const int x = x0 + c % wx, y = y0 + (c / wx) % wy, z = z0 + c / (wx * wy);
+    Real v[NP];
+    load_phases<NP>(phi, (long long)(z - P.zbase) * zst + (long long)y * P.px + x, P.plane, v);
+    bool p = v[0] == Real(1);
+#pragma unroll
+    for (int a = 1; a < NP; ++a) p = p && v[a] == Real(0);
+    liq = liq && p;
+  }
+  liq = __syncthreads_and(liq);
+  if (threadIdx.x == 0) flags[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = liq;
+}
+
+}  // namespace gpflbm
