@@ -164,6 +164,19 @@ struct DevParams {
 __device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
+// Explicitly rounded operations: the compiler fuses a*b+c into one rounding
+// where it sees fit, which may differ between two kernels; the arithmetic
+// that the liquid-tile kernel shares with the general kernel is written
+// with these so that both give the same bits.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
 template <class Real>
 __device__ __forceinline__ int fold_axis(const DevParams<Real>& P, int i, int a) {
   const int n = P.n[a];
@@ -208,6 +221,55 @@ __device__ __forceinline__ bool liquid_reach(const DevParams<Real>& P, const uns
   }
   __syncthreads();
   return s_all != 0;
+}
+
+// ------------------------------------------------------------------ shared cell arithmetic
+// Buoyancy drive of the melt at a cell: g beta_T (T - T_ref) +
+// sum_i g beta_i (c_l,i(mu) - c_ref,i), theta = T - T_E; EXT: c_l,i at T.
+template <int NC, bool EXT, class Real>
+__device__ __forceinline__ Real buoyancy_drive(const DevParams<Real>& P, Real theta, const Real* mu) {
+  Real drive = mul_rn(P.gbeta_T, add_rn(theta, P.dT_ref));
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    Real cl = P.dcl_ref[i];
+    if constexpr (EXT) cl = fma_rn(P.dceq_dT[0][i], theta, cl);
+    drive = fma_rn(P.gbeta_c[i], fma_rn(mu[i], P.inv2A[0], cl), drive);
+  }
+  return drive;
+}
+
+// Force-corrected velocity and total force of a cell (vertical axis D - 1):
+// F_B = rho phl drive, U = (m + F_B/2) / (rho (1 + kappa/2)),
+// F = F_B - rho kappa U, kappa = kappa0 (1 - phl)^2.
+template <int D, class Real>
+__device__ __forceinline__ void force_velocity(const DevParams<Real>& P, Real rho, Real phl, Real drive,
+                                               const Real* m, Real* u, Real* F) {
+  const Real sl = sub_rn(Real(1), phl);
+  const Real kappa = mul_rn(mul_rn(P.kappa0, sl), sl);
+  const Real FB = mul_rn(mul_rn(rho, phl), drive);
+  const Real inv = rcp_rn(mul_rn(rho, fma_rn(Real(0.5), kappa, Real(1))));
+  const Real rk = mul_rn(rho, kappa);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const Real fb = a == D - 1 ? FB : Real(0);
+    u[a] = mul_rn(fma_rn(Real(0.5), fb, m[a]), inv);
+    F[a] = fma_rn(-rk, u[a], fb);
+  }
+}
+
+// Solute flux between two pure-liquid cells a, b (M = M0, h_l = 1):
+// J = -M0 (mu_b - mu_a) + (u_a c_a + u_b c_b) / 2, c = ceq_l + mu / (2 A_l).
+template <class Real>
+__device__ __forceinline__ Real liquid_flux(const DevParams<Real>& P, Real ma, Real mb, Real ua, Real ub,
+                                            Real ceqa, Real ceqb) {
+  const Real adv = mul_rn(Real(0.5), fma_rn(ua, fma_rn(ma, P.inv2A[0], ceqa), mul_rn(ub, fma_rn(mb, P.inv2A[0], ceqb))));
+  return fma_rn(-P.M0, sub_rn(mb, ma), adv);
+}
+
+// mu^{n+1} of an unchanged pure-liquid cell: mu + (-div - src) / (2 A_l)^-1.
+template <class Real>
+__device__ __forceinline__ Real liquid_mu(const DevParams<Real>& P, Real mu, Real div, Real src) {
+  return fma_rn(sub_rn(-div, src), P.chi_pure[0], mu);
 }
 
 // ------------------------------------------------------------------ thermodynamics
@@ -275,17 +337,21 @@ __device__ __forceinline__ void collide(const DevParams<Real>& P, const Real* dk
   using Lat = Lattice<Q>;
   constexpr int D = Lat::D;
   const Real itau = P.inv_tau_f, pre = P.force_pre, omega = Real(1) - itau;
+  // every product and sum rounded as written (fma_rn etc.), so that the two
+  // 3D kernels, which both collide liquid cells, give the same bits
+  const Real irho = mul_rn(itau, rho), pre9 = mul_rn(Real(9), pre);
   Real uu = Real(0), uF = Real(0), v[D], z[D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    uu += u[a] * u[a];
-    uF += u[a] * F[a];
-    const Real ru = itau * rho * u[a];
-    v[a] = Real(3) * (ru + pre * F[a]);
-    z[a] = Real(4.5) * ru + Real(9) * pre * F[a];
+    uu = fma_rn(u[a], u[a], uu);
+    uF = fma_rn(u[a], F[a], uF);
+    const Real ru = mul_rn(irho, u[a]);
+    v[a] = mul_rn(Real(3), fma_rn(pre, F[a], ru));
+    z[a] = fma_rn(Real(4.5), ru, mul_rn(pre9, F[a]));
   }
-  const Real alpha = itau * (drho - Real(1.5) * rho * uu) - Real(3) * pre * uF;
-  put(0, omega * dk[0] + Real(Lat::w(0)) * alpha);
+  const Real alpha =
+      fma_rn(itau, fma_rn(mul_rn(Real(-1.5), rho), uu, drho), mul_rn(mul_rn(Real(-3), pre), uF));
+  put(0, fma_rn(omega, dk[0], mul_rn(Real(Lat::w(0)), alpha)));
 #pragma unroll
   for (int k = 1; k < Q; ++k) {
     if (Lat::opp(k) < k) continue;  // each pair once, at its first index
@@ -304,9 +370,9 @@ __device__ __forceinline__ void collide(const DevParams<Real>& P, const Real* dk
       }
     }
     const Real wk = Real(Lat::w(k));
-    const Real wq = wk * (alpha + cu * cz), wl = wk * cv;
-    put(k, omega * dk[k] + (wq + wl));
-    put(kb, omega * dk[kb] + (wq - wl));
+    const Real wq = mul_rn(wk, fma_rn(cu, cz, alpha)), wl = mul_rn(wk, cv);
+    put(k, fma_rn(omega, dk[k], add_rn(wq, wl)));
+    put(kb, fma_rn(omega, dk[kb], sub_rn(wq, wl)));
   }
 }
 

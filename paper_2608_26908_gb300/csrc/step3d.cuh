@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   // EXT: ceq_a,i(T) at vertical index v, T - T_E = theta_base + G v
   auto ceq_of = [&](int a, int i, int v) -> Real {
     if constexpr (EXT)
-      return P.ceq[a][i] + P.dceq_dT[a][i] * (theta_base + P.G * Real(v));
+      return fma_rn(P.dceq_dT[a][i], fma_rn(P.G, Real(v), theta_base), P.ceq[a][i]);
     else
       return P.ceq[a][i];
   };
@@ -323,27 +323,11 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       const Real rho = Real(1) + drho;
       // phi_l^n of this cell (plane C was read as plane L one step earlier)
       const Real phl = obs ? Real(0) : PH(C, 0, r2);
-      const Real sl = Real(1) - phl;
-      const Real kappa = P.kappa0 * sl * sl;
-      Real drive = P.gbeta_T * (theta_base + P.G * Real(fzc) + P.dT_ref);
-#pragma unroll
-      for (int i = 0; i < NC; ++i) {
-        if constexpr (EXT)
-          drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * (theta_base + P.G * Real(fzc)) +
-                                   mu[i] * P.inv2A[0]);
-        else
-          drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
-      }
-      const Real FB = rho * phl * drive;
-      const Real inv = rcp_rn(rho * (Real(1) + Real(0.5) * kappa));
+      const Real drive = buoyancy_drive<NC, EXT>(P, fma_rn(P.G, Real(fzc), theta_base), mu);
       Real u[3], F[3];
+      force_velocity<3>(P, rho, phl, drive, m3, u, F);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const Real fb = a == 2 ? FB : Real(0);
-        u[a] = (m3[a] + Real(0.5) * fb) * inv;
-        F[a] = fb - rho * kappa * u[a];
-        s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
-      }
+      for (int a = 0; a < 3; ++a) s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
       // A slab also collides the cells of its halo planes next to a
       // neighbouring slab and keeps only the populations that stream into
       // its own planes (hdir = +1 below, -1 above): the same values the
@@ -661,8 +645,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
 #pragma unroll
           for (int i = 0; i < NC; ++i) {
             const Real ma = s_mu[(slot2(pA) * NC + i) * NT + A], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
-            J[i] = -P.M0 * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fzm) + ma * P.inv2A[0]) +
-                                                    ub * (ceq_of(0, i, fzB) + mb * P.inv2A[0]));
+            J[i] = liquid_flux(P, ma, mb, ua, ub, ceq_of(0, i, fzm), ceq_of(0, i, fzB));
           }
           return;
         }
@@ -766,7 +749,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
 #pragma unroll
             for (int a = 0; a < NP; ++a) src -= Real(P.GV) * P.dceq_dT[a][i] * (a == 0 ? Real(1) : Real(0));
           }
-          mu_out[i * P.plane + g] = mu + (-div - src) * P.chi_pure[0];
+          mu_out[i * P.plane + g] = liquid_mu(P, mu, div, src);
         }
       } else if (has_walls && obstacle(P, fx, fy, fzm)) {
 #pragma unroll

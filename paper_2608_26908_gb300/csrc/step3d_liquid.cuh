@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
   auto ceq_of = [&](int a, int i, int v) -> Real {
     if constexpr (EXT)
-      return P.ceq[a][i] + P.dceq_dT[a][i] * (theta_base + P.G * Real(v));
+      return fma_rn(P.dceq_dT[a][i], fma_rn(P.G, Real(v), theta_base), P.ceq[a][i]);
     else
       return P.ceq[a][i];
   };
@@ -110,29 +110,12 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
           if (Lat::c(k, a) != 0) m3[a] += Real(Lat::c(k, a)) * dk[k];
       }
       const Real rho = Real(1) + drho;
-      // the general path's arithmetic with phi_l = 1
-      const Real phl = Real(1);
-      const Real sl = Real(1) - phl;
-      const Real kappa = P.kappa0 * sl * sl;
-      Real drive = P.gbeta_T * (theta_base + P.G * Real(fzc) + P.dT_ref);
-#pragma unroll
-      for (int i = 0; i < NC; ++i) {
-        if constexpr (EXT)
-          drive += P.gbeta_c[i] * (P.dcl_ref[i] + P.dceq_dT[0][i] * (theta_base + P.G * Real(fzc)) +
-                                   mu[i] * P.inv2A[0]);
-        else
-          drive += P.gbeta_c[i] * (P.dcl_ref[i] + mu[i] * P.inv2A[0]);
-      }
-      const Real FB = rho * phl * drive;
-      const Real inv = rcp_rn(rho * (Real(1) + Real(0.5) * kappa));
+      // the general kernel's arithmetic with phi_l = 1 (the same helpers)
+      const Real drive = buoyancy_drive<NC, EXT>(P, fma_rn(P.G, Real(fzc), theta_base), mu);
       Real u[3], F[3];
+      force_velocity<3>(P, rho, Real(1), drive, m3, u, F);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const Real fb = a == 2 ? FB : Real(0);
-        u[a] = (m3[a] + Real(0.5) * fb) * inv;
-        F[a] = fb - rho * kappa * u[a];
-        s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
-      }
+      for (int a = 0; a < 3; ++a) s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
       if (owner && C >= z0 && C < z0 + ZS && C < P.v_hi) {
         const bool inner_z = C >= 1 && C + 1 < nz;
         if (inner_xy && inner_z) {
@@ -177,8 +160,7 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
           const Real ma = s_mu[(slot2(M) * NC + i) * NT + tid], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
-          J[i] = -P.M0 * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fzm) + ma * P.inv2A[0]) +
-                                                  ub * (ceq_of(0, i, fzB) + mb * P.inv2A[0]));
+          J[i] = liquid_flux(P, ma, mb, ua, ub, ceq_of(0, i, fzm), ceq_of(0, i, fzB));
         }
       };
       face(2, M + 1, tid, M + 1, mz_hi);
@@ -216,7 +198,7 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
 #pragma unroll
           for (int a = 0; a < NP; ++a) src -= Real(P.GV) * P.dceq_dT[a][i] * (a == 0 ? Real(1) : Real(0));
         }
-        mu_out[i * P.plane + g] = mu + (-div - src) * P.chi_pure[0];
+        mu_out[i * P.plane + g] = liquid_mu(P, mu, div, src);
       }
     }
     if (doM && M >= z0) {
