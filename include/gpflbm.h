@@ -243,10 +243,10 @@ gpflbm_status gpflbm_step(gpflbm_t h, int n_steps, void* stream);
 gpflbm_status gpflbm_shift_frame(gpflbm_t h, int rows, void* stream);
 
 /* One step launched directly (not from a graph) that records two caller
- * CUDA events (cudaEvent_t) on `stream`: events[0] before the step kernel
- * (one fused launch for all three updates) and events[1] after it, for
- * kernel timing with cudaEventElapsedTime.  Same result as
- * gpflbm_step(h, 1, stream). */
+ * CUDA events (cudaEvent_t) on `stream`: events[0] before the step's
+ * kernels and events[1] after them (gpflbm_step_launches launches, all
+ * three updates fused in each), for kernel timing with
+ * cudaEventElapsedTime.  Same result as gpflbm_step(h, 1, stream). */
 gpflbm_status gpflbm_step_timed(gpflbm_t h, void* const* events, void* stream);
 
 /* Copy fields of the current state out.  field_mask is an OR of
@@ -364,6 +364,13 @@ gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizo
  * handle is left at S^{t0+H}.  Synchronises `stream`. */
 gpflbm_status gpflbm_vjp(gpflbm_t h, int horizon, int ckpt_every, void* workspace, size_t workspace_bytes,
                          const void* seed, void* grad, double* dparams, int flags, void* stream);
+
+/* Kernel launches one step makes with the current parameters: 1 (2D, and
+ * 3D slabs or 3D runs with shrinkage or obstacle rows), or 2 (3D: the
+ * general step kernel over the tiles whose reach holds more than pure
+ * liquid, then the liquid-tile kernel over the others; each tile is
+ * advanced by exactly one of them).  Does not touch the GPU. */
+gpflbm_status gpflbm_step_launches(gpflbm_t h, int* launches);
 
 /* Step counter of the current state (the t of T(v, t)). */
 gpflbm_status gpflbm_time(gpflbm_t h, long long* t);

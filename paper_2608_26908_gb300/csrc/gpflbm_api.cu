@@ -1138,6 +1138,12 @@ gpflbm_status gpflbm_halo_unpack(gpflbm_t h, int side, const void* msg, void* st
   return st;
 }
 
+gpflbm_status gpflbm_step_launches(gpflbm_t h, int* launches) {
+  if (!h || !launches) return GPFLBM_ERR_ARG;
+  *launches = h->pf.liq_dispatch ? 2 : 1;
+  return GPFLBM_OK;
+}
+
 gpflbm_status gpflbm_time(gpflbm_t h, long long* t) {
   if (!h || !t) return GPFLBM_ERR_ARG;
   *t = h->t;

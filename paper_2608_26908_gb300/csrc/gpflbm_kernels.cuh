@@ -195,6 +195,41 @@ __device__ __forceinline__ bool obstacle(const DevParams<Real>& P, int x, int y,
   return false;
 }
 
+// ------------------------------------------------------------------ push streaming
+// Where the populations of a cell stream to along one axis: the offset (in
+// elements) of the +1 and -1 neighbour, periodic axes wrapping, and whether a
+// wall lies in between (halfway bounce-back: a population that would cross
+// it returns reversed into the cell itself).
+struct PushAxis {
+  int op, om;
+  bool wp, wm;
+};
+__device__ __forceinline__ PushAxis push_axis(int i, int n, bool wall, int stride) {
+  PushAxis a;
+  a.wp = wall && i + 1 >= n;
+  a.wm = wall && i - 1 < 0;
+  a.op = (i + 1 < n ? 1 : (wall ? 0 : 1 - n)) * stride;
+  a.om = (i - 1 >= 0 ? -1 : (wall ? 0 : n - 1)) * stride;
+  return a;
+}
+
+// Stores population k of the cell at gi into its destination (one of the
+// cells around it, or back into the cell reversed across a wall).
+template <class Lat, class Store>
+__device__ __forceinline__ void push_store(Store* __restrict__ f_out, long long plane, int gi, int k, Store v,
+                                           const PushAxis& X, const PushAxis& Y, const PushAxis& Z) {
+  constexpr int dims = Lat::D;
+  const int c0 = Lat::c(k, 0), c1 = Lat::c(k, 1), c2 = dims == 3 ? Lat::c(k, 2) : 0;
+  const bool bounce = (c0 > 0 && X.wp) || (c0 < 0 && X.wm) || (c1 > 0 && Y.wp) || (c1 < 0 && Y.wm) ||
+                      (c2 > 0 && Z.wp) || (c2 < 0 && Z.wm);
+  const int off = (c0 > 0 ? X.op : (c0 < 0 ? X.om : 0)) + (c1 > 0 ? Y.op : (c1 < 0 ? Y.om : 0)) +
+                  (c2 > 0 ? Z.op : (c2 < 0 ? Z.om : 0));
+  if (bounce)
+    f_out[Lat::opp(k) * plane + gi] = v;
+  else
+    f_out[k * plane + gi + off] = v;
+}
+
 // ------------------------------------------------------------------ liquid tiles
 // All 27 tiles around (bx, by, bz) -- wrapped on periodic axes, skipped
 // beyond walls (a wall mirrors the tile's own cells) -- are flagged pure

@@ -345,30 +345,14 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
             (f_out + k * P.plane + off)[gi] = Codec<Store>::put(val);
           });
         } else {
+        // push to x + c_k (periodic axes wrap; across a wall the population
+        // returns reversed into the cell)
+        const PushAxis X = push_axis(gx, nx, P.bc[0] == kWall, 1);
+        const PushAxis Y = push_axis(gy, ny, P.bc[1] == kWall, px);
+        const PushAxis Z = push_axis(C, nz, P.bc[2] == kWall, zst);
         collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
           if (hdir != 0 && Lat::c(k, 2) != hdir) return;
-          const Store v = Codec<Store>::put(val);
-          const int cx = Lat::c(k, 0), cy = Lat::c(k, 1), cz = Lat::c(k, 2);
-          // push to x + c_k; across a wall the population returns reversed
-          int tx_ = gx + cx, ty_ = gy + cy, tz_ = C + cz, kk = k;
-          long long dst;
-          {
-            const bool bx = P.bc[0] == kWall && (tx_ < 0 || tx_ >= nx);
-            const bool by = P.bc[1] == kWall && (ty_ < 0 || ty_ >= ny);
-            const bool bz = P.bc[2] == kWall && (tz_ < 0 || tz_ >= nz);
-            if (bx || by || bz) {
-              kk = Lat::opp(k);
-              tx_ = gx;
-              ty_ = gy;
-              tz_ = C;
-            } else {
-              tx_ = tx_ < 0 ? tx_ + nx : (tx_ >= nx ? tx_ - nx : tx_);
-              ty_ = ty_ < 0 ? ty_ + ny : (ty_ >= ny ? ty_ - ny : ty_);
-              tz_ = tz_ < 0 ? tz_ + nz : (tz_ >= nz ? tz_ - nz : tz_);
-            }
-            dst = (long long)(tz_ - P.zbase) * zst + (long long)ty_ * px + tx_;
-          }
-          f_out[kk * P.plane + dst] = v;
+          push_store<Lat>(f_out, P.plane, gi, k, Codec<Store>::put(val), X, Y, Z);
         });
         }
       }

@@ -100,6 +100,7 @@ def lib():
         L.gpflbm_create_slab.argtypes = [ctypes.POINTER(Grid), i, i, i, i, ctypes.POINTER(Params), vp, sz,
                                          ctypes.POINTER(vp)]
         L.gpflbm_halo_bytes.argtypes = [vp, ctypes.POINTER(sz)]
+        L.gpflbm_step_launches.argtypes = [vp, ctypes.POINTER(i)]
         L.gpflbm_halo_pack.argtypes = [vp, i, vp, vp]
         L.gpflbm_halo_unpack.argtypes = [vp, i, vp, vp]
         L.gpflbm_last_error.argtypes = [vp]
@@ -111,7 +112,7 @@ def lib():
                      "gpflbm_get_deviations", "gpflbm_invariants", "gpflbm_time",
                      "gpflbm_adjoint_workspace_bytes", "gpflbm_adjoint", "gpflbm_vjp",
                      "gpflbm_slab_workspace_bytes", "gpflbm_create_slab", "gpflbm_halo_bytes",
-                     "gpflbm_halo_pack", "gpflbm_halo_unpack"):
+                     "gpflbm_halo_pack", "gpflbm_halo_unpack", "gpflbm_step_launches"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -292,6 +293,11 @@ class Sim:
         the step kernel) on the current stream."""
         raw = (ctypes.c_void_p * 2)(*[e.cuda_event for e in events[:2]])
         self._check(lib().gpflbm_step_timed(self.h, raw, _stream(self.torch)), "step_timed")
+
+    def step_launches(self):
+        n = ctypes.c_int()
+        self._check(lib().gpflbm_step_launches(self.h, ctypes.byref(n)), "step_launches")
+        return n.value
 
     def time(self):
         t = ctypes.c_longlong()
