@@ -198,15 +198,14 @@ gpflbm_status check_grid(const gpflbm_grid* g, int NP, int NC, int* D, const Ops
   return GPFLBM_OK;
 }
 
-// Tiles of the 3D step grid (an upper bound over the arithmetic types):
-// one liquid flag each.
+// xy tiles of the 3D step grid (an upper bound over the arithmetic types)
+// times planes: one liquid flag each.
 long long step_tiles(const gpflbm_grid* g, int nz_own) {
   using F = gpflbm::Block3D<float>;
   using Dd = gpflbm::Block3D<double>;
   const long long ox = F::BX - 2 < Dd::BX - 2 ? F::BX - 2 : Dd::BX - 2;
   const long long oy = F::BY - 2 < Dd::BY - 2 ? F::BY - 2 : Dd::BY - 2;
-  const long long zs = F::ZS < Dd::ZS ? F::ZS : Dd::ZS;
-  return ((g->nx + ox - 1) / ox) * ((g->ny + oy - 1) / oy) * ((nz_own + zs - 1) / zs);
+  return ((g->nx + ox - 1) / ox) * ((g->ny + oy - 1) / oy) * nz_own;
 }
 
 Layout make_layout(const Ops* ops, long long cells, long long plane, long long tiles) {
@@ -343,18 +342,17 @@ void slab_views(gpflbm_t h, DevParams<Real>& P, DevParams<Real>& X) {
 
 // Liquid tiles take the lean kernel in 3D, except on slabs (their halo
 // planes come from another handle), with shrinkage or obstacle rows, and
-// where a periodic axis ends in a tile of one cell (a tile's reach would
-// then wrap past its neighbour tiles).
+// where a periodic x or y axis ends in a tile of one cell (a tile's reach
+// would then wrap past its neighbour tiles; planes are flagged one by one).
 bool liquid_dispatch(gpflbm_t h) {
   if (h->D != 3 || h->slab || h->pf.shrink) return false;
   const gpflbm_grid& g = h->grid;
   if (g.wall_rows[0] | g.wall_rows[1] | g.wall_rows[2]) return false;
   const bool fp64 = g.precision == GPFLBM_FP64;
-  const int o[3] = {(fp64 ? gpflbm::Block3D<double>::BX : gpflbm::Block3D<float>::BX) - 2,
-                    (fp64 ? gpflbm::Block3D<double>::BY : gpflbm::Block3D<float>::BY) - 2,
-                    fp64 ? gpflbm::Block3D<double>::ZS : gpflbm::Block3D<float>::ZS};
-  const int n[3] = {g.nx, g.ny, g.nz};
-  for (int a = 0; a < 3; ++a)
+  const int o[2] = {(fp64 ? gpflbm::Block3D<double>::BX : gpflbm::Block3D<float>::BX) - 2,
+                    (fp64 ? gpflbm::Block3D<double>::BY : gpflbm::Block3D<float>::BY) - 2};
+  const int n[2] = {g.nx, g.ny};
+  for (int a = 0; a < 2; ++a)
     if (g.bc[a] == GPFLBM_PERIODIC && n[a] % o[a] == 1) return false;
   return true;
 }

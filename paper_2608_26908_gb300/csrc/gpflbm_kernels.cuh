@@ -231,28 +231,37 @@ __device__ __forceinline__ void push_store(Store* __restrict__ f_out, long long 
 }
 
 // ------------------------------------------------------------------ liquid tiles
-// All 27 tiles around (bx, by, bz) -- wrapped on periodic axes, skipped
-// beyond walls (a wall mirrors the tile's own cells) -- are flagged pure
-// liquid.  Every thread of the CTA calls it; the answer is uniform.
-template <class Real>
+// Liquid flags are kept per xy tile of the step grid and per plane: flag
+// (tile, v) says that every cell the tile owns in plane v is pure liquid.
+__device__ __forceinline__ long long liquid_flag_index(int bx, int by, int v, int gx, int gy) {
+  return ((long long)v * gy + by) * gx + bx;
+}
+
+// The reach of the z segment starting at plane z0 of xy tile (bx, by) -- the
+// 3 x 3 tiles around it (wrapped on periodic axes, skipped beyond walls,
+// where a wall mirrors the tile's own cells) on planes z0 - 2 .. z0 + ZS + 1
+// (folded like the cells) -- is flagged pure liquid.  Every thread of the CTA
+// calls it; the answer is uniform.
+template <int ZS, class Real>
 __device__ __forceinline__ bool liquid_reach(const DevParams<Real>& P, const unsigned char* __restrict__ flags,
-                                             int bx, int by, int bz, int gx, int gy, int gz) {
+                                             int bx, int by, int z0, int gx, int gy) {
   __shared__ int s_all;
   if (threadIdx.x == 0) s_all = 1;
   __syncthreads();
-  if (threadIdx.x < 27) {
-    const int t = threadIdx.x;
-    int c[3] = {bx + t % 3 - 1, by + (t / 3) % 3 - 1, bz + t / 9 - 1};
-    const int n[3] = {gx, gy, gz};
+  if (threadIdx.x < 9 * (ZS + 4)) {
+    const int t = threadIdx.x % 9;
+    const int v = fold_axis(P, z0 - 2 + (int)threadIdx.x / 9, 2);
+    int c[2] = {bx + t % 3 - 1, by + t / 3 - 1};
+    const int n[2] = {gx, gy};
     bool skip = false;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
+    for (int a = 0; a < 2; ++a) {
       if (c[a] < 0 || c[a] >= n[a]) {
         if (P.bc[a] == kWall) skip = true;
         c[a] = c[a] < 0 ? c[a] + n[a] : c[a] - n[a];
       }
     }
-    if (!skip && !flags[((long long)c[2] * gy + c[1]) * gx + c[0]]) s_all = 0;
+    if (!skip && !flags[liquid_flag_index(c[0], c[1], v, gx, gy)]) s_all = 0;
   }
   __syncthreads();
   return s_all != 0;

@@ -201,9 +201,8 @@ struct Impl {
   static cudaError_t classify(const void* params, const void* phi, unsigned char* flags, cudaStream_t s) {
     if constexpr (D == 3) {
       const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
-      const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
-                      (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS);
-      liquid_flags_kernel<NP, Real><<<grid, 256, 0, s>>>(P, static_cast<const Real*>(phi), flags);
+      const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY, P.v_hi - P.v_lo);
+      liquid_flags_kernel<NP, Real><<<grid, 128, 0, s>>>(P, static_cast<const Real*>(phi), flags);
       return cudaGetLastError();
     } else {
       (void)params;

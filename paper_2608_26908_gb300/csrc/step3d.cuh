@@ -87,8 +87,8 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
   constexpr int W2 = S::W2, H2 = S::H2, C2 = S::C2, NS = S::NS;
   // a tile whose reach is pure liquid belongs to step3d_liquid_kernel
-  if (P.liq_dispatch && liquid_reach(P, io.flags_in, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x,
-                                     gridDim.y, gridDim.z))
+  if (P.liq_dispatch && liquid_reach<ZS>(P, io.flags_in, blockIdx.x, blockIdx.y, P.v_lo + blockIdx.z * ZS,
+                                         gridDim.x, gridDim.y))
     return;
   extern __shared__ __align__(16) unsigned char smem[];
   Real* s_phi = reinterpret_cast<Real*>(smem + S::phi);
@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   constexpr bool LIQ = !SHRINK;
   unsigned liq_hist = 0;
 
-  // every phase value this thread writes is pure liquid (for the tile's flag)
+  // every phase value this thread writes in the plane is pure liquid (for
+  // the tile's flag of that plane)
   bool out_liq = true;
 
   // OR of the phase masks over the 3x3 in-plane neighbourhood of this
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       }
 #pragma unroll
       for (int sidx = 0; sidx < NS; ++sidx) phi_out[sidx * P.plane + g] = pn[NP == 2 ? 1 : sidx];
-      out_liq = out_liq && pure_liquid(pn);
+      out_liq = pure_liquid(pn);
       if (lean_d) {
         // unchanged liquid cell: chi = 1 / (2 A_l); the source is the
         // temperature term alone (extended model)
@@ -787,11 +788,15 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
 #pragma unroll
       for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
     }
-    __syncthreads();
-  }
-  if (P.liq_dispatch) {
-    const bool all = __syncthreads_and(out_liq);
-    if (tid == 0) io.flags_out[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = all;
+    if (P.liq_dispatch) {
+      // the flag of plane M of this tile (the barrier the loop ends with)
+      const bool all = __syncthreads_and(out_liq);
+      if (tid == 0 && outM && M >= z0)
+        io.flags_out[liquid_flag_index(blockIdx.x, blockIdx.y, M, gridDim.x, gridDim.y)] = all;
+      out_liq = true;
+    } else {
+      __syncthreads();
+    }
   }
 }
 

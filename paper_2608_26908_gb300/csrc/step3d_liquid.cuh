@@ -28,10 +28,12 @@ struct Liquid3D {
   static constexpr int NT = BX * BY;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
-  static constexpr size_t u = 0;                                    // 2 planes x 3 x NT
-  static constexpr size_t mu = al(u + sizeof(Real) * 2 * 3 * NT);   // 2 planes x NC x NT
-  static constexpr size_t flux = al(mu + sizeof(Real) * 2 * NC * NT);  // 2 x NC x NT (x, y faces)
-  static constexpr size_t bytes = al(flux + sizeof(Real) * 2 * NC * NT);
+  // a ring of three planes of U and mu, and the in-plane solute fluxes of
+  // two planes: two barriers a plane (see the kernel)
+  static constexpr size_t u = 0;                                    // 3 planes x 3 x NT
+  static constexpr size_t mu = al(u + sizeof(Real) * 3 * 3 * NT);   // 3 planes x NC x NT
+  static constexpr size_t flux = al(mu + sizeof(Real) * 3 * NC * NT);  // 2 planes x 2 x NC x NT
+  static constexpr size_t bytes = al(flux + sizeof(Real) * 2 * 2 * NC * NT);
 };
 
 template <int NP, int NC, class Real, class Store, int QQ = 19, bool EXT = false>
@@ -41,8 +43,8 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
   using Lat = Lattice<QQ>;
   constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
   constexpr int NS = PhiStore<NP>::NS;
-  const int gxt = gridDim.x, gyt = gridDim.y, gzt = gridDim.z;
-  if (!liquid_reach(P, io.flags_in, blockIdx.x, blockIdx.y, blockIdx.z, gxt, gyt, gzt)) return;
+  const int gxt = gridDim.x, gyt = gridDim.y;
+  if (!liquid_reach<ZS>(P, io.flags_in, blockIdx.x, blockIdx.y, P.v_lo + blockIdx.z * ZS, gxt, gyt)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   Real* s_u = reinterpret_cast<Real*>(smem + S::u);
   Real* s_mu = reinterpret_cast<Real*>(smem + S::mu);
@@ -79,24 +81,32 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
     return f < P.v_lo - 2 ? P.v_lo - 2 : (f > P.v_hi + 1 ? P.v_hi + 1 : f);
   };
   auto zrow = [&](int fz) { return (fz - P.zbase) * zst; };
-  auto slot2 = [](int p) { return p & 1; };
+  // the segment and its two halo planes lie inside the grid: no folding and
+  // no closed z-face (in-plane faces of an inner tile are never closed)
+  const bool zin = z0 >= 1 && z0 + ZS <= nz - 1;
+  auto vzi = [&](int v) { return zin ? v : vz(v); };
 
   // solute z-face fluxes of this column: (M-1, M) carried, (M, M+1) new
   Real mz_lo[NC], mz_hi[NC];
 #pragma unroll
   for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i] = Real(0);
 
+  // Ring slots of planes M and C = M + 1 (three slots: the plane the
+  // update of one iteration reads is not rewritten before every thread has
+  // passed the next iteration's two barriers).
+  int sM = 2, sC = 0;
   for (int C = z0 - 1; C <= z0 + ZS; ++C) {
     const int M = C - 1;
+    Real* fl = s_flux + (C & 1) * 2 * NC * NT;  // in-plane fluxes of plane M
     // B. moments, U and (owned planes) collision + push, plane C
     {
-      const int fzc = vz(C);
+      const int fzc = vzi(C);
       const int gi = zrow(fzc) + gxy;
       Real mu[NC];
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
         mu[i] = (mu_in + i * P.plane)[gi];
-        s_mu[(slot2(C) * NC + i) * NT + tid] = mu[i];
+        s_mu[(sC * NC + i) * NT + tid] = mu[i];
       }
       Real dk[Q];
 #pragma unroll
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
       Real u[3], F[3];
       force_velocity<3>(P, rho, Real(1), drive, m3, u, F);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
+      for (int a = 0; a < 3; ++a) s_u[(sC * 3 + a) * NT + tid] = u[a];
       if (owner && C >= z0 && C < z0 + ZS && C < P.v_hi) {
         const bool inner_z = C >= 1 && C + 1 < nz;
         if (inner_xy && inner_z) {
@@ -137,35 +147,37 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
     // D. solute fluxes of plane M (M-1 .. M+1 liquid: M = M0, h_l = 1)
     const bool doM = M >= z0 - 1 && M <= z0 + ZS - 1;
     if (doM) {
-      const int fzm = vz(M);
-      auto face = [&](int d, int pB, int nbT, int gbd, Real* J) {
-        const bool closed = (P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d];
+      const int fzm = vzi(M);
+      // face between this cell (plane M) and nbT in plane pB (slot sB)
+      auto face = [&](int d, int pB, int sB, int nbT, int gbd, Real* J) {
+        const bool open = d == 2 ? zin : inner_xy;
+        const bool closed = !open && ((P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d]);
 #pragma unroll
         for (int i = 0; i < NC; ++i) J[i] = Real(0);
         if (closed) return;
-        const Real ua = s_u[(slot2(M) * 3 + d) * NT + tid], ub = s_u[(slot2(pB) * 3 + d) * NT + nbT];
-        const int fzB = d == 2 ? vz(pB) : fzm;
+        const Real ua = s_u[(sM * 3 + d) * NT + tid], ub = s_u[(sB * 3 + d) * NT + nbT];
+        const int fzB = d == 2 ? vzi(pB) : fzm;
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-          const Real ma = s_mu[(slot2(M) * NC + i) * NT + tid], mb = s_mu[(slot2(pB) * NC + i) * NT + nbT];
+          const Real ma = s_mu[(sM * NC + i) * NT + tid], mb = s_mu[(sB * NC + i) * NT + nbT];
           J[i] = liquid_flux(P, ma, mb, ua, ub, ceq_of(0, i, fzm), ceq_of(0, i, fzB));
         }
       };
-      face(2, M + 1, tid, M + 1, mz_hi);
+      face(2, M + 1, sC, tid, M + 1, mz_hi);
       if (M == z0 - 1) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
       } else {
         Real J[NC];
         if (tx < BX - 1) {
-          face(0, M, tid + 1, gx + 1, J);
+          face(0, M, sM, tid + 1, gx + 1, J);
 #pragma unroll
-          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 0) * NT + tid] = J[i];
+          for (int i = 0; i < NC; ++i) fl[(i * 2 + 0) * NT + tid] = J[i];
         }
         if (ty < BY - 1) {
-          face(1, M, tid + BX, gy + 1, J);
+          face(1, M, sM, tid + BX, gy + 1, J);
 #pragma unroll
-          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 1) * NT + tid] = J[i];
+          for (int i = 0; i < NC; ++i) fl[(i * 2 + 1) * NT + tid] = J[i];
         }
       }
     }
@@ -177,10 +189,10 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
         phi_out[sidx * P.plane + g] = (NP != 2 && sidx == 0) ? Real(1) : Real(0);
 #pragma unroll
       for (int i = 0; i < NC; ++i) {
-        const Real* Jx = s_flux + (i * 2 + 0) * NT;
-        const Real* Jy = s_flux + (i * 2 + 1) * NT;
+        const Real* Jx = fl + (i * 2 + 0) * NT;
+        const Real* Jy = fl + (i * 2 + 1) * NT;
         const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
-        const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
+        const Real mu = s_mu[(sM * NC + i) * NT + tid];
         Real src = Real(0);
         if constexpr (EXT) {
 #pragma unroll
@@ -193,24 +205,26 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
 #pragma unroll
       for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
     }
-    __syncthreads();
+    sM = sC;
+    sC = sC == 2 ? 0 : sC + 1;
   }
-  if (tid == 0) io.flags_out[((long long)blockIdx.z * gyt + blockIdx.y) * gxt + blockIdx.x] = 1;
+  if (tid < ZS && z0 + tid < P.v_hi) io.flags_out[liquid_flag_index(blockIdx.x, blockIdx.y, z0 + tid, gxt, gyt)] = 1;
 }
 
-// The liquid flag of every tile of a state (after a load or a frame shift):
-// one CTA per tile, set when every cell the tile owns is pure liquid.
+// The liquid flags of a state (after a load or a frame shift): one CTA per
+// xy tile and plane, the flag set when every cell the tile owns in the plane
+// is pure liquid.
 template <int NP, class Real>
 __global__ void liquid_flags_kernel(const DevParams<Real> P, const Real* __restrict__ phi,
                                     unsigned char* __restrict__ flags) {
-  constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZS;
+  constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY;
   constexpr int OX = BX - 2, OY = BY - 2;
-  const int x0 = blockIdx.x * OX, y0 = blockIdx.y * OY, z0 = P.v_lo + blockIdx.z * ZS;
-  const int wx = min(OX, P.n[0] - x0), wy = min(OY, P.n[1] - y0), wz = min(ZS, P.v_hi - z0);
+  const int x0 = blockIdx.x * OX, y0 = blockIdx.y * OY, z = P.v_lo + blockIdx.z;
+  const int wx = min(OX, P.n[0] - x0), wy = min(OY, P.n[1] - y0);
   const int zst = P.px * P.n[1];
   bool liq = true;
-  for (int c = threadIdx.x; c < wx * wy * wz; c += blockDim.x) {
-    const int x = x0 + c % wx, y = y0 + (c / wx) % wy, z = z0 + c / (wx * wy);
+  for (int c = threadIdx.x; c < wx * wy; c += blockDim.x) {
+    const int x = x0 + c % wx, y = y0 + c / wx;
     Real v[NP];
     load_phases<NP>(phi, (long long)(z - P.zbase) * zst + (long long)y * P.px + x, P.plane, v);
     bool p = v[0] == Real(1);
@@ -219,7 +233,7 @@ __global__ void liquid_flags_kernel(const DevParams<Real> P, const Real* __restr
     liq = liq && p;
   }
   liq = __syncthreads_and(liq);
-  if (threadIdx.x == 0) flags[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = liq;
+  if (threadIdx.x == 0) flags[liquid_flag_index(blockIdx.x, blockIdx.y, z, gridDim.x, gridDim.y)] = liq;
 }
 
 }  // namespace gpflbm
