@@ -101,12 +101,14 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
   // the populations and mu of plane Cn of this thread's column, copied
   // into the thread's own shared-memory slots (no other thread reads them)
   auto prefetch = [&](int Cn) {
-    const int gn = zrow(vzi(Cn)) + gxy;
+    if constexpr (S::PREF) {
+      const int gn = zrow(vzi(Cn)) + gxy;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) cp_async<sizeof(Store)>(s_pf + k * NT + tid, f_in + k * P.plane + gn);
+      for (int k = 0; k < Q; ++k) cp_async<sizeof(Store)>(s_pf + k * NT + tid, f_in + k * P.plane + gn);
 #pragma unroll
-    for (int i = 0; i < NC; ++i) cp_async<sizeof(Real)>(s_pmu + i * NT + tid, mu_in + i * P.plane + gn);
-    cp_async_commit();
+      for (int i = 0; i < NC; ++i) cp_async<sizeof(Real)>(s_pmu + i * NT + tid, mu_in + i * P.plane + gn);
+      cp_async_commit();
+    }
   };
   if constexpr (S::PREF) prefetch(z0 - 1);
 
