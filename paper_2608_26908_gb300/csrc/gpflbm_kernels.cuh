@@ -195,26 +195,6 @@ __device__ __forceinline__ bool obstacle(const DevParams<Real>& P, int x, int y,
   return false;
 }
 
-// ------------------------------------------------------------------ asynchronous copies
-// A copy of one 4- or 8-byte word from global into shared memory that the
-// issuing thread waits for later (cp.async): the load of the next plane runs
-// while the thread works on the current one.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-  static_assert(BYTES == 4 || BYTES == 8, "cp.async copies 4, 8 or 16 bytes");
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  if constexpr (BYTES == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-// Nothing after this point is issued before v has been computed (so the
-// shared-memory reads v depends on have returned).
-__device__ __forceinline__ void after(float v) { asm volatile("" ::"f"(v) : "memory"); }
-__device__ __forceinline__ void after(double v) { asm volatile("" ::"d"(v) : "memory"); }
-
 // ------------------------------------------------------------------ push streaming
 // Where the populations of a cell stream to along one axis: the offset (in
 // elements) of the +1 and -1 neighbour, periodic axes wrapping, and whether a

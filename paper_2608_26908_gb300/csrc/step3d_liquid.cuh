@@ -33,12 +33,7 @@ struct Liquid3D {
   static constexpr size_t u = 0;                                    // 3 planes x 3 x NT
   static constexpr size_t mu = al(u + sizeof(Real) * 3 * 3 * NT);   // 3 planes x NC x NT
   static constexpr size_t flux = al(mu + sizeof(Real) * 3 * NC * NT);  // 2 planes x 2 x NC x NT
-  // the next plane's populations and mu of every thread, copied ahead
-  // (cp.async moves 4- and 8-byte words: FP32 and FP64 storage)
-  static constexpr bool PREF = sizeof(Store) >= 4;
-  static constexpr size_t pf = al(flux + sizeof(Real) * 2 * 2 * NC * NT);  // QQ x NT
-  static constexpr size_t pmu = al(pf + (PREF ? sizeof(Store) * QQ * NT : 0));  // NC x NT
-  static constexpr size_t bytes = al(pmu + (PREF ? sizeof(Real) * NC * NT : 0));
+  static constexpr size_t bytes = al(flux + sizeof(Real) * 2 * 2 * NC * NT);
 };
 
 template <int NP, int NC, class Real, class Store, int QQ = 19, bool EXT = false>
@@ -54,8 +49,6 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
   Real* s_u = reinterpret_cast<Real*>(smem + S::u);
   Real* s_mu = reinterpret_cast<Real*>(smem + S::mu);
   Real* s_flux = reinterpret_cast<Real*>(smem + S::flux);
-  Store* s_pf = reinterpret_cast<Store*>(smem + S::pf);
-  Real* s_pmu = reinterpret_cast<Real*>(smem + S::pmu);
 
   const Real* __restrict__ mu_in = static_cast<const Real*>(io.mu_in);
   const Store* __restrict__ f_in = static_cast<const Store*>(io.f_in);
@@ -98,20 +91,6 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
 #pragma unroll
   for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i] = Real(0);
 
-  // the populations and mu of plane Cn of this thread's column, copied
-  // into the thread's own shared-memory slots (no other thread reads them)
-  auto prefetch = [&](int Cn) {
-    if constexpr (S::PREF) {
-      const int gn = zrow(vzi(Cn)) + gxy;
-#pragma unroll
-      for (int k = 0; k < Q; ++k) cp_async<sizeof(Store)>(s_pf + k * NT + tid, f_in + k * P.plane + gn);
-#pragma unroll
-      for (int i = 0; i < NC; ++i) cp_async<sizeof(Real)>(s_pmu + i * NT + tid, mu_in + i * P.plane + gn);
-      cp_async_commit();
-    }
-  };
-  if constexpr (S::PREF) prefetch(z0 - 1);
-
   // Ring slots of planes M and C = M + 1 (three slots: the plane the
   // update of one iteration reads is not rewritten before every thread has
   // passed the next iteration's two barriers).
@@ -123,21 +102,15 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
     {
       const int fzc = vzi(C);
       const int gi = zrow(fzc) + gxy;
-      Real mu[NC], dk[Q];
-      if constexpr (S::PREF) {
-        cp_async_wait_all();  // this thread's copies of plane C have landed
+      Real mu[NC];
 #pragma unroll
-        for (int i = 0; i < NC; ++i) mu[i] = s_pmu[i * NT + tid];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(s_pf[k * NT + tid]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < NC; ++i) mu[i] = (mu_in + i * P.plane)[gi];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
+      for (int i = 0; i < NC; ++i) {
+        mu[i] = (mu_in + i * P.plane)[gi];
+        s_mu[(sC * NC + i) * NT + tid] = mu[i];
       }
+      Real dk[Q];
 #pragma unroll
-      for (int i = 0; i < NC; ++i) s_mu[(sC * NC + i) * NT + tid] = mu[i];
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
       Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
@@ -145,15 +118,6 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
 #pragma unroll
         for (int a = 0; a < 3; ++a)
           if (Lat::c(k, a) != 0) m3[a] += Real(Lat::c(k, a)) * dk[k];
-      }
-      if constexpr (S::PREF) {
-        // the slots of plane C are read (drho and mu use them): copy plane C + 1
-        if (C + 1 <= z0 + ZS) {
-          after(drho);
-#pragma unroll
-          for (int i = 0; i < NC; ++i) after(mu[i]);
-          prefetch(C + 1);
-        }
       }
       const Real rho = Real(1) + drho;
       // the general kernel's arithmetic with phi_l = 1 (the same helpers)
