@@ -43,7 +43,7 @@ struct Step3D {
   // resident CTAs per SM the register budget is cut for: two (64 registers)
   // for two phases on D3Q19 in FP32; with more phases, or 27 populations,
   // the registers spill at 64 and one CTA of 128 registers runs faster
-  static constexpr int MIN_CTAS = (sizeof(Real) == 4 && NP == 2 && QQ == 19) ? 2 : 1;
+  static constexpr int MIN_CTAS = (sizeof(Real) == 4 && QQ == 19) ? 2 : 1;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;
   static constexpr int RING = C2 - NT;
