@@ -65,10 +65,6 @@ struct gpflbm_s {
   cudaStream_t xfer;
   cudaEvent_t ev_mark, ev_loaded;
   unsigned long long mut, marked;
-  // 3D with liquid tiles: the liquid-tile kernel runs on `side` beside the
-  // general kernel on the step's stream (fork and join events)
-  cudaStream_t side;
-  cudaEvent_t ev_fork, ev_join;
   // device parameters in the arithmetic type (only one is used)
   DevParams<double> pd;
   DevParams<float> pf;
@@ -416,9 +412,6 @@ gpflbm::StepIO step_io(gpflbm_t h, int from) {
   io.clock_out = reinterpret_cast<double*>(at(h, h->lay.clock)) + 1 - from;
   io.flags_in = static_cast<const unsigned char*>(at(h, h->lay.flags[from]));
   io.flags_out = static_cast<unsigned char*>(at(h, h->lay.flags[1 - from]));
-  io.side = h->side;
-  io.fork = h->ev_fork;
-  io.join = h->ev_join;
   return io;
 }
 
@@ -615,14 +608,10 @@ gpflbm_status create_impl(const gpflbm_grid* grid, int n_phases, int n_component
   cudaError_t e = h->ops->configure();
   if (e == cudaSuccess) e = h->ops_ext->configure();
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking);
-  if (e == cudaSuccess && D == 3 && !slab) {
-    e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-  }
   if (e != cudaSuccess) {
     std::fprintf(stderr, "gpflbm_create: %s\n", cudaGetErrorString(e));
-    gpflbm_destroy(h);
+    if (h->owns_ws) cudaFree(h->ws);
+    delete h;
     return GPFLBM_ERR_CUDA;
   }
   e = cudaMemset(h->ws, 0, h->lay.total);  // padding cells stay finite
@@ -1165,12 +1154,6 @@ void gpflbm_destroy(gpflbm_t h) {
   if (!h) return;
   drop_graphs(h);
   if (h->capture) cudaStreamDestroy(h->capture);
-  if (h->side) {
-    cudaStreamSynchronize(h->side);
-    cudaStreamDestroy(h->side);
-  }
-  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
-  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->xfer) {
     // an asynchronous load may still write the workspace, which the caller
     // may free once this returns
@@ -1399,8 +1382,6 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     io.clock_out = forward_pass ? fw_clk(c, j + 1) : clk_at(c, j + 1);
     io.flags_in = nullptr;  // 2D: no liquid-tile flags
     io.flags_out = nullptr;
-    io.side = nullptr;
-    io.fork = io.join = nullptr;
     return stepper(h)->step(P, io, st);
   };
   // copies of one stored state: handle -> slot, or slot -> handle

@@ -23,11 +23,6 @@ struct StepIO {
   double* clock_out;
   const unsigned char* flags_in;  // 3D: liquid flag per tile of the input state
   unsigned char* flags_out;       // ... of the output state
-  // 3D with liquid tiles: a second stream and two events on which the
-  // liquid-tile kernel runs beside the general kernel (they advance disjoint
-  // tiles); null: one after the other on the step's stream
-  cudaStream_t side;
-  cudaEvent_t fork, join;
 };
 
 struct FieldsIO {
@@ -133,27 +128,13 @@ struct Impl {
                       (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS);
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in,    io.mu_out,    io.f_in,
                             io.f_out,  io.clock_in, io.clock_out, io.flags_in, io.flags_out};
-      const bool beside = P.liq_dispatch && io.side != nullptr;
-      cudaError_t e = cudaSuccess;
-      if (beside) e = cudaEventRecord(io.fork, s);
-      if (e != cudaSuccess) return e;
       if (P.shrink)
         step3d_kernel<NP, NC, Real, Store, true, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
       else
         step3d_kernel<NP, NC, Real, Store, false, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
-      // the tiles whose reach is pure liquid (the general kernel returns
-      // there), beside the general kernel when a second stream is given
-      if (P.liq_dispatch) {
-        const cudaStream_t t = beside ? io.side : s;
-        if (beside) e = cudaStreamWaitEvent(io.side, io.fork, 0);
-        if (e != cudaSuccess) return e;
-        step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<grid, SL::NT, SL::bytes, t>>>(P, sio);
-        if (beside) {
-          e = cudaEventRecord(io.join, io.side);
-          if (e == cudaSuccess) e = cudaStreamWaitEvent(s, io.join, 0);
-          if (e != cudaSuccess) return e;
-        }
-      }
+      // the tiles whose reach is pure liquid (the general kernel returned there)
+      if (P.liq_dispatch)
+        step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<grid, SL::NT, SL::bytes, s>>>(P, sio);
     }
     return cudaGetLastError();
   }
