@@ -687,7 +687,8 @@ def our_arm(args):
         pg.destroy_process_group() if pg else None
         return 0
     nx_, ny_, nz_ = inputs.dims(sc)
-    # one step: one fused launch in 2D; in 3D the general kernel and the
+    # one step: one fused launch in 2D; in 3D one launch over the general and
+    # the liquid tiles (FP32 on D3Q19), else the general kernel and the
     # liquid-tile kernel over disjoint tiles (every cell advanced once)
     dom_name = ("step3d_kernel + step3d_liquid_kernel" if launches == 2 else
                 "step%dd_kernel" % (3 if nz_ > 1 else 2))

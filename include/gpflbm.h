@@ -365,11 +365,13 @@ gpflbm_status gpflbm_adjoint(gpflbm_t h, const gpflbm_objective* obj, int horizo
 gpflbm_status gpflbm_vjp(gpflbm_t h, int horizon, int ckpt_every, void* workspace, size_t workspace_bytes,
                          const void* seed, void* grad, double* dparams, int flags, void* stream);
 
-/* Kernel launches one step makes with the current parameters: 1 (2D, and
- * 3D slabs or 3D runs with shrinkage or obstacle rows), or 2 (3D: the
- * general step kernel over the tiles whose reach holds more than pure
- * liquid, then the liquid-tile kernel over the others; each tile is
- * advanced by exactly one of them).  Does not touch the GPU. */
+/* Kernel launches one step makes with the current parameters: 1 or 2.
+ * In 3D the tiles whose reach is pure liquid take a lean path and the
+ * others the general one (not on slabs, nor with shrinkage or obstacle
+ * rows); each tile is advanced by exactly one of them.  With FP32
+ * arithmetic on D3Q19 one launch runs both paths (the general tiles start
+ * first); with FP64 or D3Q27 the general kernel runs, then the liquid-tile
+ * kernel: 2.  Every other case: 1.  Does not touch the GPU. */
 gpflbm_status gpflbm_step_launches(gpflbm_t h, int* launches);
 
 /* Step counter of the current state (the t of T(v, t)). */

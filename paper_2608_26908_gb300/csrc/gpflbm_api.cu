@@ -1138,7 +1138,7 @@ gpflbm_status gpflbm_halo_unpack(gpflbm_t h, int side, const void* msg, void* st
 
 gpflbm_status gpflbm_step_launches(gpflbm_t h, int* launches) {
   if (!h || !launches) return GPFLBM_ERR_ARG;
-  *launches = h->pf.liq_dispatch ? 2 : 1;
+  *launches = h->pf.liq_dispatch ? stepper(h)->liquid_step_launches : 1;
   return GPFLBM_OK;
 }
 

@@ -154,8 +154,8 @@ struct DevParams {
   // planes v_lo .. v_hi - 1 of a grid of n[2] planes, and the field buffers
   // start at plane zbase.  A whole grid: v_lo = 0, v_hi = n[2], zbase = 0.
   int v_lo, v_hi, zbase;
-  // 3D: tiles whose reach is pure liquid go to step3d_liquid_kernel (per-tile
-  // flags of the state); 0 = every tile takes the general kernel
+  // 3D: tiles whose reach is pure liquid take the liquid path (per-tile
+  // flags of the state); 0 = every tile takes the general path
   int liq_dispatch;
 };
 

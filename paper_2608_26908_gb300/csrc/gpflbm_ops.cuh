@@ -43,6 +43,9 @@ struct Ops {
   int D, NP, NC, Q;
   size_t real_size, store_size;
   int stored_phi_planes;
+  // 3D: launches of one step when liquid tiles take their own path (1: one
+  // launch runs both paths; 2: the general kernel, then the liquid kernel)
+  int liquid_step_launches;
   // opts the step kernels in to their dynamic shared memory (once per process)
   cudaError_t (*configure)();
   // one time step S^n -> S^{n+1}: one fused launch
@@ -91,6 +94,8 @@ struct Impl {
   using SZ = Step2D<NP, NC, Real, Store>;
   using S3 = Step3D<NP, NC, Real, Store, (D == 3 ? Q : 19)>;
   using SL = Liquid3D<NP, NC, Real, Store, (D == 3 ? Q : 19), EXT>;
+  // 3D: dynamic shared memory of step3d_kernel (both paths when it runs both)
+  static constexpr size_t step3d_bytes = !S3::ONE_LAUNCH ? S3::bytes : (S3::bytes > SL::bytes ? S3::bytes : SL::bytes);
 
   static cudaError_t configure() {
     cudaError_t e;
@@ -102,13 +107,15 @@ struct Impl {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
     } else {
       e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false, Q, EXT>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step3d_bytes);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q, EXT>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S3::bytes);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL::bytes);
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step3d_bytes);
+      if constexpr (!S3::ONE_LAUNCH) {
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL::bytes);
+      }
     }
     return e;
   }
@@ -124,17 +131,21 @@ struct Impl {
       else
         step2d_kernel<NP, NC, Real, Store, false, EXT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
     } else {
+      // the tiling (twice over in z when one launch takes both passes)
+      const unsigned gz = (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS;
       const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
-                      (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS);
+                      S3::ONE_LAUNCH && P.liq_dispatch ? 2 * gz : gz);
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in,    io.mu_out,    io.f_in,
                             io.f_out,  io.clock_in, io.clock_out, io.flags_in, io.flags_out};
       if (P.shrink)
-        step3d_kernel<NP, NC, Real, Store, true, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, true, Q, EXT><<<grid, S3::NT, step3d_bytes, s>>>(P, sio);
       else
-        step3d_kernel<NP, NC, Real, Store, false, Q, EXT><<<grid, S3::NT, S3::bytes, s>>>(P, sio);
+        step3d_kernel<NP, NC, Real, Store, false, Q, EXT><<<grid, S3::NT, step3d_bytes, s>>>(P, sio);
       // the tiles whose reach is pure liquid (the general kernel returned there)
-      if (P.liq_dispatch)
-        step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<grid, SL::NT, SL::bytes, s>>>(P, sio);
+      if constexpr (!S3::ONE_LAUNCH) {
+        if (P.liq_dispatch)
+          step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<grid, SL::NT, SL::bytes, s>>>(P, sio);
+      }
     }
     return cudaGetLastError();
   }
@@ -230,6 +241,7 @@ struct Impl {
                             sizeof(Real),
                             sizeof(Store),
                             PhiStore<NP>::NS,
+                            D == 3 && !S3::ONE_LAUNCH ? 2 : 1,
                             &Impl::configure,
                             &Impl::step,
                             &Impl::load,

@@ -44,6 +44,8 @@ struct Step3D {
   // for two phases on D3Q19 in FP32; with more phases, or 27 populations,
   // the registers spill at 64 and one CTA of 128 registers runs faster
   static constexpr int MIN_CTAS = (sizeof(Real) == 4 && QQ == 19) ? 2 : 1;
+  // both paths in one launch where they have the same register budget
+  static constexpr bool ONE_LAUNCH = MIN_CTAS == 2;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;
   static constexpr int RING = C2 - NT;
@@ -79,17 +81,15 @@ struct Step3DIO {
 // and equilibrium compositions ceq_a(T) with the temperature term of Eq. conc.
 // SHRINK: the shrinkage force needs phi^{n+1}, so the collision of a plane
 // moves after its phase-field update (its populations are read again then).
-template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19, bool EXT = false>
-__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
-    step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
+// The general path for one tile: xy tile (bx, by) of a gxt x gyt tiling,
+// z segment bz.  The kernels that run it are at the end of step3d_liquid.cuh.
+template <int NP, int NC, class Real, class Store, bool SHRINK, int QQ, bool EXT>
+__device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Step3DIO& io, int bx, int by, int bz,
+                                             int gxt, int gyt) {
   using S = Step3D<NP, NC, Real, Store, QQ>;
   using Lat = Lattice<QQ>;
   constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
   constexpr int W2 = S::W2, H2 = S::H2, C2 = S::C2, NS = S::NS;
-  // a tile whose reach is pure liquid belongs to step3d_liquid_kernel
-  if (P.liq_dispatch && liquid_reach<ZS>(P, io.flags_in, blockIdx.x, blockIdx.y, P.v_lo + blockIdx.z * ZS,
-                                         gridDim.x, gridDim.y))
-    return;
   extern __shared__ __align__(16) unsigned char smem[];
   Real* s_phi = reinterpret_cast<Real*>(smem + S::phi);
   unsigned char* s_mask = smem + S::mask;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   const int zst = px * ny;  // plane stride (a plane holds fewer than 2^31 cells)
   // z segments start at the first owned plane (v_lo = 0 for a whole grid;
   // a slab owns planes v_lo .. v_hi - 1 of the vertical axis)
-  const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY, z0 = P.v_lo + blockIdx.z * ZS;
+  const int x0 = bx * S::OX, y0 = by * S::OY, z0 = P.v_lo + bz * ZS;
   const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
   const bool inner_xy = x0 >= 2 && x0 - 2 + W2 <= nx && y0 >= 2 && y0 - 2 + H2 <= ny;
   const int fx = inner_xy ? gx : fold_axis(P, gx, 0);
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   // inner columns of the tile write the tile's cells
   const bool owner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && gx < nx && gy < ny;
   const double t_now = io.clock_in[0];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
+  if (bx == 0 && by == 0 && bz == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
   // EXT: ceq_a,i(T) at vertical index v, T - T_E = theta_base + G v
   auto ceq_of = [&](int a, int i, int v) -> Real {
@@ -792,7 +792,7 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
       // the flag of plane M of this tile (the barrier the loop ends with)
       const bool all = __syncthreads_and(out_liq);
       if (tid == 0 && outM && M >= z0)
-        io.flags_out[liquid_flag_index(blockIdx.x, blockIdx.y, M, gridDim.x, gridDim.y)] = all;
+        io.flags_out[liquid_flag_index(bx, by, M, gxt, gyt)] = all;
       out_liq = true;
     } else {
       __syncthreads();

@@ -4,17 +4,17 @@
 // in every 3x3x3 neighbourhood, so it has no rate), the chemical potential
 // diffusing with M = D_liq / (2 A_l) and advected by U^n with h_l = 1 and
 // chi = 1 / (2 A_l), and the lattice Boltzmann step with phi_l = 1 (no drag,
-// the full buoyancy).  step3d_liquid_kernel advances such tiles with the
-// same arithmetic, term for term, as step3d_kernel's liquid-plane path --
+// the full buoyancy).  liquid_tile advances such tiles with the same
+// arithmetic, term for term, as the general path's liquid planes --
 // the results are bit-identical -- but without the phase-field machinery,
 // so it needs far fewer registers and instructions.
 //
 // Which tiles are liquid: a flag per tile of the step grid (x tile, y tile,
 // z segment) says that every cell the tile owns is pure liquid.  A tile whose
 // own flag and its 26 neighbours' flags are set reads only pure liquid (its
-// reach is two cells and two planes), so the liquid kernel takes it and the
-// general kernel returns at once; otherwise the general kernel takes it and
-// the liquid kernel returns.  Both write the flag of the tile's new state.
+// reach is two cells and two planes), so the liquid path takes it;
+// otherwise the general path does.  Both write the flags of the tile's new
+// state, one per plane.
 #pragma once
 
 #include "gpflbm_kernels.cuh"
@@ -36,15 +36,14 @@ struct Liquid3D {
   static constexpr size_t bytes = al(flux + sizeof(Real) * 2 * 2 * NC * NT);
 };
 
-template <int NP, int NC, class Real, class Store, int QQ = 19, bool EXT = false>
-__global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
-    step3d_liquid_kernel(const DevParams<Real> P, const Step3DIO io) {
+// The liquid path for one tile (coordinates as for general_tile).
+template <int NP, int NC, class Real, class Store, int QQ, bool EXT>
+__device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step3DIO& io, int bx, int by, int bz,
+                                            int gxt, int gyt) {
   using S = Liquid3D<NP, NC, Real, Store, QQ, EXT>;
   using Lat = Lattice<QQ>;
   constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
   constexpr int NS = PhiStore<NP>::NS;
-  const int gxt = gridDim.x, gyt = gridDim.y;
-  if (!liquid_reach<ZS>(P, io.flags_in, blockIdx.x, blockIdx.y, P.v_lo + blockIdx.z * ZS, gxt, gyt)) return;
   extern __shared__ __align__(16) unsigned char smem[];
   Real* s_u = reinterpret_cast<Real*>(smem + S::u);
   Real* s_mu = reinterpret_cast<Real*>(smem + S::mu);
@@ -60,7 +59,7 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
   const int tx = tid % BX, ty = tid / BX;
   const int nx = P.n[0], ny = P.n[1], nz = P.n[2], px = P.px;
   const int zst = px * ny;
-  const int x0 = blockIdx.x * S::OX, y0 = blockIdx.y * S::OY, z0 = P.v_lo + blockIdx.z * ZS;
+  const int x0 = bx * S::OX, y0 = by * S::OY, z0 = P.v_lo + bz * ZS;
   const int gx = x0 - 1 + tx, gy = y0 - 1 + ty;
   const bool inner_xy = x0 >= 2 && x0 - 2 + BX + 2 <= nx && y0 >= 2 && y0 - 2 + BY + 2 <= ny;
   const int fx = inner_xy ? gx : fold_axis(P, gx, 0);
@@ -68,7 +67,7 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
   const int gxy = fy * px + fx;
   const bool owner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && gx < nx && gy < ny;
   const double t_now = io.clock_in[0];
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
+  if (bx == 0 && by == 0 && bz == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
   auto ceq_of = [&](int a, int i, int v) -> Real {
     if constexpr (EXT)
@@ -208,7 +207,45 @@ __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
     sM = sC;
     sC = sC == 2 ? 0 : sC + 1;
   }
-  if (tid < ZS && z0 + tid < P.v_hi) io.flags_out[liquid_flag_index(blockIdx.x, blockIdx.y, z0 + tid, gxt, gyt)] = 1;
+  if (tid < ZS && z0 + tid < P.v_hi) io.flags_out[liquid_flag_index(bx, by, z0 + tid, gxt, gyt)] = 1;
+}
+
+// The step kernels.  Where both paths fit 64 registers (FP32 arithmetic on
+// D3Q19: two CTAs share an SM either way) one launch takes every tile: its
+// grid holds the tiling twice, z blocks 0 .. gzt-1 the general pass and
+// gzt .. 2 gzt-1 the liquid pass, and a CTA returns unless its tile's flags
+// pick its pass.  CTAs start in block order, so the general tiles, the slow
+// ones, start first and the liquid tiles fill the SMs as they finish
+// instead of waiting for the last general tile.  Elsewhere (FP64, D3Q27:
+// the general path needs more registers than the liquid one, and one kernel
+// would hold the liquid tiles to its occupancy) step3d_kernel takes the
+// general tiles and step3d_liquid_kernel, launched after it, the others.
+template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19, bool EXT = false>
+__global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
+    step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
+  using S = Step3D<NP, NC, Real, Store, QQ>;
+  constexpr int ZS = S::ZS;
+  const int gxt = gridDim.x, gyt = gridDim.y, gzt = (P.v_hi - P.v_lo + ZS - 1) / ZS;
+  const int bx = blockIdx.x, by = blockIdx.y;
+  const bool liquid_pass = S::ONE_LAUNCH && (int)blockIdx.z >= gzt;
+  const int bz = liquid_pass ? (int)blockIdx.z - gzt : (int)blockIdx.z;
+  if (P.liq_dispatch && liquid_reach<ZS>(P, io.flags_in, bx, by, P.v_lo + bz * ZS, gxt, gyt) != liquid_pass) return;
+  if constexpr (S::ONE_LAUNCH) {
+    if (liquid_pass) {
+      liquid_tile<NP, NC, Real, Store, QQ, EXT>(P, io, bx, by, bz, gxt, gyt);
+      return;
+    }
+  }
+  general_tile<NP, NC, Real, Store, SHRINK, QQ, EXT>(P, io, bx, by, bz, gxt, gyt);
+}
+
+template <int NP, int NC, class Real, class Store, int QQ = 19, bool EXT = false>
+__global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
+    step3d_liquid_kernel(const DevParams<Real> P, const Step3DIO io) {
+  constexpr int ZS = Liquid3D<NP, NC, Real, Store, QQ, EXT>::ZS;
+  if (!liquid_reach<ZS>(P, io.flags_in, blockIdx.x, blockIdx.y, P.v_lo + blockIdx.z * ZS, gridDim.x, gridDim.y))
+    return;
+  liquid_tile<NP, NC, Real, Store, QQ, EXT>(P, io, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
 }
 
 // The liquid flags of a state (after a load or a frame shift): one CTA per
