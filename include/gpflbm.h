@@ -368,9 +368,9 @@ gpflbm_status gpflbm_vjp(gpflbm_t h, int horizon, int ckpt_every, void* workspac
 /* Kernel launches one step makes with the current parameters: 1 or 2.
  * In 3D the tiles whose reach is pure liquid take a lean path and the
  * others the general one (not on slabs, nor with shrinkage or obstacle
- * rows); each tile is advanced by exactly one of them.  With FP32
- * arithmetic on D3Q19 one launch runs both paths (the general tiles start
- * first); with FP64 or D3Q27 the general kernel runs, then the liquid-tile
+ * rows); each tile is advanced by exactly one of them.  Two phases with
+ * FP32 arithmetic on D3Q19: one launch runs both paths (the general tiles
+ * start first).  Otherwise the general kernel runs, then the liquid-tile
  * kernel: 2.  Every other case: 1.  Does not touch the GPU. */
 gpflbm_status gpflbm_step_launches(gpflbm_t h, int* launches);
 

@@ -530,9 +530,13 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
         J[i] = -Mf * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fy) + ma * P.inv2A[0]) +
                                               ub * (ceq_of(0, i, vb) + mb * P.inv2A[0]));
       }
-      if (any_changed && P.at_eps != Real(0) && (s_chg[tid] | s_chg[nb])) {
+      // the current carries phi_l's face value as a factor of every term: on a
+      // face without liquid it is exactly 0 and skipped
+      const Real liq = any_changed && P.at_eps != Real(0) && (s_chg[tid] | s_chg[nb])
+                           ? Real(0.5) * (s_phi[r2] + s_phi[nr])
+                           : Real(0);
+      if (liq != Real(0)) {
         const int st = d == 0 ? W2 : 1;  // transverse stride
-        const Real liq = Real(0.5) * (s_phi[r2] + s_phi[nr]);
         Real at[NC];
 #pragma unroll
         for (int i = 0; i < NC; ++i) at[i] = Real(0);

@@ -44,8 +44,12 @@ struct Step3D {
   // for two phases on D3Q19 in FP32; with more phases, or 27 populations,
   // the registers spill at 64 and one CTA of 128 registers runs faster
   static constexpr int MIN_CTAS = (sizeof(Real) == 4 && QQ == 19) ? 2 : 1;
-  // both paths in one launch where they have the same register budget
-  static constexpr bool ONE_LAUNCH = MIN_CTAS == 2;
+  // both paths in one launch where they have the same register budget and
+  // the general path is light (two phases).  With more phases a general
+  // tile sharing its SM with a liquid-tile CTA, which issues far more
+  // often, is slowed so much that the slowest general tiles end last: the
+  // ternary eutectic takes 2.32 ms a step in one launch, 2.04 ms in two.
+  static constexpr bool ONE_LAUNCH = MIN_CTAS == 2 && NP == 2;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;
   static constexpr int RING = C2 - NT;
@@ -646,8 +650,13 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
           J[i] = -Mf * (mb - ma) + Real(0.5) * (ua * (ceq_of(0, i, fzm) + ma * P.inv2A[0]) +
                                                 ub * (ceq_of(0, i, fzB) + mb * P.inv2A[0]));
         }
-        if (P.at_eps != Real(0) && (s_chg[slot2(pA) * NT + A] | s_chg[slot2(pB) * NT + nbT])) {
-          const Real liq = Real(0.5) * (PH(pA, 0, rA) + PH(pB, 0, nbR));
+        // the current carries phi_l's face value as a factor of every term: on
+        // a face without liquid (grain boundaries inside the solid) it is
+        // exactly 0 and skipped
+        const Real liq = P.at_eps != Real(0) && (s_chg[slot2(pA) * NT + A] | s_chg[slot2(pB) * NT + nbT])
+                             ? Real(0.5) * (PH(pA, 0, rA) + PH(pB, 0, nbR))
+                             : Real(0);
+        if (liq != Real(0)) {
           Real at[NC];
 #pragma unroll
           for (int i = 0; i < NC; ++i) at[i] = Real(0);

@@ -211,15 +211,17 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
 }
 
 // The step kernels.  Where both paths fit 64 registers (FP32 arithmetic on
-// D3Q19: two CTAs share an SM either way) one launch takes every tile: its
+// D3Q19: two CTAs share an SM either way) and the general path is that of
+// two phases (Step3D::ONE_LAUNCH), one launch takes every tile: its
 // grid holds the tiling twice, z blocks 0 .. gzt-1 the general pass and
 // gzt .. 2 gzt-1 the liquid pass, and a CTA returns unless its tile's flags
 // pick its pass.  CTAs start in block order, so the general tiles, the slow
 // ones, start first and the liquid tiles fill the SMs as they finish
 // instead of waiting for the last general tile.  Elsewhere (FP64, D3Q27:
 // the general path needs more registers than the liquid one, and one kernel
-// would hold the liquid tiles to its occupancy) step3d_kernel takes the
-// general tiles and step3d_liquid_kernel, launched after it, the others.
+// would hold the liquid tiles to its occupancy; three or four phases: see
+// ONE_LAUNCH) step3d_kernel takes the general tiles and
+// step3d_liquid_kernel, launched after it, the others.
 template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19, bool EXT = false>
 __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
