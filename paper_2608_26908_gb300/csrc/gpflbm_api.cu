@@ -249,6 +249,7 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
     for (int b = 0; b < 4; ++b) {
       P.gamma[a][b] = (Real)p.gamma[a][b];
       P.delta[a][b] = (Real)p.delta[a][b];
+      if (a < h->NP && b < h->NP && a != b && P.delta[a][b] != Real(0)) P.aniso = 1;
     }
     P.inv2A[a] = (Real)(1.0 / (2.0 * p.A[a]));
     P.inv4A[a] = (Real)(1.0 / (4.0 * p.A[a]));
@@ -259,7 +260,7 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
       const double th = a < h->NP && b < h->NP && a != b ? p.tilt[a][b] : 0.0;
       P.tilt_c[a][b] = (Real)std::cos(th);
       P.tilt_s[a][b] = (Real)std::sin(th);
-      if (th != 0.0) P.tilted = 1;
+      if (th != 0.0) P.tilted = P.aniso = 1;
     }
     for (int i = 0; i < 2; ++i) {
       const double k = a < h->NP && i < h->NC ? p.dceq_dT[a][i] : 0.0;

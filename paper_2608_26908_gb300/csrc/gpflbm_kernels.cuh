@@ -157,6 +157,11 @@ struct DevParams {
   // 3D: tiles whose reach is pure liquid take the liquid path (per-tile
   // flags of the state); 0 = every tile takes the general path
   int liq_dispatch;
+  // 1 if any pair of the problem's phases has a nonzero anisotropy delta, or
+  // a turned crystal frame.  Otherwise dA/dq = 2 q, and a face flux needs
+  // only the normal component of each face gradient (the transverse ones
+  // are skipped, exactly).
+  int aniso;
 };
 
 // 1/x rounded to nearest: the same value as the IEEE division 1/x, by the
@@ -352,13 +357,14 @@ __device__ __forceinline__ Real interp_dh(const Real* p, int b, int a) {
 // Only component j is returned, but it depends on all of q.
 template <int D, class Real>
 __device__ __forceinline__ Real dAdq(const Real* q, Real delta, Real q_floor, int j) {
+  if (delta == Real(0)) return Real(2) * q[j];  // isotropic pair
   Real s2 = Real(0), s4 = Real(0);
 #pragma unroll
   for (int t = 0; t < D; ++t) {
     s2 += q[t] * q[t];
     s4 += q[t] * q[t] * q[t] * q[t];
   }
-  if (delta == Real(0) || s2 <= q_floor) return Real(2) * q[j];
+  if (s2 <= q_floor) return Real(2) * q[j];
   const Real inv2 = Real(1) / s2;
   const Real r4 = s4 * inv2 * inv2;
   const Real ac = Real(1) - delta * (Real(3) - Real(4) * r4);
@@ -424,10 +430,12 @@ __device__ __forceinline__ void collide(const DevParams<Real>& P, const Real* dk
 template <int D, class Real>
 __device__ __forceinline__ void dAdq_vec(const Real* q, Real delta, Real q_floor, Real* out) {
   Real s2 = Real(0), s4 = Real(0);
+  if (delta != Real(0)) {  // an isotropic pair needs neither sum
 #pragma unroll
-  for (int t = 0; t < D; ++t) {
-    s2 += q[t] * q[t];
-    s4 += q[t] * q[t] * q[t] * q[t];
+    for (int t = 0; t < D; ++t) {
+      s2 += q[t] * q[t];
+      s4 += q[t] * q[t] * q[t] * q[t];
+    }
   }
   if (delta == Real(0) || s2 <= q_floor) {
 #pragma unroll

@@ -355,7 +355,8 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
           const Real* sp = s_phi + a * C2;
           pf[a] = Real(0.5) * (sp[ca] + sp[cb]);
           gn[a] = sp[cb] - sp[ca];
-          gt[a] = Real(0.25) * (sp[ca + st] + sp[cb + st] - sp[ca - st] - sp[cb - st]);
+          // dA/dq = 2 q without anisotropy: only q_d enters the flux
+          gt[a] = P.aniso ? Real(0.25) * (sp[ca + st] + sp[cb + st] - sp[ca - st] - sp[cb - st]) : Real(0);
         }
 #pragma unroll
         for (int a = 0; a < NP; ++a)

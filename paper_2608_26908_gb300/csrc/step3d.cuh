@@ -245,13 +245,13 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
       if (!(grp & (1u << a))) continue;
       const Real va = PH(pa, a, ia), vb = PH(pb, a, ib);
       pf[a] = Real(0.5) * (va + vb);
+      g3[a][d] = vb - va;
+      if (!P.aniso) continue;  // dA/dq = 2 q: only q_d enters the flux
       if (d == 2) {
-        g3[a][2] = vb - va;
         g3[a][0] = Real(0.25) * (PH(pa, a, ia + 1) + PH(pb, a, ib + 1) - PH(pa, a, ia - 1) - PH(pb, a, ib - 1));
         g3[a][1] = Real(0.25) * (PH(pa, a, ia + W2) + PH(pb, a, ib + W2) - PH(pa, a, ia - W2) - PH(pb, a, ib - W2));
       } else {
         const int st = d == 0 ? W2 : 1;  // the other in-plane axis
-        g3[a][d] = vb - va;
         g3[a][1 - d] = Real(0.25) * (PH(pa, a, ia + st) + PH(pb, a, ib + st) - PH(pa, a, ia - st) - PH(pb, a, ib - st));
         g3[a][2] = Real(0.25) * (PH(pa + 1, a, ia) + PH(pb + 1, a, ib) - PH(pa - 1, a, ia) - PH(pb - 1, a, ib));
       }
