@@ -131,12 +131,10 @@ struct Impl {
       else
         step2d_kernel<NP, NC, Real, Store, false, EXT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
     } else {
-      // the general tiling, followed in z by the liquid one when one launch
-      // takes both passes
-      const unsigned gzg = (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS;
-      const unsigned gzl = (P.v_hi - P.v_lo + SL::ZS - 1) / SL::ZS;
-      const unsigned gx = (P.n[0] + S3::OX - 1) / S3::OX, gy = (P.n[1] + S3::OY - 1) / S3::OY;
-      const dim3 grid(gx, gy, S3::ONE_LAUNCH && P.liq_dispatch ? gzg + gzl : gzg);
+      // the tiling (twice over in z when one launch takes both passes)
+      const unsigned gz = (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS;
+      const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
+                      S3::ONE_LAUNCH && P.liq_dispatch ? 2 * gz : gz);
       const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in,    io.mu_out,    io.f_in,
                             io.f_out,  io.clock_in, io.clock_out, io.flags_in, io.flags_out};
       if (P.shrink)
@@ -146,7 +144,7 @@ struct Impl {
       // the tiles whose reach is pure liquid (the general kernel returned there)
       if constexpr (!S3::ONE_LAUNCH) {
         if (P.liq_dispatch)
-          step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<dim3(gx, gy, gzl), SL::NT, SL::bytes, s>>>(P, sio);
+          step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<grid, SL::NT, SL::bytes, s>>>(P, sio);
       }
     }
     return cudaGetLastError();

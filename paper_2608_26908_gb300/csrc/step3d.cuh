@@ -24,27 +24,20 @@
 
 namespace gpflbm {
 
-// Tiles of the 3D step: BX x BY threads (BX-2 x BY-2 owned columns).  ZS:
-// the planes of a liquid-tile CTA, and the z segment a tile's liquid flag
-// check covers; ZSG: the planes of a general-path CTA (a divisor of ZS, so
-// that every general CTA lies inside one checked segment).  Short general
-// CTAs shorten the march a lone CTA makes on an SM; the liquid CTAs are
-// issue-bound, and longer marches spend less on their halo planes.
 template <class Real>
 struct Block3D;
 template <>
 struct Block3D<float> {
-  static constexpr int BX = 32, BY = 16, ZS = 16, ZSG = 16;
+  static constexpr int BX = 32, BY = 16, ZS = 16;
 };
 template <>
 struct Block3D<double> {
-  static constexpr int BX = 32, BY = 8, ZS = 16, ZSG = 16;
+  static constexpr int BX = 32, BY = 8, ZS = 16;
 };
 
 template <int NP, int NC, class Real, class Store, int QQ = 19>
 struct Step3D {
-  static constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZSG;
-  static_assert(Block3D<Real>::ZS % Block3D<Real>::ZSG == 0, "a general CTA lies inside one checked segment");
+  static constexpr int BX = Block3D<Real>::BX, BY = Block3D<Real>::BY, ZS = Block3D<Real>::ZS;
   static constexpr int NT = BX * BY, Q = QQ;  // D3Q19 or D3Q27
   static constexpr int NS = PhiStore<NP>::NS;
   // resident CTAs per SM the register budget is cut for: two (64 registers)

@@ -226,14 +226,12 @@ template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ =
 __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
     step3d_kernel(const DevParams<Real> P, const Step3DIO io) {
   using S = Step3D<NP, NC, Real, Store, QQ>;
-  constexpr int ZSG = S::ZS, ZSL = Block3D<Real>::ZS;  // general CTA, checked segment
-  const int gxt = gridDim.x, gyt = gridDim.y, gzg = (P.v_hi - P.v_lo + ZSG - 1) / ZSG;
+  constexpr int ZS = S::ZS;
+  const int gxt = gridDim.x, gyt = gridDim.y, gzt = (P.v_hi - P.v_lo + ZS - 1) / ZS;
   const int bx = blockIdx.x, by = blockIdx.y;
-  const bool liquid_pass = S::ONE_LAUNCH && (int)blockIdx.z >= gzg;
-  const int bz = liquid_pass ? (int)blockIdx.z - gzg : (int)blockIdx.z;
-  // the checked segment this CTA's planes lie in
-  const int seg0 = P.v_lo + (liquid_pass ? bz : bz * ZSG / ZSL) * ZSL;
-  if (P.liq_dispatch && liquid_reach<ZSL>(P, io.flags_in, bx, by, seg0, gxt, gyt) != liquid_pass) return;
+  const bool liquid_pass = S::ONE_LAUNCH && (int)blockIdx.z >= gzt;
+  const int bz = liquid_pass ? (int)blockIdx.z - gzt : (int)blockIdx.z;
+  if (P.liq_dispatch && liquid_reach<ZS>(P, io.flags_in, bx, by, P.v_lo + bz * ZS, gxt, gyt) != liquid_pass) return;
   if constexpr (S::ONE_LAUNCH) {
     if (liquid_pass) {
       liquid_tile<NP, NC, Real, Store, QQ, EXT>(P, io, bx, by, bz, gxt, gyt);
