@@ -24,11 +24,18 @@
 
 namespace gpflbm {
 
+// Tiles of the 3D step: BX x BY threads (BX-2 x BY-2 owned columns), ZS
+// planes a CTA.  FP32: six planes, measured best on both 3D workloads
+// (ternary eutectic 1.82 ms a step against 1.89 / 1.98 ms at 8 / 16 planes;
+// dendrite 0.670 ms against 0.689 / 0.715), although a CTA's march then
+// repeats a larger share of halo planes: the marches are short, the grid
+// is deep, and no general tile, whose lone march sets the step's tail,
+// runs long.
 template <class Real>
 struct Block3D;
 template <>
 struct Block3D<float> {
-  static constexpr int BX = 32, BY = 16, ZS = 16;
+  static constexpr int BX = 32, BY = 16, ZS = 6;
 };
 template <>
 struct Block3D<double> {
