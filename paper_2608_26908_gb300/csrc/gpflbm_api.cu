@@ -229,6 +229,13 @@ Layout make_layout(const Ops* ops, long long cells, long long plane, long long t
   return L;
 }
 
+// Velocity c_k of the lattice with Q populations (D2Q9, D3Q19, D3Q27).
+void lattice_velocity(int Q, int k, int* c) {
+  for (int a = 0; a < 3; ++a)
+    c[a] = Q == 9 ? (a < 2 ? gpflbm::Lattice<9>::c(k, a) : 0)
+                  : (Q == 19 ? gpflbm::Lattice<19>::c(k, a) : gpflbm::Lattice<27>::c(k, a));
+}
+
 template <class Real>
 void fill_params(gpflbm_t h, DevParams<Real>& P) {
   const gpflbm_params& p = h->params;
@@ -287,6 +294,14 @@ void fill_params(gpflbm_t h, DevParams<Real>& P) {
   P.v_lo = 0;
   P.v_hi = h->D == 3 ? h->grid.nz : h->grid.ny;
   P.zbase = 0;
+  // population byte offsets: a cell's own k, and where its collided k lands
+  const long long es = (long long)h->ops->store_size, zst = (long long)h->px * h->grid.ny;
+  for (int k = 0; k < h->ops->Q; ++k) {
+    int c[3];
+    lattice_velocity(h->ops->Q, k, c);
+    P.f_at[k] = (long long)k * h->plane * es;
+    P.f_to[k] = ((long long)k * h->plane + c[0] + (long long)c[1] * h->px + (long long)c[2] * zst) * es;
+  }
 }
 
 gpflbm_status check_params(const gpflbm_params* p, int NP, std::string* why) {

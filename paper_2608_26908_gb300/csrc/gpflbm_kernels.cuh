@@ -162,6 +162,12 @@ struct DevParams {
   // only the normal component of each face gradient (the transverse ones
   // are skipped, exactly).
   int aniso;
+  // Byte offsets in a population buffer from a cell's population 0 (the
+  // stored type's size): f_at[k] = k plane, the cell's own population k;
+  // f_to[k] = f_at[k] + c_k . (1, px, px ny), where the collided population
+  // k of a cell away from the edges lands.  Host-computed, so that each
+  // access is one 64-bit add of a parameter to the cell's address.
+  long long f_at[27], f_to[27];
 };
 
 // 1/x rounded to nearest: the same value as the IEEE division 1/x, by the
@@ -198,6 +204,16 @@ __device__ __forceinline__ bool obstacle(const DevParams<Real>& P, int x, int y,
   for (int a = 0; a < 3; ++a)
     if (P.wall[a] > 0 && (c[a] < P.wall[a] || c[a] >= P.n[a] - P.wall[a])) return true;
   return false;
+}
+
+// The element `off` bytes after p (population offsets f_at, f_to).
+template <class T>
+__device__ __forceinline__ T& at_bytes(T* p, long long off) {
+  return *reinterpret_cast<T*>(reinterpret_cast<char*>(p) + off);
+}
+template <class T>
+__device__ __forceinline__ const T& at_bytes(const T* p, long long off) {
+  return *reinterpret_cast<const T*>(reinterpret_cast<const char*>(p) + off);
 }
 
 // ------------------------------------------------------------------ push streaming

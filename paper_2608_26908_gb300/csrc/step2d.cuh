@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   {
     Real dk[Q];
 #pragma unroll
-    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[g]);
+    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + g, P.f_at[k]));
     if constexpr (SHRINK) {
 #pragma unroll
       for (int k = 0; k < Q; ++k) s_fs[k * NT + tid] = Codec<Store>::put(dk[k]);  // exact round trip
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     if (inner_tile) {
 #pragma unroll
       for (int k = 0; k < Q; ++k)
-        (f_out + k * P.plane)[g] = s_fs[k * NT + tid - Lat::c(k, 0) - Lat::c(k, 1) * BX];
+        at_bytes(f_out + g, P.f_at[k]) = s_fs[k * NT + tid - Lat::c(k, 0) - Lat::c(k, 1) * BX];
     } else {
       const bool wx = P.bc[0] == kWall, wy = P.bc[1] == kWall;
 #pragma unroll
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
         const bool bounce =
             (wx && (gx - cx < 0 || gx - cx >= nx)) || (wy && (gy - cy < 0 || gy - cy >= ny));
         const Store v = bounce ? s_fs[Lat::opp(k) * NT + tid] : s_fs[k * NT + tid - cx - cy * BX];
-        (f_out + k * P.plane)[g] = v;
+        at_bytes(f_out + g, P.f_at[k]) = v;
       }
     }
   };

@@ -323,7 +323,7 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
       if constexpr (!SHRINK) {
       Real dk[Q];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + gi, P.f_at[k]));
       Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
@@ -351,10 +351,10 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         const bool inner_z = C >= 1 && C + 1 < nz;
         if (inner_xy && inner_z) {
           // x + c_k is inside the grid: population k lands at gi + c_k . (1, px, zst)
+          Store* const fo = f_out + gi;
           collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
             if (hdir != 0 && Lat::c(k, 2) != hdir) return;
-            const int off = Lat::c(k, 0) + Lat::c(k, 1) * px + Lat::c(k, 2) * zst;
-            (f_out + k * P.plane + off)[gi] = Codec<Store>::put(val);
+            at_bytes(fo, P.f_to[k]) = Codec<Store>::put(val);
           });
         } else {
         // push to x + c_k (periodic axes wrap; across a wall the population
@@ -557,7 +557,7 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         const bool obs = has_walls && obstacle(P, fx, fy, fzc);
         Real dk[Q];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
+        for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + gi, P.f_at[k]));
         Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
         for (int k = 0; k < Q; ++k) {

@@ -109,7 +109,7 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
       }
       Real dk[Q];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load((f_in + k * P.plane)[gi]);
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + gi, P.f_at[k]));
       Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
@@ -128,10 +128,8 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
       if (owner && C >= z0 && C < z0 + ZS && C < P.v_hi) {
         const bool inner_z = C >= 1 && C + 1 < nz;
         if (inner_xy && inner_z) {
-          collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
-            const int off = Lat::c(k, 0) + Lat::c(k, 1) * px + Lat::c(k, 2) * zst;
-            (f_out + k * P.plane + off)[gi] = Codec<Store>::put(val);
-          });
+          Store* const fo = f_out + gi;
+          collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) { at_bytes(fo, P.f_to[k]) = Codec<Store>::put(val); });
         } else {
           const PushAxis X = push_axis(gx, nx, P.bc[0] == kWall, 1);
           const PushAxis Y = push_axis(gy, ny, P.bc[1] == kWall, px);
