@@ -29,7 +29,7 @@ struct Liquid3D {
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
   // a ring of three planes of U and mu, and the in-plane solute fluxes of
-  // two planes: two barriers a plane (see the kernel)
+  // two planes: one barrier a plane (see liquid_tile)
   static constexpr size_t u = 0;                                    // 3 planes x 3 x NT
   static constexpr size_t mu = al(u + sizeof(Real) * 3 * 3 * NT);   // 3 planes x NC x NT
   static constexpr size_t flux = al(mu + sizeof(Real) * 3 * NC * NT);  // 2 planes x 2 x NC x NT
@@ -90,13 +90,14 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
 #pragma unroll
   for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i] = Real(0);
 
-  // Ring slots of planes M and C = M + 1 (three slots: the plane the
-  // update of one iteration reads is not rewritten before every thread has
-  // passed the next iteration's two barriers).
+  // Ring slots of planes M and C = M + 1.  One barrier a plane: the in-plane
+  // fluxes of a plane are formed in the iteration that produced its U and
+  // mu, into one half of a double buffer, and read by the next iteration's
+  // update; three slots of U and mu, so that the slot B overwrites held the
+  // plane three back, which no thread reads after the previous barrier.
   int sM = 2, sC = 0;
   for (int C = z0 - 1; C <= z0 + ZS; ++C) {
     const int M = C - 1;
-    Real* fl = s_flux + (C & 1) * 2 * NC * NT;  // in-plane fluxes of plane M
     // B. moments, U and (owned planes) collision + push, plane C
     {
       const int fzc = vzi(C);
@@ -141,45 +142,36 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
       }
     }
     __syncthreads();
-    // D. solute fluxes of plane M (M-1 .. M+1 liquid: M = M0, h_l = 1)
+    // D. solute fluxes (every plane M-1 .. C+1 liquid: M = M0, h_l = 1).
+    // face between this cell in plane pA (slot sA) and nbT in plane pB (slot sB)
+    auto face = [&](int d, int pA, int sA, int pB, int sB, int nbT, int gbd, Real* J) {
+      const bool open = d == 2 ? zin : inner_xy;
+      const bool closed = !open && ((P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d]);
+#pragma unroll
+      for (int i = 0; i < NC; ++i) J[i] = Real(0);
+      if (closed) return;
+      const int fzA = vzi(pA);
+      const Real ua = s_u[(sA * 3 + d) * NT + tid], ub = s_u[(sB * 3 + d) * NT + nbT];
+      const int fzB = d == 2 ? vzi(pB) : fzA;
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        const Real ma = s_mu[(sA * NC + i) * NT + tid], mb = s_mu[(sB * NC + i) * NT + nbT];
+        J[i] = liquid_flux(P, ma, mb, ua, ub, ceq_of(0, i, fzA), ceq_of(0, i, fzB));
+      }
+    };
+    // the z-face (M, C) of this column
     const bool doM = M >= z0 - 1 && M <= z0 + ZS - 1;
     if (doM) {
-      const int fzm = vzi(M);
-      // face between this cell (plane M) and nbT in plane pB (slot sB)
-      auto face = [&](int d, int pB, int sB, int nbT, int gbd, Real* J) {
-        const bool open = d == 2 ? zin : inner_xy;
-        const bool closed = !open && ((P.bc[d] == kWall && (gbd == 0 || gbd == P.n[d])) || gbd > P.n[d]);
-#pragma unroll
-        for (int i = 0; i < NC; ++i) J[i] = Real(0);
-        if (closed) return;
-        const Real ua = s_u[(sM * 3 + d) * NT + tid], ub = s_u[(sB * 3 + d) * NT + nbT];
-        const int fzB = d == 2 ? vzi(pB) : fzm;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) {
-          const Real ma = s_mu[(sM * NC + i) * NT + tid], mb = s_mu[(sB * NC + i) * NT + nbT];
-          J[i] = liquid_flux(P, ma, mb, ua, ub, ceq_of(0, i, fzm), ceq_of(0, i, fzB));
-        }
-      };
-      face(2, M + 1, sC, tid, M + 1, mz_hi);
+      face(2, M, sM, C, sC, tid, C, mz_hi);
       if (M == z0 - 1) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
-      } else {
-        Real J[NC];
-        if (tx < BX - 1) {
-          face(0, M, sM, tid + 1, gx + 1, J);
-#pragma unroll
-          for (int i = 0; i < NC; ++i) fl[(i * 2 + 0) * NT + tid] = J[i];
-        }
-        if (ty < BY - 1) {
-          face(1, M, sM, tid + BX, gy + 1, J);
-#pragma unroll
-          for (int i = 0; i < NC; ++i) fl[(i * 2 + 1) * NT + tid] = J[i];
-        }
       }
     }
-    __syncthreads();
+    // the update of plane M: its in-plane fluxes (formed last iteration) and
+    // its two z-faces
     if (doM && M >= z0 && M < P.v_hi && owner) {
+      const Real* fl = s_flux + (M & 1) * 2 * NC * NT;
       const int g = zrow(M) + gxy;
 #pragma unroll
       for (int sidx = 0; sidx < NS; ++sidx)
@@ -201,6 +193,21 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
     if (doM && M >= z0) {
 #pragma unroll
       for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
+    }
+    // the in-plane fluxes of plane C, for its update in the next iteration
+    if (C >= z0 && C <= z0 + ZS - 1) {
+      Real* fl = s_flux + (C & 1) * 2 * NC * NT;
+      Real J[NC];
+      if (tx < BX - 1) {
+        face(0, C, sC, C, sC, tid + 1, gx + 1, J);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) fl[(i * 2 + 0) * NT + tid] = J[i];
+      }
+      if (ty < BY - 1) {
+        face(1, C, sC, C, sC, tid + BX, gy + 1, J);
+#pragma unroll
+        for (int i = 0; i < NC; ++i) fl[(i * 2 + 1) * NT + tid] = J[i];
+      }
     }
     sM = sC;
     sC = sC == 2 ? 0 : sC + 1;
