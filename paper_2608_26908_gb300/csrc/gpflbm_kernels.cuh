@@ -216,28 +216,6 @@ __device__ __forceinline__ const T& at_bytes(const T* p, long long off) {
   return *reinterpret_cast<const T*>(reinterpret_cast<const char*>(p) + off);
 }
 
-// L2 prefetch of the row a warp reads in a later plane (a row of BX = 32
-// cells, one per lane, spans at most two 128-byte lines per array): lane k
-// < Q takes population k, lanes Q .. Q+NC-1 the chemical potentials, each
-// the lines of the row's first and last cells.  g: this lane's cell.
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-template <int Q, int NC, class Store, class Real>
-__device__ __forceinline__ void prefetch_row(const DevParams<Real>& P, const Store* f, const Real* mu, int g) {
-  const int lane = threadIdx.x & 31;
-  const int first = __shfl_sync(0xffffffffu, g, 0), last = __shfl_sync(0xffffffffu, g, 31);
-  if (lane < Q) {
-    const Store* b = &at_bytes(f, P.f_at[lane]);
-    prefetch_l2(b + first);
-    prefetch_l2(b + last);
-  } else if (lane < Q + NC) {
-    const Real* m = mu + (lane - Q) * P.plane;
-    prefetch_l2(m + first);
-    prefetch_l2(m + last);
-  }
-}
-
 // ------------------------------------------------------------------ push streaming
 // Where the populations of a cell stream to along one axis: the offset (in
 // elements) of the +1 and -1 neighbour, periodic axes wrapping, and whether a

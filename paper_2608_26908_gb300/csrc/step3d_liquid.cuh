@@ -98,8 +98,6 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
   int sM = 2, sC = 0;
   for (int C = z0 - 1; C <= z0 + ZS; ++C) {
     const int M = C - 1;
-    // the next plane's rows on their way to L2 while this one is worked on
-    if (C < z0 + ZS) prefetch_row<Q, NC>(P, f_in, mu_in, zrow(vzi(C + 1)) + gxy);
     // B. moments, U and (owned planes) collision + push, plane C
     {
       const int fzc = vzi(C);
