@@ -83,32 +83,6 @@ inline unsigned exchange_blocks(long long items, int threads) {
   return (unsigned)(need < 2LL * sms ? need : 2LL * sms);
 }
 
-// Shared-memory carveout hint for a kernel of `threads` threads a CTA and
-// `bytes` of dynamic shared memory: the smallest split that holds as many
-// CTAs as its registers let reside on an SM (with the system's reservation
-// and the few static bytes), so that the rest of the SM's unified 256 KB
-// stays L1 cache.
-template <class K>
-cudaError_t carve(K kernel, size_t bytes, int threads) {
-  static int max_smem = -1;
-  if (max_smem < 0) {
-    int dev = 0, v = 0;
-    max_smem = cudaGetDevice(&dev) == cudaSuccess &&
-                       cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess
-                   ? v
-                   : 0;
-  }
-  cudaFuncAttributes a;
-  if (max_smem <= 0 || cudaFuncGetAttributes(&a, kernel) != cudaSuccess || a.numRegs <= 0) return cudaSuccess;
-  const int per_warp = (a.numRegs * 32 + 255) / 256 * 256;  // registers are allocated per warp
-  int ctas = 65536 / (per_warp * (threads / 32));
-  if (ctas > 2048 / threads) ctas = 2048 / threads;
-  if (ctas < 1) ctas = 1;
-  const size_t need = (size_t)ctas * (bytes + 1024 + 128);
-  const int pct = (int)((need * 100 + (size_t)max_smem - 1) / (size_t)max_smem);
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
-}
-
 // QQ: lattice size (0 = D2Q9 in 2D, D3Q19 in 3D; 27 = D3Q27).
 // EXT: the step kernels of the extended model -- turned crystal axes and
 // temperature-dependent equilibrium compositions (a separate table, so that
@@ -131,21 +105,16 @@ struct Impl {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(step2d_kernel<NP, NC, Real, Store, true, EXT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SZ::bytes);
-      if (e == cudaSuccess) e = carve(step2d_kernel<NP, NC, Real, Store, false, EXT>, SZ::bytes, SZ::NT);
-      if (e == cudaSuccess) e = carve(step2d_kernel<NP, NC, Real, Store, true, EXT>, SZ::bytes, SZ::NT);
     } else {
       e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, false, Q, EXT>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step3d_bytes);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(step3d_kernel<NP, NC, Real, Store, true, Q, EXT>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step3d_bytes);
-      if (e == cudaSuccess) e = carve(step3d_kernel<NP, NC, Real, Store, false, Q, EXT>, step3d_bytes, S3::NT);
-      if (e == cudaSuccess) e = carve(step3d_kernel<NP, NC, Real, Store, true, Q, EXT>, step3d_bytes, S3::NT);
       if constexpr (!S3::ONE_LAUNCH) {
         if (e == cudaSuccess)
           e = cudaFuncSetAttribute(step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL::bytes);
-        if (e == cudaSuccess) e = carve(step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT>, SL::bytes, SL::NT);
       }
     }
     return e;
