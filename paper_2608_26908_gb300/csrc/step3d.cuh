@@ -52,10 +52,11 @@ struct Step3D {
   // the registers spill at 64 and one CTA of 128 registers runs faster
   static constexpr int MIN_CTAS = (sizeof(Real) == 4 && QQ == 19) ? 2 : 1;
   // both paths in one launch where they have the same register budget and
-  // the general path is light (two phases).  With more phases a general
-  // tile sharing its SM with a liquid-tile CTA, which issues far more
-  // often, is slowed so much that the slowest general tiles end last: the
-  // ternary eutectic takes 2.32 ms a step in one launch, 2.04 ms in two.
+  // the general path's shared memory is small (two phases: 54 KB).  A launch
+  // reserves its largest path's shared memory for every CTA, and with more
+  // phases (108 KB) the liquid tiles are left too little L1 for their loads
+  // in flight: the ternary eutectic takes 2.22 ms a step in one launch,
+  // 1.79 ms in two.
   static constexpr bool ONE_LAUNCH = MIN_CTAS == 2 && NP == 2;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;

@@ -224,8 +224,8 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
 // ones, start first and the liquid tiles fill the SMs as they finish
 // instead of waiting for the last general tile.  Elsewhere (FP64, D3Q27:
 // the general path needs more registers than the liquid one, and one kernel
-// would hold the liquid tiles to its occupancy; three or four phases: see
-// ONE_LAUNCH) step3d_kernel takes the general tiles and
+// would hold the liquid tiles to its occupancy; three or four phases: its
+// shared memory, see ONE_LAUNCH) step3d_kernel takes the general tiles and
 // step3d_liquid_kernel, launched after it, the others.
 template <int NP, int NC, class Real, class Store, bool SHRINK = false, int QQ = 19, bool EXT = false>
 __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP, NC, Real, Store, QQ>::MIN_CTAS)
