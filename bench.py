@@ -688,8 +688,8 @@ def our_arm(args):
         return 0
     nx_, ny_, nz_ = inputs.dims(sc)
     # one step: one fused launch in 2D; in 3D one launch over the general and
-    # the liquid tiles (FP32 on D3Q19), else the general kernel and the
-    # liquid-tile kernel over disjoint tiles (every cell advanced once)
+    # the liquid tiles (two phases, FP32 on D3Q19), else the general kernel
+    # and the liquid-tile kernel over disjoint tiles (every cell advanced once)
     dom_name = ("step3d_kernel + step3d_liquid_kernel" if launches == 2 else
                 "step%dd_kernel" % (3 if nz_ > 1 else 2))
     # the committed ncu summaries hold the traffic of a full-size launch of

@@ -688,7 +688,7 @@ gpflbm_status gpflbm_set_params(gpflbm_t h, const gpflbm_params* params) {
   drop_graphs(h);  // parameters are baked into captured launches
   ++h->mut;
   if (h->has_state && h->pf.liq_dispatch && !had) {
-    // the flags were not kept while every tile took the general kernel
+    // the flags were not kept while every tile took the general path
     cudaError_t e = classify(h, h->cur, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
     if (e != cudaSuccess) return cuda_fail(h, e, "set_params: liquid tiles");

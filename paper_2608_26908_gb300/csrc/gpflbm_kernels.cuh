@@ -177,8 +177,8 @@ __device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
 
 // Explicitly rounded operations: the compiler fuses a*b+c into one rounding
 // where it sees fit, which may differ between two kernels; the arithmetic
-// that the liquid-tile kernel shares with the general kernel is written
-// with these so that both give the same bits.
+// that the liquid path shares with the general path (in one kernel or two)
+// is written with these so that both give the same bits.
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }

@@ -141,7 +141,7 @@ struct Impl {
         step3d_kernel<NP, NC, Real, Store, true, Q, EXT><<<grid, S3::NT, step3d_bytes, s>>>(P, sio);
       else
         step3d_kernel<NP, NC, Real, Store, false, Q, EXT><<<grid, S3::NT, step3d_bytes, s>>>(P, sio);
-      // the tiles whose reach is pure liquid (the general kernel returned there)
+      // the tiles whose reach is pure liquid (step3d_kernel returned there)
       if constexpr (!S3::ONE_LAUNCH) {
         if (P.liq_dispatch)
           step3d_liquid_kernel<NP, NC, Real, Store, Q, EXT><<<grid, SL::NT, SL::bytes, s>>>(P, sio);

@@ -1,5 +1,7 @@
-// Fused 3D step kernel for sm_103a: one launch advances the grid by one time
-// step (Algorithm 1: phase field, chemical potential, lattice Boltzmann).
+// Fused 3D step for sm_103a, the general path (Algorithm 1: phase field,
+// chemical potential, lattice Boltzmann).  Tiles whose reach is pure liquid
+// take the lean path of step3d_liquid.cuh instead; the kernels that run the
+// two are at the end of that file.
 //
 // A CTA owns an xy tile and a z segment of ZS planes.  It runs one thread per
 // cell of the tile's one-cell xy halo region ("R1", BX x BY columns) and
@@ -48,8 +50,9 @@ struct Step3D {
   static constexpr int NT = BX * BY, Q = QQ;  // D3Q19 or D3Q27
   static constexpr int NS = PhiStore<NP>::NS;
   // resident CTAs per SM the register budget is cut for: two (64 registers)
-  // for two phases on D3Q19 in FP32; with more phases, or 27 populations,
-  // the registers spill at 64 and one CTA of 128 registers runs faster
+  // on D3Q19 in FP32, for any number of phases (three and four phases spill
+  // a few dozen bytes, yet two CTAs of 64 registers beat one of 128: 1.79
+  // against 1.91 ms on the ternary eutectic); FP64 and 27 populations: one
   static constexpr int MIN_CTAS = (sizeof(Real) == 4 && QQ == 19) ? 2 : 1;
   // both paths in one launch where they have the same register budget and
   // the general path's shared memory is small (two phases: 54 KB).  A launch

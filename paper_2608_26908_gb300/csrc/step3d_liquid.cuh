@@ -120,7 +120,7 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
           if (Lat::c(k, a) != 0) m3[a] += Real(Lat::c(k, a)) * dk[k];
       }
       const Real rho = Real(1) + drho;
-      // the general kernel's arithmetic with phi_l = 1 (the same helpers)
+      // the general path's arithmetic with phi_l = 1 (the same helpers)
       const Real drive = buoyancy_drive<NC, EXT>(P, fma_rn(P.G, Real(fzc), theta_base), mu);
       Real u[3], F[3];
       force_velocity<3>(P, rho, Real(1), drive, m3, u, F);
