@@ -53,11 +53,7 @@ typedef enum {
   GPFLBM_ERR_OOM = -2,         /* workspace too small or device allocation failed */
   GPFLBM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
   GPFLBM_ERR_NONFINITE = -4,   /* NaN or Inf found in the state by gpflbm_invariants */
-  GPFLBM_ERR_TIMEOUT = -5,     /* a bounded device wait gave up: the 3D step waits (at most half
-                                  a second) for the bulk copies that stage its liquid tiles'
-                                  planes in shared memory; on giving up it loads the plane
-                                  directly (the state stays correct) and records the event,
-                                  which gpflbm_invariants and gpflbm_invariants_noalloc report */
+  /* -5 is not used: no kernel of the library waits on another agent */
   GPFLBM_ERR_STATE = -6,       /* call out of order (e.g. step before set_state) */
   GPFLBM_ERR_UNSUPPORTED = -7  /* valid but not built: phase/solute count, lattice */
 } gpflbm_status;
@@ -282,9 +278,7 @@ gpflbm_status gpflbm_get_deviations(gpflbm_t h, void* dst, int dst_is_device, vo
  * xor-butterfly (offsets 16, 8, 4, 2, 1); lane 0 of warps 0..7 are then
  * added in order; the G block sums are added in order.  Synchronises
  * `stream`.  Returns GPFLBM_ERR_NONFINITE (totals still written) if any
- * cell of the state is NaN or Inf, else GPFLBM_ERR_TIMEOUT (totals still
- * written) if a 3D step since the handle was created gave up waiting for
- * its staged loads.  Any output pointer may be NULL. */
+ * cell of the state is NaN or Inf.  Any output pointer may be NULL. */
 gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double* solid_frac,
                                 void* stream);
 
@@ -304,7 +298,7 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
  * cudaDeviceReset (after one, handles and this entry point on that device
  * are not usable).  Calls share the array: calls that overlap on the GPU
  * race.  Synchronises `stream`; outputs and statuses (GPFLBM_ERR_NONFINITE,
- * GPFLBM_ERR_TIMEOUT, GPFLBM_ERR_STATE) as for gpflbm_invariants. */
+ * GPFLBM_ERR_STATE) as for gpflbm_invariants. */
 gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, double* solute,
                                         double* solid_frac, void* stream);
 

@@ -29,7 +29,7 @@ constexpr int kChunk = 16;  // steps per replayed CUDA graph
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t phi[2], mu[2], f[2], stage, clock, partial, red, flags[2], err;
+  size_t phi[2], mu[2], f[2], stage, clock, partial, red, flags[2];
   size_t total;
 };
 
@@ -225,7 +225,6 @@ Layout make_layout(const Ops* ops, long long cells, long long plane, long long t
   L.partial = take(gpflbm::kRedMaxBlocks * (ops->NC + 3) * sizeof(double));
   L.red = take((ops->NC + 3) * sizeof(double));
   for (int i = 0; i < 2; ++i) L.flags[i] = take((size_t)tiles);
-  L.err = take(sizeof(unsigned int));  // zero until a bounded device wait gives up
   L.total = off;
   return L;
 }
@@ -429,7 +428,6 @@ gpflbm::StepIO step_io(gpflbm_t h, int from) {
   io.clock_out = reinterpret_cast<double*>(at(h, h->lay.clock)) + 1 - from;
   io.flags_in = static_cast<const unsigned char*>(at(h, h->lay.flags[from]));
   io.flags_out = static_cast<unsigned char*>(at(h, h->lay.flags[1 - from]));
-  io.err = static_cast<unsigned int*>(at(h, h->lay.err));
   return io;
 }
 
@@ -1030,14 +1028,9 @@ gpflbm_status gpflbm_invariants(gpflbm_t h, double* mass, double* solute, double
   cudaError_t e = run_invariants(h, partial, blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: kernel");
   double out[GPFLBM_MAX_SOLUTES + 3];
-  unsigned int err_word = 0;
   e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&err_word, at(h, h->lay.err), sizeof(err_word), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants: copy");
-  if (err_word)
-    return fail(h, GPFLBM_ERR_TIMEOUT, "invariants: a bounded wait of the 3D step for its staged loads gave up "
-                "(the step fell back to plain loads)");
   if (mass) *mass = out[0] + (double)h->cells;
   if (solute)
     for (int i = 0; i < h->NC; ++i) solute[i] = out[1 + i];
@@ -1275,14 +1268,9 @@ extern "C" gpflbm_status gpflbm_invariants_noalloc(gpflbm_t h, double* mass, dou
   e = run_invariants(h, partial, (int)blocks, red, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: kernel");
   double out[kNoAllocValues];
-  unsigned int err_word = 0;
   e = cudaMemcpyAsync(out, red, (h->NC + 3) * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&err_word, at(h, h->lay.err), sizeof(err_word), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "invariants_noalloc: copy");
-  if (err_word)
-    return fail(h, GPFLBM_ERR_TIMEOUT, "invariants_noalloc: a bounded wait of the 3D step for its staged loads gave up "
-                "(the step fell back to plain loads)");
   if (mass) *mass = out[0] + (double)h->cells;
   if (solute)
     for (int i = 0; i < h->NC; ++i) solute[i] = out[1 + i];
@@ -1410,7 +1398,6 @@ gpflbm_status adjoint_run(gpflbm_t h, const gpflbm_objective* obj, int H, const 
     io.clock_out = forward_pass ? fw_clk(c, j + 1) : clk_at(c, j + 1);
     io.flags_in = nullptr;  // 2D: no liquid-tile flags
     io.flags_out = nullptr;
-    io.err = nullptr;
     return stepper(h)->step(P, io, st);
   };
   // copies of one stored state: handle -> slot, or slot -> handle

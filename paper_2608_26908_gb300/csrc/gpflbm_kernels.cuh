@@ -216,62 +216,6 @@ __device__ __forceinline__ const T& at_bytes(const T* p, long long off) {
   return *reinterpret_cast<const T*>(reinterpret_cast<const char*>(p) + off);
 }
 
-// ------------------------------------------------------------------ bulk copies
-// Bulk asynchronous copies from global into shared memory (the TMA unit),
-// completed on a shared-memory mbarrier of the CTA.  Every wait is bounded:
-// it gives up after kWaitNs of the global timer and reports that to the
-// caller, which then falls back to plain loads and records the failure.
-constexpr unsigned long long kWaitNs = 500000000ull;  // half a second
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// the one arrival of a phase, announcing the bytes its copies will bring
-__device__ __forceinline__ void mbar_arrive_expect(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// waits until the phase of the given parity has completed; false if it gave
-// up after kWaitNs
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  if (mbar_test(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_test(bar, parity))
-    if (global_ns() - t0 > kWaitNs) return false;
-  return true;
-}
-// bytes (a multiple of 16) from a 16-byte aligned global address into
-// shared memory, completing on bar
-__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-// orders this thread's earlier shared-memory accesses before later bulk
-// copies into the same memory
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 // ------------------------------------------------------------------ push streaming
 // Where the populations of a cell stream to along one axis: the offset (in
 // elements) of the +1 and -1 neighbour, periodic axes wrapping, and whether a

@@ -23,7 +23,6 @@ struct StepIO {
   double* clock_out;
   const unsigned char* flags_in;  // 3D: liquid flag per tile of the input state
   unsigned char* flags_out;       // ... of the output state
-  unsigned int* err;              // 3D: error word of the handle (see Step3DIO)
 };
 
 struct FieldsIO {
@@ -136,8 +135,8 @@ struct Impl {
       const unsigned gz = (P.v_hi - P.v_lo + S3::ZS - 1) / S3::ZS;
       const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY,
                       S3::ONE_LAUNCH && P.liq_dispatch ? 2 * gz : gz);
-      const Step3DIO sio = {io.phi_in,  io.phi_out,  io.mu_in,    io.mu_out,     io.f_in,   io.f_out,
-                            io.clock_in, io.clock_out, io.flags_in, io.flags_out, io.err};
+      const Step3DIO sio = {io.phi_in, io.phi_out, io.mu_in,    io.mu_out,    io.f_in,
+                            io.f_out,  io.clock_in, io.clock_out, io.flags_in, io.flags_out};
       if (P.shrink)
         step3d_kernel<NP, NC, Real, Store, true, Q, EXT><<<grid, S3::NT, step3d_bytes, s>>>(P, sio);
       else

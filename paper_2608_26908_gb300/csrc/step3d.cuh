@@ -90,7 +90,6 @@ struct Step3DIO {
   double* clock_out;
   const unsigned char* flags_in;  // liquid flag per tile of the input state
   unsigned char* flags_out;       // ... of the output state
-  unsigned int* err;              // bit 0: a bounded wait for staged loads gave up (may be null)
 };
 
 // EXT: the extended model -- pairs' crystal axes turned about z (dAdq_pair)

@@ -28,27 +28,12 @@ struct Liquid3D {
   static constexpr int NT = BX * BY;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
-  // Staged planes (FP32 arithmetic on D3Q19, where two CTAs still fit an
-  // SM): a plane's populations and mu reach shared memory by bulk copies,
-  // one per array and row of the tile.  A row starts on a 16-byte boundary
-  // (XA elements) at or before the tile's first column and is XW elements
-  // long, so that it covers the tile's BX columns wherever they start.
-  static constexpr bool STAGE = sizeof(Real) == 4 && QQ == 19;
-  static constexpr int XA = 16 / (int)sizeof(Store);
-  static constexpr int XW = (BX + XA - 1 + XA - 1) / XA * XA;
-  static constexpr int NROWS = (QQ + NC) * BY;  // one copy a thread
-  static constexpr unsigned stage_bytes =
-      STAGE ? (unsigned)(QQ * BY * XW * sizeof(Store) + NC * BY * XW * sizeof(Real)) : 0u;
-  static constexpr size_t fst = 0;  // Q x BY x XW populations
-  static constexpr size_t mst = al(fst + (STAGE ? sizeof(Store) * QQ * BY * XW : 0));  // NC x BY x XW mu
   // a ring of three planes of U and mu, and the in-plane solute fluxes of
   // two planes: one barrier a plane (see liquid_tile)
-  static constexpr size_t u = al(mst + (STAGE ? sizeof(Real) * NC * BY * XW : 0));  // 3 planes x 3 x NT
+  static constexpr size_t u = 0;                                    // 3 planes x 3 x NT
   static constexpr size_t mu = al(u + sizeof(Real) * 3 * 3 * NT);   // 3 planes x NC x NT
   static constexpr size_t flux = al(mu + sizeof(Real) * 3 * NC * NT);  // 2 planes x 2 x NC x NT
   static constexpr size_t bytes = al(flux + sizeof(Real) * 2 * 2 * NC * NT);
-  static_assert(!STAGE || NROWS <= NT, "one row copy a thread");
-  static_assert(!STAGE || (XW * sizeof(Store)) % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
 // The liquid path for one tile (coordinates as for general_tile).
@@ -60,12 +45,9 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
   constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
   constexpr int NS = PhiStore<NP>::NS;
   extern __shared__ __align__(16) unsigned char smem[];
-  Store* s_fst = reinterpret_cast<Store*>(smem + S::fst);
-  Real* s_mst = reinterpret_cast<Real*>(smem + S::mst);
   Real* s_u = reinterpret_cast<Real*>(smem + S::u);
   Real* s_mu = reinterpret_cast<Real*>(smem + S::mu);
   Real* s_flux = reinterpret_cast<Real*>(smem + S::flux);
-  __shared__ __align__(8) unsigned long long s_bar;
 
   const Real* __restrict__ mu_in = static_cast<const Real*>(io.mu_in);
   const Store* __restrict__ f_in = static_cast<const Store*>(io.f_in);
@@ -108,37 +90,6 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
 #pragma unroll
   for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i] = Real(0);
 
-  // Staging of the planes a CTA reads (inner tiles whose rows fit the
-  // padded row pitch): plane C's rows are copied while plane C-1 is being
-  // finished, into one buffer, after the barrier that ends plane C-1's reads
-  // of it.  One mbarrier phase a plane: thread 0 arrives announcing the
-  // bytes, threads tid < NROWS copy one row each.  A wait that gives up
-  // (the copies never landed) records it in io.err and the CTA goes on with
-  // plain loads.
-  const int xs = (x0 - 1) / S::XA * S::XA;  // first staged column (x0 >= 2 on inner tiles)
-  const int rx = x0 - 1 - xs;               // the tile's first column in the staged rows
-  bool stage = S::STAGE && inner_xy && zin && xs + S::XW <= px;
-  const unsigned bar = smem_addr(&s_bar);
-  int gave_up = -1;  // parity of a phase this thread stopped waiting for
-  auto issue = [&](int v) {  // the copies of plane v (inside the grid)
-    if (tid < S::NROWS) {
-      const int k = tid / BY, yy = tid % BY;
-      const long long row = (long long)zrow(v) + (long long)(y0 - 1 + yy) * px + xs;
-      if (k < Q)
-        bulk_load(smem_addr(s_fst + (k * BY + yy) * S::XW), &at_bytes(f_in, P.f_at[k]) + row,
-                  S::XW * (unsigned)sizeof(Store), bar);
-      else
-        bulk_load(smem_addr(s_mst + ((k - Q) * BY + yy) * S::XW), mu_in + (k - Q) * P.plane + row,
-                  S::XW * (unsigned)sizeof(Real), bar);
-    }
-  };
-  if (stage) {  // the same on every thread of the CTA
-    if (tid == 0) mbar_init(bar, 1);
-    __syncthreads();
-    if (tid == 0) mbar_arrive_expect(bar, S::stage_bytes);
-    issue(z0 - 1);
-  }
-
   // Ring slots of planes M and C = M + 1.  One barrier a plane: the in-plane
   // fluxes of a plane are formed in the iteration that produced its U and
   // mu, into one half of a double buffer, and read by the next iteration's
@@ -151,29 +102,15 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
     {
       const int fzc = vzi(C);
       const int gi = zrow(fzc) + gxy;
-      const unsigned parity = (unsigned)(C - (z0 - 1)) & 1u;
-      if (stage && !mbar_wait(bar, parity)) {
-        stage = false;
-        gave_up = (int)parity;
-        if (io.err) atomicOr(io.err, 1u);
+      Real mu[NC];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        mu[i] = (mu_in + i * P.plane)[gi];
+        s_mu[(sC * NC + i) * NT + tid] = mu[i];
       }
-      Real mu[NC], dk[Q];
-      if (stage) {
-        const int o = ty * S::XW + tx + rx;
+      Real dk[Q];
 #pragma unroll
-        for (int i = 0; i < NC; ++i) mu[i] = s_mst[i * BY * S::XW + o];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(s_fst[k * BY * S::XW + o]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < NC; ++i) mu[i] = (mu_in + i * P.plane)[gi];
-#pragma unroll
-        for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + gi, P.f_at[k]));
-      }
-      // the next plane's copies are announced once this one has landed
-      if (stage && tid == 0 && C < z0 + ZS) mbar_arrive_expect(bar, S::stage_bytes);
-#pragma unroll
-      for (int i = 0; i < NC; ++i) s_mu[(sC * NC + i) * NT + tid] = mu[i];
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + gi, P.f_at[k]));
       Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
@@ -204,16 +141,7 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
         }
       }
     }
-    // every thread has read plane C's staged rows: the buffer takes plane C+1
-    if (S::STAGE) {
-      stage = __syncthreads_and(stage);
-      if (stage && C < z0 + ZS) {
-        fence_async_smem();
-        issue(C + 1);
-      }
-    } else {
-      __syncthreads();
-    }
+    __syncthreads();
     // D. solute fluxes (every plane M-1 .. C+1 liquid: M = M0, h_l = 1).
     // face between this cell in plane pA (slot sA) and nbT in plane pB (slot sB)
     auto face = [&](int d, int pA, int sA, int pB, int sB, int nbT, int gbd, Real* J) {
@@ -285,8 +213,6 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
     sC = sC == 2 ? 0 : sC + 1;
   }
   if (tid < ZS && z0 + tid < P.v_hi) io.flags_out[liquid_flag_index(bx, by, z0 + tid, gxt, gyt)] = 1;
-  // copies this thread stopped waiting for must not land after the CTA ends
-  if (gave_up >= 0) mbar_wait(bar, (unsigned)gave_up);
 }
 
 // The step kernels.  Where both paths fit 64 registers (FP32 arithmetic on

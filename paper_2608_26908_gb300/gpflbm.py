@@ -16,8 +16,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libgpflbm.so")
 OK = 0
 # exchange flags of gpflbm_set_state / gpflbm_get_fields (include/gpflbm.h)
 ON_DEVICE, ASYNC = 1, 2
-ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_STATE, ERR_UNSUPPORTED = (
-    -1, -2, -3, -4, -5, -6, -7)
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_STATE, ERR_UNSUPPORTED = (
+    -1, -2, -3, -4, -6, -7)
 PERIODIC, WALL = 0, 1
 D2Q9, D3Q19, D3Q27 = 9, 19, 27
 PRECISION = {"fp64": 0, "fp32": 1, "fp32_f16": 2, "fp32_bf16": 3}
