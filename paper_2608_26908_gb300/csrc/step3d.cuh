@@ -68,9 +68,12 @@ struct Step3D {
   static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
   static constexpr size_t phi = 0;                                  // 4 planes x NS x C2
   static constexpr size_t mask = al(phi + sizeof(Real) * 4 * NS * C2);  // 3 planes x C2
-  static constexpr size_t pn = al(mask + 3 * C2);                   // 3 planes x NP x NT
-  static constexpr size_t u = al(pn + sizeof(Real) * 3 * NP * NT);   // 2 planes x 3 x NT
-  static constexpr size_t mu = al(u + sizeof(Real) * 2 * 3 * NT);    // 2 planes x NC x NT
+  // phi^{n+1} of planes C and M (written in C, read by the solute faces
+  // and the update of the next iteration); U_x, U_y of the same two planes
+  // (U_z only enters this column's own z-face: registers)
+  static constexpr size_t pn = al(mask + 3 * C2);                   // 2 planes x NP x NT
+  static constexpr size_t u = al(pn + sizeof(Real) * 2 * NP * NT);   // 2 planes x 2 x NT
+  static constexpr size_t mu = al(u + sizeof(Real) * 2 * 2 * NT);    // 2 planes x NC x NT
   static constexpr size_t hl = al(mu + sizeof(Real) * 2 * NC * NT);  // 2 planes x NT
   static constexpr size_t chg = al(hl + sizeof(Real) * 2 * NT);      // 2 planes x NT bytes
   static constexpr size_t flux = al(chg + 2 * NT);                   // PF or solute in-plane faces
@@ -221,6 +224,8 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
   Real pfz_lo[NP], pfz_hi[NP];
   // solute z-face fluxes of this column: (M-1, M) carried, (M, M+1) new
   Real mz_lo[NC], mz_hi[NC];
+  // U_z of this column in planes M and C
+  Real uz_M = Real(0), uz_C = Real(0);
 #pragma unroll
   for (int a = 0; a < NP; ++a) pfz_lo[a] = pfz_hi[a] = Real(0);
 #pragma unroll
@@ -285,6 +290,7 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
   const int L0 = z0 - 2, L1 = z0 + ZS + 1;
   for (int L = L0; L <= L1; ++L) {
     const int C = L - 1, M = L - 2;
+    uz_M = uz_C;  // plane C of the previous iteration is this one's M
     bool liq_l;  // this thread's cells of plane L are pure liquid
     // A. phi^n of plane L
     {
@@ -343,7 +349,8 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
       Real u[3], F[3];
       force_velocity<3>(P, rho, phl, drive, m3, u, F);
 #pragma unroll
-      for (int a = 0; a < 3; ++a) s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
+      for (int a = 0; a < 2; ++a) s_u[(slot2(C) * 2 + a) * NT + tid] = u[a];
+      uz_C = u[2];
       // A slab also collides the cells of its halo planes next to a
       // neighbouring slab and keeps only the populations that stream into
       // its own planes (hdir = +1 below, -1 above): the same values the
@@ -533,7 +540,7 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
       bool changed = false;
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
-        s_pn[(slot3(C) * NP + a) * NT + tid] = out[a];
+        s_pn[(slot2(C) * NP + a) * NT + tid] = out[a];
         changed = changed || out[a] != PH(C, a, r2);
       }
       if constexpr (SHRINK) {
@@ -592,8 +599,9 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
           const Real fb = a == 2 ? FB : Real(0);
           u[a] = (m3[a] + Real(0.5) * (fb + fs[a])) * inv;
           F[a] = fb + fs[a] - rho * kappa * u[a];
-          s_u[(slot2(C) * 3 + a) * NT + tid] = u[a];
+          if (a < 2) s_u[(slot2(C) * 2 + a) * NT + tid] = u[a];
         }
+        uz_C = u[2];
         if (owner && C >= z0 && C < z0 + ZS && C < P.v_hi) {
           collide<Q>(P, dk, drho, rho, u, F, [&](int k, Real val) {
             const Store v = Codec<Store>::put(val);
@@ -640,7 +648,8 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         if (closed) return;
         const int pA = M, A = tid, rA = r2;
         if (lean_d) {
-          const Real ua = s_u[(slot2(pA) * 3 + d) * NT + A], ub = s_u[(slot2(pB) * 3 + d) * NT + nbT];
+          const Real ua = d == 2 ? uz_M : s_u[(slot2(pA) * 2 + d) * NT + A];
+          const Real ub = d == 2 ? uz_C : s_u[(slot2(pB) * 2 + d) * NT + nbT];
           const int fzB = d == 2 ? vz(pB) : fzm;
 #pragma unroll
           for (int i = 0; i < NC; ++i) {
@@ -649,11 +658,11 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
           }
           return;
         }
-        const Real* pnA = s_pn + slot3(pA) * NP * NT;
-        const Real* pnB = s_pn + slot3(pB) * NP * NT;
+        const Real* pnA = s_pn + slot2(pA) * NP * NT;
+        const Real* pnB = s_pn + slot2(pB) * NP * NT;
         const Real Mf = Real(0.5) * P.M0 * (pnA[A] + pnB[nbT]);  // plane 0 = liquid
-        const Real ua = s_u[(slot2(pA) * 3 + d) * NT + A] * s_hl[slot2(pA) * NT + A];
-        const Real ub = s_u[(slot2(pB) * 3 + d) * NT + nbT] * s_hl[slot2(pB) * NT + nbT];
+        const Real ua = (d == 2 ? uz_M : s_u[(slot2(pA) * 2 + d) * NT + A]) * s_hl[slot2(pA) * NT + A];
+        const Real ub = (d == 2 ? uz_C : s_u[(slot2(pB) * 2 + d) * NT + nbT]) * s_hl[slot2(pB) * NT + nbT];
         const int fzB = d == 2 ? vz(pB) : fzm;  // vertical index of B (ceq(T))
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
@@ -735,7 +744,7 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
         po[a] = PH(M, a, r2);
-        pn[a] = s_pn[(slot3(M) * NP + a) * NT + tid];
+        pn[a] = s_pn[(slot2(M) * NP + a) * NT + tid];
       }
 #pragma unroll
       for (int sidx = 0; sidx < NS; ++sidx) phi_out[sidx * P.plane + g] = pn[NP == 2 ? 1 : sidx];
