@@ -55,11 +55,11 @@ struct Step3D {
   // against 1.91 ms on the ternary eutectic); FP64 and 27 populations: one
   static constexpr int MIN_CTAS = (sizeof(Real) == 4 && QQ == 19) ? 2 : 1;
   // both paths in one launch where they have the same register budget and
-  // the general path's shared memory is small (two phases: 54 KB).  A launch
+  // the general path's shared memory is small (two phases: 46 KB).  A launch
   // reserves its largest path's shared memory for every CTA, and with more
-  // phases (108 KB) the liquid tiles are left too little L1 for their loads
-  // in flight: the ternary eutectic takes 2.22 ms a step in one launch,
-  // 1.79 ms in two.
+  // phases (96 KB) the liquid tiles are left too little L1 for their loads
+  // in flight: the ternary eutectic takes 1.88 ms a step in one launch,
+  // 1.77 ms in two.
   static constexpr bool ONE_LAUNCH = MIN_CTAS == 2 && NP == 2;
   static constexpr int OX = BX - 2, OY = BY - 2;
   static constexpr int W2 = BX + 2, H2 = BY + 2, C2 = W2 * H2;
