@@ -356,13 +356,12 @@ void slab_views(gpflbm_t h, DevParams<Real>& P, DevParams<Real>& X) {
   X.zbase = 0;
 }
 
-// Liquid tiles take the lean path in 3D, and skip their phase-field loads
-// in 2D, from per-tile flags of the state; not on slabs (their halo planes
-// come from another handle), with shrinkage or obstacle rows, and where a
-// periodic x or y axis ends in a tile of one cell (a tile's reach would
-// then wrap past its neighbour tiles).
+// Liquid tiles take the lean kernel in 3D, except on slabs (their halo
+// planes come from another handle), with shrinkage or obstacle rows, and
+// where a periodic x or y axis ends in a tile of one cell (a tile's reach
+// would then wrap past its neighbour tiles; planes are flagged one by one).
 bool liquid_dispatch(gpflbm_t h) {
-  if (h->slab || h->pf.shrink) return false;
+  if (h->D != 3 || h->slab || h->pf.shrink) return false;
   const gpflbm_grid& g = h->grid;
   if (g.wall_rows[0] | g.wall_rows[1] | g.wall_rows[2]) return false;
   const bool fp64 = g.precision == GPFLBM_FP64;

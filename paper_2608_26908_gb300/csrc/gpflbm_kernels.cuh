@@ -288,29 +288,6 @@ __device__ __forceinline__ bool liquid_reach(const DevParams<Real>& P, const uns
   return s_all != 0;
 }
 
-// 2D: the flags of the 3x3 tiles around xy tile (bx, by) (one plane, v = 0)
-// are all set.  Every thread reads the nine flags itself: no barrier.
-template <class Real>
-__device__ __forceinline__ bool liquid_reach2d(const DevParams<Real>& P, const unsigned char* __restrict__ flags,
-                                               int bx, int by, int gx, int gy) {
-  bool all = true;
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    int c[2] = {bx + t % 3 - 1, by + t / 3 - 1};
-    const int n[2] = {gx, gy};
-    bool skip = false;
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      if (c[a] < 0 || c[a] >= n[a]) {
-        if (P.bc[a] == kWall) skip = true;
-        c[a] = c[a] < 0 ? c[a] + n[a] : c[a] - n[a];
-      }
-    }
-    if (!skip && !flags[liquid_flag_index(c[0], c[1], 0, gx, gy)]) all = false;
-  }
-  return all;
-}
-
 // ------------------------------------------------------------------ shared cell arithmetic
 // Buoyancy drive of the melt at a cell: g beta_T (T - T_ref) +
 // sum_i g beta_i (c_l,i(mu) - c_ref,i), theta = T - T_E; EXT: c_l,i at T.

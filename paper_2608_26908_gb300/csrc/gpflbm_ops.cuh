@@ -124,8 +124,8 @@ struct Impl {
     const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
     if constexpr (D == 2) {
       const dim3 grid((P.n[0] + SZ::OX - 1) / SZ::OX, (P.n[1] + SZ::OY - 1) / SZ::OY);
-      const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in,    io.mu_out,    io.f_in,
-                            io.f_out,  io.clock_in, io.clock_out, io.flags_in, io.flags_out};
+      const Step2DIO sio = {io.phi_in, io.phi_out, io.mu_in, io.mu_out,
+                            io.f_in,   io.f_out,   io.clock_in, io.clock_out};
       if (P.shrink)
         step2d_kernel<NP, NC, Real, Store, true, EXT><<<grid, SZ::NT, SZ::bytes, s>>>(P, sio);
       else
@@ -209,15 +209,19 @@ struct Impl {
     return cudaGetLastError();
   }
 
-  // The liquid flags of a state: per xy tile and plane in 3D, per tile in
-  // 2D (one plane; the 2D tiles have the 3D tiles' shape).
   static cudaError_t classify(const void* params, const void* phi, unsigned char* flags, cudaStream_t s) {
-    static_assert(Block2D<Real>::BX == Block3D<Real>::BX && Block2D<Real>::BY == Block3D<Real>::BY,
-                  "2D tiles are classified with the 3D tiling");
-    const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
-    const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY, D == 3 ? P.v_hi - P.v_lo : 1);
-    liquid_flags_kernel<NP, Real><<<grid, 128, 0, s>>>(P, static_cast<const Real*>(phi), flags);
-    return cudaGetLastError();
+    if constexpr (D == 3) {
+      const DevParams<Real>& P = *static_cast<const DevParams<Real>*>(params);
+      const dim3 grid((P.n[0] + S3::OX - 1) / S3::OX, (P.n[1] + S3::OY - 1) / S3::OY, P.v_hi - P.v_lo);
+      liquid_flags_kernel<NP, Real><<<grid, 128, 0, s>>>(P, static_cast<const Real*>(phi), flags);
+      return cudaGetLastError();
+    } else {
+      (void)params;
+      (void)phi;
+      (void)flags;
+      (void)s;
+      return cudaSuccess;
+    }
   }
 
   static cudaError_t invariants(const InvParams& p, const void* phi, const void* mu, const void* f,

@@ -74,8 +74,6 @@ struct Step2DIO {
   void* f_out;
   const double* clock_in;
   double* clock_out;
-  const unsigned char* flags_in;  // liquid flag per tile of the input state (null: none kept)
-  unsigned char* flags_out;       // ... of the output state (null: none kept)
 };
 
 // EXT: the extended model -- pairs' crystal axes turned about z (dAdq_pair)
@@ -134,19 +132,9 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     for (int a = 1; a < NP; ++a) p = p && v[a] == Real(0);
     return p;
   };
-  // A tile whose 3x3 tile neighbourhood is flagged pure liquid (the flags of
-  // the input state) holds pure liquid in R1 and its ring: its phases are
-  // the pure-liquid values, and it reads no phi.
-  const bool flagged = P.liq_dispatch && io.flags_in &&
-                       liquid_reach2d(P, io.flags_in, (int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y);
   Real ph[NP];
-  if (flagged) {
-#pragma unroll
-    for (int a = 0; a < NP; ++a) ph[a] = a == 0 ? Real(1) : Real(0);
-  } else {
-    load_phases<NP>(phi_in, g, P.plane, ph);
-  }
-  bool liquid = flagged || (pure_liquid(ph) && !obs);  // the tile's cells, for the liquid-tile path
+  load_phases<NP>(phi_in, g, P.plane, ph);
+  bool liquid = pure_liquid(ph) && !obs;  // the tile's cells, for the liquid-tile path
   // the ring cell of a thread tid < RING: its R1-plus-ring index rr and its
   // offset in a plane
   auto ring_cell = [&](int& rr) {
@@ -169,7 +157,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     rr = ry * W2 + rx;
     return qy * px + qx;
   };
-  if (!flagged && tid < S::RING) {
+  if (tid < S::RING) {
     int rr;
     Real rv[NP];
     load_phases<NP>(phi_in, ring_cell(rr), P.plane, rv);
@@ -316,8 +304,6 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
     if (tx < BX - 1) face(0);
     if (ty < BY - 1) face(1);
     __syncthreads();
-    if (tid == 0 && io.flags_out)  // the tile stays pure liquid
-      io.flags_out[liquid_flag_index((int)blockIdx.x, (int)blockIdx.y, 0, (int)gridDim.x, (int)gridDim.y)] = 1;
     if (!inner) return;
 #pragma unroll
     for (int sidx = 0; sidx < NS; ++sidx) (phi_out + sidx * P.plane)[g] = ph[NP == 2 ? 1 : sidx];
@@ -586,10 +572,7 @@ __global__ void __launch_bounds__(Step2D<NP, NC, Real, Store>::NT, Block2D<Real>
   };
   if (tx < BX - 1) mu_face(0);
   if (ty < BY - 1) mu_face(1);
-  // the tile's flag of the new state: every cell it owns pure liquid
-  const bool tile_liq = __syncthreads_and(!inner || (pure_liquid(out) && !obs));
-  if (tid == 0 && io.flags_out)
-    io.flags_out[liquid_flag_index((int)blockIdx.x, (int)blockIdx.y, 0, (int)gridDim.x, (int)gridDim.y)] = tile_liq;
+  __syncthreads();
 
   // 3. inner cells: mu^{n+1}, phi^{n+1}, pulled f^{n+1}
   if (!inner) return;
