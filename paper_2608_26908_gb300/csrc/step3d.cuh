@@ -74,12 +74,11 @@ struct Step3D {
   static constexpr size_t pn = al(mask + 3 * C2);                   // 2 planes x NP x NT
   static constexpr size_t u = al(pn + sizeof(Real) * 2 * NP * NT);   // 2 planes x 2 x NT
   static constexpr size_t mu = al(u + sizeof(Real) * 2 * 2 * NT);    // 2 planes x NC x NT
-  // the changed flags of planes C and M, one bit a cell (a word a warp)
-  static constexpr size_t chg = al(mu + sizeof(Real) * 2 * NC * NT);  // 2 planes x NT / 32 words
-  // y faces of the phase field or of the solute (an x face travels between
-  // the lanes of a warp, which is a row of the tile)
-  static constexpr size_t flux = al(chg + sizeof(unsigned) * 2 * (NT / 32));
-  static constexpr size_t flux_n = NP * PFY > NC * NT ? NP * PFY : NC * NT;
+  static constexpr size_t hl = al(mu + sizeof(Real) * 2 * NC * NT);  // 2 planes x NT
+  static constexpr size_t chg = al(hl + sizeof(Real) * 2 * NT);      // 2 planes x NT bytes
+  static constexpr size_t flux = al(chg + 2 * NT);                   // PF or solute in-plane faces
+  static constexpr size_t flux_n =
+      NP * (PFX + PFY) > 2 * NC * NT ? NP * (PFX + PFY) : 2 * NC * NT;
   static constexpr size_t bytes = al(flux + sizeof(Real) * flux_n);
 };
 
@@ -115,7 +114,8 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
   Real* s_pn = reinterpret_cast<Real*>(smem + S::pn);
   Real* s_u = reinterpret_cast<Real*>(smem + S::u);
   Real* s_mu = reinterpret_cast<Real*>(smem + S::mu);
-  unsigned* s_chg = reinterpret_cast<unsigned*>(smem + S::chg);
+  Real* s_hl = reinterpret_cast<Real*>(smem + S::hl);
+  unsigned char* s_chg = smem + S::chg;
   Real* s_flux = reinterpret_cast<Real*>(smem + S::flux);
 
   const Real* __restrict__ phi_in = static_cast<const Real*>(io.phi_in);
@@ -197,8 +197,6 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
     return b[a * C2 + i];
   };
   auto MK = [&](int p, int i) -> unsigned { return s_mask[slot3(p) * C2 + i]; };
-  // the changed flag of cell i (a thread index) of plane p (C or M)
-  auto chg_bit = [&](int p, int i) -> bool { return (s_chg[slot2(p) * (NT / 32) + (i >> 5)] >> (i & 31)) & 1u; };
   // a cell of pure liquid: phi_0 = 1 and every other phase 0, exactly
   auto pure_liquid = [](const Real* v) {
     bool p = v[0] == Real(1);
@@ -417,34 +415,32 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
     // plane (and the z-face above it) is exactly zero.
     // (planes C-1, C and L all liquid: nothing mixes, and the CTA knows it
     // without another barrier)
-    Real pfdx[NP];  // x-face difference of each phase's flux at this cell
     if ((liq_hist & 7u) == 7u || !__syncthreads_or(pfC && mixed)) {
 #pragma unroll
       for (int a = 0; a < NP; ++a) pfz_hi[a] = Real(0);
     } else {
       if (pfC) {
-        // x faces: this cell's +x face, and its -x face from the lane to
-        // the left (lane 0 forms its own); y faces into shared memory
-        Real fl[NP], flm[NP];
+        // in-plane faces of plane C into shared memory
+        Real fl[NP];
         const bool cx_hi = P.bc[0] == kWall && (gx + 1 == 0 || gx + 1 == nx);
         pf_flux(C, r2, C, r2 + 1, 0, cx_hi, fl);
 #pragma unroll
-        for (int a = 0; a < NP; ++a) flm[a] = __shfl_up_sync(0xffffffffu, fl[a], 1);
+        for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + ty * (BX + 1) + tx + 1] = fl[a];
         if (tx == 0) {
           const bool cx_lo = P.bc[0] == kWall && (gx == 0 || gx == nx);
-          pf_flux(C, r2 - 1, C, r2, 0, cx_lo, flm);
-        }
+          pf_flux(C, r2 - 1, C, r2, 0, cx_lo, fl);
 #pragma unroll
-        for (int a = 0; a < NP; ++a) pfdx[a] = fl[a] - flm[a];
+          for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + ty * (BX + 1)] = fl[a];
+        }
         const bool cy_hi = P.bc[1] == kWall && (gy + 1 == 0 || gy + 1 == ny);
         pf_flux(C, r2, C, r2 + W2, 1, cy_hi, fl);
 #pragma unroll
-        for (int a = 0; a < NP; ++a) s_flux[a * S::PFY + (ty + 1) * BX + tx] = fl[a];
+        for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + S::PFX + (ty + 1) * BX + tx] = fl[a];
         if (ty == 0) {
           const bool cy_lo = P.bc[1] == kWall && (gy == 0 || gy == ny);
           pf_flux(C, r2 - W2, C, r2, 1, cy_lo, fl);
 #pragma unroll
-          for (int a = 0; a < NP; ++a) s_flux[a * S::PFY + tx] = fl[a];
+          for (int a = 0; a < NP; ++a) s_flux[a * (S::PFX + S::PFY) + S::PFX + tx] = fl[a];
         }
         // z-faces of this column: (C, C+1), and (C-1, C) on the first plane
         const bool cz_hi = P.bc[2] == kWall && (C + 1 == 0 || C + 1 == nz);
@@ -459,8 +455,9 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         Real div[NP], gc[NP][3];
 #pragma unroll
         for (int a = 0; a < NP; ++a) {
-          const Real* fa = s_flux + a * S::PFY;
-          div[a] = pfdx[a] + (fa[(ty + 1) * BX + tx] - fa[ty * BX + tx]) + (pfz_hi[a] - pfz_lo[a]);
+          const Real* fa = s_flux + a * (S::PFX + S::PFY);
+          div[a] = (fa[ty * (BX + 1) + tx + 1] - fa[ty * (BX + 1) + tx]) +
+                   (fa[S::PFX + (ty + 1) * BX + tx] - fa[S::PFX + ty * BX + tx]) + (pfz_hi[a] - pfz_lo[a]);
           // a phase absent from the 3x3x3 neighbourhood has a zero central
           // gradient, and its pairs contribute exactly 0 below
           gc[a][0] = gc[a][1] = gc[a][2] = Real(0);
@@ -626,14 +623,8 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
           });
         }
       }
-      const unsigned chw = __ballot_sync(0xffffffffu, changed);
-      if ((tid & 31) == 0) s_chg[slot2(C) * (NT / 32) + (tid >> 5)] = chw;
-      // U is kept premultiplied by h_l(phi^{n+1}), the factor of the
-      // advective solute flux (1 exactly in pure liquid)
-      const Real hl = interp_h<NP>(out, 0);
-      s_u[(slot2(C) * 2 + 0) * NT + tid] *= hl;
-      s_u[(slot2(C) * 2 + 1) * NT + tid] *= hl;
-      uz_C *= hl;
+      s_chg[slot2(C) * NT + tid] = changed ? 1 : 0;
+      s_hl[slot2(C) * NT + tid] = interp_h<NP>(out, 0);
 #pragma unroll
       for (int a = 0; a < NP; ++a) pfz_lo[a] = pfz_hi[a];
     }
@@ -641,7 +632,6 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
 
     // D. solute fluxes of plane M and the update of the owned planes
     const bool doM = M >= z0 - 1 && M <= z0 + ZS - 1;
-    Real mdx[NC];  // x-face difference of the solute fluxes at this cell
     const bool outM = doM && M >= z0 && M < P.v_hi;
     // planes M-1 .. M+2 liquid: phi^{n+1} = phi^n = liquid on planes M and
     // M+1, so h_l = 1, M = M0, no antitrapping, chi = 1 / (2 A_l), no obstacles
@@ -671,8 +661,8 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         const Real* pnA = s_pn + slot2(pA) * NP * NT;
         const Real* pnB = s_pn + slot2(pB) * NP * NT;
         const Real Mf = Real(0.5) * P.M0 * (pnA[A] + pnB[nbT]);  // plane 0 = liquid
-        const Real ua = d == 2 ? uz_M : s_u[(slot2(pA) * 2 + d) * NT + A];  // U h_l
-        const Real ub = d == 2 ? uz_C : s_u[(slot2(pB) * 2 + d) * NT + nbT];
+        const Real ua = (d == 2 ? uz_M : s_u[(slot2(pA) * 2 + d) * NT + A]) * s_hl[slot2(pA) * NT + A];
+        const Real ub = (d == 2 ? uz_C : s_u[(slot2(pB) * 2 + d) * NT + nbT]) * s_hl[slot2(pB) * NT + nbT];
         const int fzB = d == 2 ? vz(pB) : fzm;  // vertical index of B (ceq(T))
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
@@ -683,7 +673,7 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         // the current carries phi_l's face value as a factor of every term: on
         // a face without liquid (grain boundaries inside the solid) it is
         // exactly 0 and skipped
-        const Real liq = P.at_eps != Real(0) && (chg_bit(pA, A) | chg_bit(pB, nbT))
+        const Real liq = P.at_eps != Real(0) && (s_chg[slot2(pA) * NT + A] | s_chg[slot2(pB) * NT + nbT])
                              ? Real(0.5) * (PH(pA, 0, rA) + PH(pB, 0, nbR))
                              : Real(0);
         if (liq != Real(0)) {
@@ -730,23 +720,19 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
 #pragma unroll
         for (int i = 0; i < NC; ++i) mz_lo[i] = mz_hi[i];
       } else {
-        // in-plane faces of plane M: x faces between the lanes of a warp
-        // (the -x face of this cell is the +x face of the lane to the left),
-        // y faces in shared memory
+        // in-plane faces of plane M
         Real J[NC];
-#pragma unroll
-        for (int i = 0; i < NC; ++i) J[i] = Real(0);
         if (tx < BX - 1) {
           const bool ob = walls && !lean_d && obstacle(P, fold_axis(P, gx + 1, 0), fy, fzm);
           mu_face(0, M, tid + 1, r2 + 1, gx + 1, ob, J);
-        }
 #pragma unroll
-        for (int i = 0; i < NC; ++i) mdx[i] = J[i] - __shfl_up_sync(0xffffffffu, J[i], 1);
+          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 0) * NT + tid] = J[i];
+        }
         if (ty < BY - 1) {
           const bool ob = walls && !lean_d && obstacle(P, fx, fold_axis(P, gy + 1, 1), fzm);
           mu_face(1, M, tid + BX, r2 + W2, gy + 1, ob, J);
 #pragma unroll
-          for (int i = 0; i < NC; ++i) s_flux[i * NT + tid] = J[i];
+          for (int i = 0; i < NC; ++i) s_flux[(i * 2 + 1) * NT + tid] = J[i];
         }
       }
     }
@@ -768,8 +754,9 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         // temperature term alone (extended model)
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-          const Real* Jy = s_flux + i * NT;
-          const Real div = mdx[i] + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
+          const Real* Jx = s_flux + (i * 2 + 0) * NT;
+          const Real* Jy = s_flux + (i * 2 + 1) * NT;
+          const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
           const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
           Real src = Real(0);
           if constexpr (EXT) {
@@ -781,7 +768,7 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
       } else if (has_walls && obstacle(P, fx, fy, fzm)) {
 #pragma unroll
         for (int i = 0; i < NC; ++i) mu_out[i * P.plane + g] = s_mu[(slot2(M) * NC + i) * NT + tid];
-      } else if (!EXT && !chg_bit(M, tid) && pure_phase<NP>(pn) >= 0) {
+      } else if (!EXT && s_chg[slot2(M) * NT + tid] == 0 && pure_phase<NP>(pn) >= 0) {
         // unchanged pure cell: source term exactly 0, chi = 1 / (2 A_pure)
         const int pa = pure_phase<NP>(pn);
         Real ichi = P.chi_pure[0];
@@ -790,14 +777,15 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
           if (pa == a) ichi = P.chi_pure[a];
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-          const Real* Jy = s_flux + i * NT;
-          const Real div = mdx[i] + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
+          const Real* Jx = s_flux + (i * 2 + 0) * NT;
+          const Real* Jy = s_flux + (i * 2 + 1) * NT;
+          const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
           const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
           mu_out[i * P.plane + g] = mu + (-div - Real(0)) * ichi;
         }
       } else {
         Real chi = Real(0), hn[NP], ho[NP];
-        const bool changed = chg_bit(M, tid);
+        const bool changed = s_chg[slot2(M) * NT + tid] != 0;
 #pragma unroll
         for (int a = 0; a < NP; ++a) {
           hn[a] = interp_h<NP>(pn, a);
@@ -807,8 +795,9 @@ __device__ __forceinline__ void general_tile(const DevParams<Real>& P, const Ste
         const Real ichi = rcp_rn(chi);
 #pragma unroll
         for (int i = 0; i < NC; ++i) {
-          const Real* Jy = s_flux + i * NT;
-          const Real div = mdx[i] + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
+          const Real* Jx = s_flux + (i * 2 + 0) * NT;
+          const Real* Jy = s_flux + (i * 2 + 1) * NT;
+          const Real div = (Jx[tid] - Jx[tid - 1]) + (Jy[tid] - Jy[tid - BX]) + (mz_hi[i] - mz_lo[i]);
           const Real mu = s_mu[(slot2(M) * NC + i) * NT + tid];
           Real src = Real(0);
           if (changed) {
