@@ -37,12 +37,9 @@ struct Liquid3D {
 };
 
 // The liquid path for one tile (coordinates as for general_tile).
-// check: the tile's flags are read here, after the loads of its first
-// plane are on their way (a tile that is not liquid returns, those loads
-// unused), so that the two latencies overlap.
 template <int NP, int NC, class Real, class Store, int QQ, bool EXT>
 __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step3DIO& io, int bx, int by, int bz,
-                                            int gxt, int gyt, bool check) {
+                                            int gxt, int gyt) {
   using S = Liquid3D<NP, NC, Real, Store, QQ, EXT>;
   using Lat = Lattice<QQ>;
   constexpr int BX = S::BX, BY = S::BY, ZS = S::ZS, NT = S::NT, Q = QQ;
@@ -70,6 +67,7 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
   const int gxy = fy * px + fx;
   const bool owner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && gx < nx && gy < ny;
   const double t_now = io.clock_in[0];
+  if (bx == 0 && by == 0 && bz == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
   const Real theta_base = Real(P.theta0) - Real(P.GV) * Real(t_now);
   auto ceq_of = [&](int a, int i, int v) -> Real {
     if constexpr (EXT)
@@ -97,18 +95,6 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
   // mu, into one half of a double buffer, and read by the next iteration's
   // update; three slots of U and mu, so that the slot B overwrites held the
   // plane three back, which no thread reads after the previous barrier.
-  // this column's populations and mu of the plane being read
-  Real mu[NC], dk[Q];
-  auto load_plane = [&](int gi) {
-#pragma unroll
-    for (int i = 0; i < NC; ++i) mu[i] = (mu_in + i * P.plane)[gi];
-#pragma unroll
-    for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + gi, P.f_at[k]));
-  };
-  load_plane(zrow(vzi(z0 - 1)) + gxy);
-  if (check && !liquid_reach<ZS>(P, io.flags_in, bx, by, z0, gxt, gyt)) return;
-  if (bx == 0 && by == 0 && bz == 0 && tid == 0) io.clock_out[0] = t_now + 1.0;
-
   int sM = 2, sC = 0;
   for (int C = z0 - 1; C <= z0 + ZS; ++C) {
     const int M = C - 1;
@@ -116,9 +102,15 @@ __device__ __forceinline__ void liquid_tile(const DevParams<Real>& P, const Step
     {
       const int fzc = vzi(C);
       const int gi = zrow(fzc) + gxy;
-      if (C > z0 - 1) load_plane(gi);
+      Real mu[NC];
 #pragma unroll
-      for (int i = 0; i < NC; ++i) s_mu[(sC * NC + i) * NT + tid] = mu[i];
+      for (int i = 0; i < NC; ++i) {
+        mu[i] = (mu_in + i * P.plane)[gi];
+        s_mu[(sC * NC + i) * NT + tid] = mu[i];
+      }
+      Real dk[Q];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) dk[k] = Codec<Store>::load(at_bytes(f_in + gi, P.f_at[k]));
       Real drho = Real(0), m3[3] = {Real(0), Real(0), Real(0)};
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
@@ -244,20 +236,23 @@ __global__ void __launch_bounds__(Step3D<NP, NC, Real, Store, QQ>::NT, Step3D<NP
   const int bx = blockIdx.x, by = blockIdx.y;
   const bool liquid_pass = S::ONE_LAUNCH && (int)blockIdx.z >= gzt;
   const int bz = liquid_pass ? (int)blockIdx.z - gzt : (int)blockIdx.z;
+  if (P.liq_dispatch && liquid_reach<ZS>(P, io.flags_in, bx, by, P.v_lo + bz * ZS, gxt, gyt) != liquid_pass) return;
   if constexpr (S::ONE_LAUNCH) {
-    if (liquid_pass) {  // checks its tile's flags itself
-      liquid_tile<NP, NC, Real, Store, QQ, EXT>(P, io, bx, by, bz, gxt, gyt, true);
+    if (liquid_pass) {
+      liquid_tile<NP, NC, Real, Store, QQ, EXT>(P, io, bx, by, bz, gxt, gyt);
       return;
     }
   }
-  if (P.liq_dispatch && liquid_reach<ZS>(P, io.flags_in, bx, by, P.v_lo + bz * ZS, gxt, gyt)) return;
   general_tile<NP, NC, Real, Store, SHRINK, QQ, EXT>(P, io, bx, by, bz, gxt, gyt);
 }
 
 template <int NP, int NC, class Real, class Store, int QQ = 19, bool EXT = false>
 __global__ void __launch_bounds__(Liquid3D<NP, NC, Real, Store, QQ, EXT>::NT, 2)
     step3d_liquid_kernel(const DevParams<Real> P, const Step3DIO io) {
-  liquid_tile<NP, NC, Real, Store, QQ, EXT>(P, io, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y, true);
+  constexpr int ZS = Liquid3D<NP, NC, Real, Store, QQ, EXT>::ZS;
+  if (!liquid_reach<ZS>(P, io.flags_in, blockIdx.x, blockIdx.y, P.v_lo + blockIdx.z * ZS, gridDim.x, gridDim.y))
+    return;
+  liquid_tile<NP, NC, Real, Store, QQ, EXT>(P, io, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x, gridDim.y);
 }
 
 // The liquid flags of a state (after a load or a frame shift): one CTA per
